@@ -1,0 +1,18 @@
+"""FP64 CPU oracle of the GRFT / DS-GRFT hot path — TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this package.  It shares no code with the CUDA library:
+  * ``grft_oracle.c``  literal FP64 loops (plain GRFT, coarse RM gather, DS-GRFT,
+    CA-CFAR + top-K, trajectory adjoint, refinement), built with gcc
+    ``-O2 -fopenmp -ffp-contract=off`` so that every FP64 operation rounds once;
+  * ``brute.py``       an independent pure-numpy restatement for tiny shapes.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
+tests/test_oracle_pins.py (closed forms, library routines, brute force, invariants);
+none is "parity unpinned".
+"""
+from .wrap import (bins_phases, coarse_rm, cfar_detect, dsgrft_rows, dsgrft_full, grft_plain_rows,
+                   grft_plain_full, load, num_threads, refine, trajectory_grad)
+
+__all__ = ["bins_phases", "coarse_rm", "cfar_detect", "dsgrft_rows", "dsgrft_full",
+           "grft_plain_rows", "grft_plain_full", "load", "num_threads", "refine", "trajectory_grad"]

@@ -1,0 +1,245 @@
+"""Radar, search-grid and scenario definitions for the seeded synthetic workloads.
+
+This module holds inputs only (sizes, axes, target draws); it contains none of the
+transform's arithmetic.  Both the FP64 oracle and the CUDA library consume these
+values, and neither imports the other.
+
+Conventions (paper Sec. II-A/II-B, Sec. III-C):
+  * c = 3e8 m/s, wavelength lambda = c / f_c.
+  * Range bin  dr = c / (2 f_s) with f_s = B (eq. delta-R).
+  * Slow time  t_m = m / PRF, m = 0..M-1 (the paper's c_0 is the range at t = 0).
+  * Trajectory r(t) = r0 + v t + a t^2 / 2 (eq. slant range with P = 2, c_2 = a/2).
+  * Plain grid: r0 = integer bins, v_j = v.start + j v.step, a_k = a.start + k a.step.
+  * Dual-scale grid (eqs. Space_c_c, Space_c_f): coarse centres
+    v_c(i) = vc.start + i vc.step, fine offsets dv_k = (k - F_v/2) vc.step / F_v,
+    k = 0..F_v-1 (half-open, so neighbouring coarse cells do not overlap), and
+    likewise for a.  The fine hypothesis set then equals the plain grid with
+    v.start = vc.start - vc.step/2 and v.step = vc.step / F_v.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+C_MPS = 3.0e8
+
+
+@dataclass(frozen=True)
+class Radar:
+    M: int            # pulses (slow-time samples)
+    N: int            # range bins (fast-time samples)
+    fc_hz: float      # carrier frequency
+    prf_hz: float     # pulse repetition frequency
+    dr_m: float       # range bin c / (2 f_s)
+    c_mps: float = C_MPS
+
+    @property
+    def wavelength(self) -> float:
+        return self.c_mps / self.fc_hz
+
+    @property
+    def cpi_s(self) -> float:
+        return self.M / self.prf_hz
+
+
+@dataclass(frozen=True)
+class Axis:
+    start: float
+    step: float
+    count: int
+
+    def values(self) -> np.ndarray:
+        return self.start + np.arange(self.count, dtype=np.float64) * self.step
+
+
+@dataclass(frozen=True)
+class PlainGrid:
+    r0_begin: int
+    r0_count: int
+    v: Axis
+    a: Axis
+
+    @property
+    def n_hyp(self) -> int:
+        return self.r0_count * self.v.count * self.a.count
+
+
+@dataclass(frozen=True)
+class DSGrid:
+    r0_begin: int
+    r0_count: int
+    vc: Axis
+    ac: Axis
+    Fv: int
+    Fa: int
+
+    @property
+    def n_cells(self) -> int:
+        return self.vc.count * self.ac.count
+
+    @property
+    def n_fine(self) -> int:
+        return self.Fv * self.Fa
+
+    @property
+    def n_hyp(self) -> int:
+        return self.r0_count * self.n_cells * self.n_fine
+
+    def plain_equivalent(self) -> PlainGrid:
+        """The single-scale grid that searches the same hypotheses."""
+        return PlainGrid(
+            self.r0_begin, self.r0_count,
+            Axis(self.vc.start - 0.5 * self.vc.step, self.vc.step / self.Fv, self.vc.count * self.Fv),
+            Axis(self.ac.start - 0.5 * self.ac.step, self.ac.step / self.Fa, self.ac.count * self.Fa),
+        )
+
+
+@dataclass(frozen=True)
+class Target:
+    r0_bins: float    # range at t = 0, in bins (may be fractional)
+    v: float          # m/s
+    a: float          # m/s^2
+    amp: complex      # complex amplitude after pulse compression
+
+
+@dataclass(frozen=True)
+class CFAR:
+    guard: int = 2
+    train: int = 16
+    pfa: float = 1e-6
+    fixed_thresh: float = 0.0
+    mode: int = 0     # 0: CA-CFAR + 3x3x3 local max; 1: fixed threshold + local max
+
+
+@dataclass
+class Scenario:
+    name: str
+    radar: Radar
+    targets: List[Target]
+    seed: int
+    plain: PlainGrid | None = None
+    ds: DSGrid | None = None
+    snr_db: List[float] = field(default_factory=list)
+
+
+def _snr_amp(rng: np.random.Generator, snr_db: float) -> complex:
+    # per-sample post-compression SNR |A|^2 / sigma^2 with sigma^2 = 1, uniform phase
+    mag = 10.0 ** (snr_db / 20.0)
+    ph = rng.uniform(0.0, 2.0 * math.pi)
+    return complex(mag * math.cos(ph), mag * math.sin(ph))
+
+
+def walk_margin_bins(radar: Radar, vmax: float, amax: float) -> int:
+    T = radar.cpi_s
+    return int(math.ceil((vmax * T + 0.5 * amax * T * T) / radar.dr_m)) + 2
+
+
+def cfg1(run: int = 0) -> Scenario:
+    """Plain GRFT parity case: M=64, N=256, f_c=1 GHz, B=10 MHz (dr=15 m), PRF=500 Hz.
+
+    One sinc-shaped target at r0 = bin 100.3, v = 180 m/s, a = 12 m/s^2, SNR 3 dB.
+    Grid 256 r0 x 64 v x 16 a; v_j = 180 + (j-32) lambda/(2T), a_k = 12 + (k-8) lambda/(4T^2).
+    """
+    radar = Radar(M=64, N=256, fc_hz=1.0e9, prf_hz=500.0, dr_m=15.0)
+    T = radar.cpi_s
+    lam = radar.wavelength
+    dv = lam / (2.0 * T)
+    da = lam / (2.0 * T * T) * 0.5
+    grid = PlainGrid(0, 256, Axis(180.0 - 32 * dv, dv, 64), Axis(12.0 - 8 * da, da, 16))
+    seed = 1000 * 1 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tgt = [Target(100.3, 180.0, 12.0, _snr_amp(rng, 3.0))]
+    return Scenario("cfg1", radar, tgt, seed, plain=grid, snr_db=[3.0])
+
+
+def _ds_grid_cfg2(radar: Radar, Fv: int, Fa: int, r0_count: int | None = None) -> DSGrid:
+    # coarse 32 v x 8 a cells tiling v in [-300, 300] m/s, a in [-20, 20] m/s^2 (cell centres)
+    vstep = 600.0 / 32
+    astep = 40.0 / 8
+    return DSGrid(0, radar.N if r0_count is None else r0_count,
+                  Axis(-300.0 + 0.5 * vstep, vstep, 32), Axis(-20.0 + 0.5 * astep, astep, 8), Fv, Fa)
+
+
+def _random_targets(rng: np.random.Generator, radar: Radar, n: int, snr_lo: float, snr_hi: float,
+                    vlim: float = 295.0, alim: float = 19.5) -> Tuple[List[Target], List[float]]:
+    margin = walk_margin_bins(radar, 300.0, 20.0)
+    tg, snrs = [], []
+    for _ in range(n):
+        r0 = rng.uniform(margin, radar.N - margin)
+        v = rng.uniform(-vlim, vlim)
+        a = rng.uniform(-alim, alim)
+        snr = rng.uniform(snr_lo, snr_hi)
+        tg.append(Target(float(r0), float(v), float(a), _snr_amp(rng, snr)))
+        snrs.append(float(snr))
+    return tg, snrs
+
+
+def cfg2(run: int = 0) -> Scenario:
+    """DS-GRFT vs plain GRFT: M=512, N=4096, f_c=1.5 GHz, PRF=1 kHz, dr=15 m, 8 targets,
+    v in [-300,300] m/s, a in [-20,20] m/s^2, SNR in [-15,0] dB.
+    Coarse grid 4096 r0 x 32 v x 8 a; fine 64 dv x 16 da per coarse cell (2^30 hypotheses)."""
+    radar = Radar(M=512, N=4096, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    seed = 1000 * 2 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tg, snrs = _random_targets(rng, radar, 8, -15.0, 0.0)
+    ds = _ds_grid_cfg2(radar, 64, 16)
+    return Scenario("cfg2", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
+
+
+def cfg3(run: int = 0) -> Scenario:
+    """Precision case: M=2048, N=8192, 32 targets, SNR in [-20,0] dB, f_c=1.5 GHz, PRF=1 kHz,
+    coarse 32 v x 8 a as in cfg2, fine 256 dv x 64 da (3.4e10 hypotheses)."""
+    radar = Radar(M=2048, N=8192, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    seed = 1000 * 3 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tg, snrs = _random_targets(rng, radar, 32, -20.0, 0.0)
+    ds = _ds_grid_cfg2(radar, 256, 64)
+    return Scenario("cfg3", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
+
+
+def cfg4(run: int = 0, n_cpi: int = 64) -> List[Scenario]:
+    """Batching case: n_cpi independent CPIs with M ~ U{256..2048}, N ~ U{1024..8192},
+    1-16 targets each at SNR in [-15,5] dB; grids as in cfg2 (fine 64 x 16)."""
+    seed = 1000 * 4 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_cpi):
+        M = int(rng.integers(256, 2049))
+        N = int(rng.integers(1024, 8193))
+        radar = Radar(M=M, N=N, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+        nt = int(rng.integers(1, 17))
+        tg, snrs = _random_targets(rng, radar, nt, -15.0, 5.0)
+        ds = _ds_grid_cfg2(radar, 64, 16)
+        out.append(Scenario(f"cfg4[{i}]", radar, tg, seed * 100 + i, plain=ds.plain_equivalent(), ds=ds,
+                            snr_db=snrs))
+    return out
+
+
+def cfg5(run: int = 0) -> Scenario:
+    """Differentiation case: M=1024, N=4096, 16 targets whose motion lies off-grid
+    (uniform sub-cell offsets); grids as in cfg2; top-1000 detections, 20 ascent steps."""
+    radar = Radar(M=1024, N=4096, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    seed = 1000 * 5 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ds = _ds_grid_cfg2(radar, 64, 16)
+    pg = ds.plain_equivalent()
+    margin = walk_margin_bins(radar, 300.0, 20.0)
+    tg, snrs = [], []
+    for _ in range(16):
+        j = int(rng.integers(2, pg.v.count - 2))
+        k = int(rng.integers(2, pg.a.count - 2))
+        n0 = int(rng.integers(margin, radar.N - margin))
+        ov, oa, orr = rng.uniform(-0.5, 0.5, size=3)
+        snr = float(rng.uniform(-10.0, 0.0))
+        tg.append(Target(n0 + float(orr), float(pg.v.start + (j + ov) * pg.v.step),
+                         float(pg.a.start + (k + oa) * pg.a.step), _snr_amp(rng, snr)))
+        snrs.append(snr)
+    return Scenario("cfg5", radar, tg, seed, plain=pg, ds=ds, snr_db=snrs)
+
+
+def scaled(s: Scenario, **radar_overrides) -> Scenario:
+    return dataclasses.replace(s, radar=dataclasses.replace(s.radar, **radar_overrides))
