@@ -1,0 +1,196 @@
+/*
+ * dsgrft.h - C ABI of libdsgrft.so: the GRFT / DS-GRFT coherent sum over motion
+ * hypotheses on one GB300 (sm_103a), after arXiv 2403.06788.
+ *
+ * The statistic (Sec. III-A, eq. standard-GRFT-TD, with the range phase of the full
+ * trajectory; eq. slant range with P = 2):
+ *
+ *     Y(r0, v, a) = sum_{m=0}^{M-1} s[m][n0 + rho(v,a,m)] * exp(+j 4 pi r(t_m) / lambda)
+ *
+ *   t_m = m / PRF,  r(t) = r0 + v t + a t^2 / 2,  r0 = n0 * dr,  lambda = c / f_c,
+ *   d   = (v*t) + ((0.5*a)*(t*t))   (IEEE FP64, each operation rounded once),
+ *   rho = floor(d/dr + 0.5)         (nearest bin, ties toward +inf), and gathered samples
+ *   whose bin falls outside [0, N) contribute zero.
+ *
+ * Conventions shared by every call
+ *   - All array arguments are DEVICE pointers owned by the caller, unless stated
+ *     otherwise; parameter structs are HOST pointers read during the call only.
+ *   - Complex data is interleaved complex64 (grft_c32).  The echo is s[M][N], range
+ *     fastest.  Hypothesis outputs are row-major [v][a][r0] (r0 fastest).
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and is
+ *     asynchronous; no call synchronises the host except grft_sync_status().
+ *   - Every call returns GRFT_OK (0) or a negative status.  Argument errors are found on
+ *     the host before anything is enqueued.  Device-side conditions (a bounded wait that
+ *     gave up, a candidate-buffer overflow) are latched in a per-device flag that
+ *     grft_sync_status() returns and clears.  No call exits the process or throws.
+ *   - Internal workspace (tables, candidate buffers) is allocated by the library on first
+ *     use per device and grown when a larger problem needs it; grow events synchronise
+ *     the device, so make the first call of a given size before any stream capture.
+ *     Calls that share a device must not run concurrently on different streams.
+ *   - Calls run on the CUDA device that is current in the calling thread.
+ */
+#ifndef DSGRFT_H_
+#define DSGRFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRFT_ABI_VERSION 1
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+    GRFT_OK = 0,
+    GRFT_EINVAL = -1,       /* null pointer, bad shape, grid or parameter */
+    GRFT_ENOMEM = -2,       /* workspace allocation failed */
+    GRFT_ECUDA = -3,        /* CUDA runtime / launch error */
+    GRFT_ETIMEOUT = -4,     /* a bounded device-side wait ran out (kernel returned early) */
+    GRFT_EUNSUPPORTED = -5, /* device is not sm_103 / precision not available */
+    GRFT_EOVERFLOW = -6     /* detection candidate buffer overflowed; top-K is incomplete */
+};
+
+/* ---------------------------------------------------------------- parameter types */
+typedef struct { float re, im; } grft_c32;
+
+/* Uniform axis: value_i = start + i * step, i = 0..count-1 (FP64 as written). */
+typedef struct { double start, step; int32_t count, reserved; } grft_axis;
+
+/* Radar / CPI parameters (Sec. II-A): M pulses, N range bins of dr = c/(2 f_s) metres. */
+typedef struct {
+    int32_t M, N;
+    double fc_hz;   /* carrier frequency f_c */
+    double prf_hz;  /* pulse repetition frequency; t_m = m / prf */
+    double dr_m;    /* range bin */
+    double c_mps;   /* propagation speed (3e8) */
+} grft_radar;
+
+/* Single-scale grid (Sec. III-C, eq. delta-Beta-1): r0 bins [r0_begin, r0_begin+r0_count). */
+typedef struct { int32_t r0_begin, r0_count; grft_axis v, a; } grft_grid;
+
+/* Dual-scale grid (Sec. IV-B, eqs. Partition-Parameter, Space_c_c, Space_c_f).
+ * Coarse centres v_c(i) = vc.start + i vc.step, a_c(l) likewise; fine offsets
+ * dv_k = (k - Fv/2) vc.step / Fv, da_q = (q - Fa/2) ac.step / Fa (half-open cells).
+ * Coarse cell index c = i * ac.count + l; fine index f = k * Fa + q. */
+typedef struct { int32_t r0_begin, r0_count; grft_axis vc, ac; int32_t Fv, Fa; } grft_dsgrid;
+
+typedef enum {
+    GRFT_FP32 = 0,   /* FP32 SIMT contraction (FFMA) */
+    GRFT_BF16X3 = 1, /* tcgen05 tensor cores, hi/lo-split BF16 operands, 3 products, FP32 accumulate */
+    GRFT_FP16X3 = 2  /* tcgen05 tensor cores, hi/lo-split FP16 operands, 3 products, FP32 accumulate */
+} grft_precision;
+
+typedef enum { GRFT_GATHER_NEAREST = 0, GRFT_GATHER_LINEAR = 1 } grft_gather;
+
+/* Detector: mode 0 = CA-CFAR along r0 (guard/train cells each side, false-alarm rate pfa);
+ * mode 1 = fixed threshold P > fixed_thresh (eq. LRT squared).  Both add a 3x3x3 local
+ * maximum test over (v, a, r0). */
+typedef struct { int32_t guard, train; double pfa; float fixed_thresh; int32_t mode; } grft_cfar;
+
+/* One detection: linear index (vi*na + ai)*nr0 + n0, grid indices, power and the
+ * on-grid estimate (Alg. 3: c0 = r0, c1 = v, c2 = a). */
+typedef struct { int64_t idx; int32_t n0, vi, ai; float p; double r0_m, v, a; } grft_det;
+
+/* One CPI of a batched DS-GRFT launch. */
+typedef struct {
+    const grft_c32 *echo; /* [M][N] */
+    float *P;             /* [nv][na][r0_count] canonical layout, nullable if Y given */
+    grft_c32 *Y;          /* same layout, nullable */
+    int32_t M, N;
+    int32_t r0_begin, r0_count;
+} grft_batch_item;
+
+/* ---------------------------------------------------------------- library */
+int grft_version(void);
+const char *grft_status_string(int status);
+
+/* Synchronise `stream`, return (and clear) the device-side status latched by earlier
+ * calls on this device: GRFT_OK, GRFT_ETIMEOUT or GRFT_EOVERFLOW. */
+int grft_sync_status(void *stream);
+
+/* Bounded-wait limit of the warp-specialised kernels, in SM clock cycles (0 restores the
+ * default of about one second).  A wait that exceeds it makes the kernel latch
+ * GRFT_ETIMEOUT and return early with partial output. */
+int grft_set_wait_limit(uint64_t cycles);
+
+/* Free this device's cached workspace (the next call reallocates it). */
+int grft_release_workspace(void);
+
+/* ---------------------------------------------------------------- the hot path */
+
+/* Trajectory tables (eq. standard-GRFT-TD's n(c,t_m); eqs. H-DFM / pre-DFM phases).
+ * For nh explicit (v[h], a[h]) pairs (device FP64 arrays): rho[h][m] = floor(d/dr + 0.5)
+ * (int32, bit-exact to the FP64 definition) and w[h][m] = exp(j 4 pi d / lambda). */
+int grft_bins_phases(const grft_radar *radar, const double *v, const double *a, int32_t nh,
+                     int32_t *rho, grft_c32 *w, void *stream);
+
+/* Plain (single-scale) TD-GRFT over the whole grid (Sec. III-A eq. standard-GRFT-TD;
+ * Table III row TD-GRFT).  Y[v][a][r0_count] (complex, nullable) and/or
+ * P[v][a][r0_count] = |Y|^2 (nullable; at least one given).  FP32 SIMT. */
+int grft_plain(const grft_radar *radar, const grft_c32 *echo, const grft_grid *grid,
+               grft_c32 *Y, float *P, void *stream);
+
+/* Coarse range-migration correction, time-domain mGIFT (Def. 2 + eq. pre-DFM, Alg. 1):
+ *   Z[c - cell_begin][m][j] = s[m][r0_begin + j + rho_c(m)] * exp(j 4 pi d_c(t_m) / lambda)
+ * for coarse cells c in [cell_begin, cell_begin + cell_count), j in [0, r0_count).
+ * The echo rows are staged through shared memory by TMA. */
+int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                     int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream);
+
+/* Fine Doppler-migration correction, the GFT of Def. 1 / Alg. 2 as a dense contraction
+ * against the dechirp matrix D[m][f] = exp(j 4 pi (dv_k t_m + da_q t_m^2 / 2) / lambda):
+ *   Y(n0; c, f) = exp(j 4 pi n0 dr / lambda) * sum_m Zc[m][n0] D[m][f]          (Alg. 3)
+ * Z = NULL: Zc is gathered on the fly from `echo` (fused with dsgrft_coarse_rm);
+ * Z given: Z is the [cell_count][M][r0_count] output of dsgrft_coarse_rm for the same cells.
+ * Output layout (Y and P, either nullable, not both): a v-slab of the canonical DS layout,
+ *   [(i - i0) * Fv + k][l * Fa + q][n0 - r0_begin],  i0 = cell_begin / ac.count,
+ * covering coarse v rows i0 .. (cell_begin + cell_count - 1) / ac.count; cells outside the
+ * range are left untouched.  precision: GRFT_FP32 (SIMT) or a split tensor-core mode. */
+int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo,
+                    const grft_dsgrid *grid, int32_t cell_begin, int32_t cell_count,
+                    grft_precision precision, grft_c32 *Y, float *P, void *stream);
+
+/* Many CPIs (uneven M, N) in one persistent launch (graph-capturable after a first
+ * uncaptured call of the same shape).  radar's M and N are ignored (per item); grid's
+ * r0 fields are ignored (per item).  items is a HOST array of at most 256 entries; its
+ * pointers are device pointers.  Tensor-core precisions only. */
+int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
+                            const grft_batch_item *items, int32_t n_items,
+                            grft_precision precision, void *stream);
+
+/* CA-CFAR / fixed threshold + 3x3x3 local maximum + top-K (eq. LRT; Alg. 3's threshold
+ * scan) over P[nv][na][nr0].  Writes min(K, total) records to out[] sorted by power
+ * (descending, ties by lower index) and the total number of detections to *n_out (both
+ * device memory).  axes (host, nullable) maps indices to the estimate (r0_m =
+ * (axes->r0_begin + n0) * dr_m, v = v.start + vi v.step, a likewise); NULL leaves the
+ * estimate fields zero.  K <= 8192. */
+int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft_cfar *cfar,
+                 const grft_grid *axes, double dr_m, int32_t K, grft_det *out, int32_t *n_out,
+                 void *stream);
+
+/* Coherent sum along K continuous trajectories theta[k] = (r0_m, v, a) (device FP64
+ * [K][3]) and its adjoint (no counterpart in the paper; gather: nearest bin or linear
+ * interpolation between bins):
+ *   P[k] = |Y_k|^2, Y[k] (each nullable),
+ *   grad_theta[k][j] = gP[k] * dP_k/dtheta_j (nullable; gP = grad_P or ones),
+ *   grad_s[m][n] += sum_k gP[k] * 2 Y_k conj(dY_k/ds[m][n])  (nullable; the
+ *                   d/dRe + j d/dIm convention of torch.autograd; accumulated, unordered).
+ * Phases are recomputed from FP64 ranges, never stored. */
+int dsgrft_backward(const grft_radar *radar, const grft_c32 *echo, int32_t K, const double *theta,
+                    grft_gather gather, const float *grad_P, float *P, grft_c32 *Y,
+                    double *grad_theta, grft_c32 *grad_s, void *stream);
+
+/* Sub-grid gradient-ascent refinement of K detections, one launch: with cell = the host
+ * array (c_r0, c_v, c_a) of grid steps, g = dP/dtheta and eta = 0.5 / max_j |cell_j g_j|,
+ * repeat `steps` times: theta' = theta + eta cell^2 . g; accept if P(theta') >= P(theta),
+ * else halve eta.  theta (device [K][3]) is updated in place, P_out[k] gets the final power. */
+int dsgrft_refine(const grft_radar *radar, const grft_c32 *echo, int32_t K, double *theta,
+                  const double *cell, int32_t steps, grft_gather gather, float *P_out,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSGRFT_H_ */

@@ -1,0 +1,342 @@
+// C ABI of libdsgrft.so: argument checks, per-device state (status word, workspace) and
+// the sequencing of table builders and kernels on the caller's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+#include "tma.cuh"
+
+namespace grft {
+
+namespace {
+
+constexpr int MAX_DEV = 64;
+constexpr uint64_t DEFAULT_WAIT_LIMIT = 2000000000ull;   // ~1 s of SM cycles
+constexpr size_t PLAIN_TABLE_BUDGET = 256ull << 20;
+
+struct DevState {
+    bool init = false;
+    int *status = nullptr;
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    int num_sms = 0;
+    int cc = 0;
+};
+
+DevState g_dev[MAX_DEV];
+std::mutex g_mu;
+uint64_t g_wait_limit = DEFAULT_WAIT_LIMIT;
+
+int make_ctx(void *stream, Ctx &c) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return GRFT_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &d = g_dev[dev];
+    if (!d.init) {
+        int major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return GRFT_ECUDA;
+        d.cc = major * 10 + minor;
+        if (cudaMalloc(&d.status, 256) != cudaSuccess) return GRFT_ENOMEM;
+        if (cudaMemset(d.status, 0, 256) != cudaSuccess) return GRFT_ECUDA;
+        d.init = true;
+    }
+    if (d.cc != 103) return GRFT_EUNSUPPORTED;   // the library is built for sm_103a only
+    c.device = dev;
+    c.stream = (cudaStream_t)stream;
+    c.status = d.status;
+    c.wait_limit = g_wait_limit;
+    c.num_sms = d.num_sms;
+    return GRFT_OK;
+}
+
+bool radar_ok(const grft_radar *r) {
+    return r && r->M > 0 && r->N > 0 && std::isfinite(r->fc_hz) && r->fc_hz > 0 &&
+           std::isfinite(r->prf_hz) && r->prf_hz > 0 && std::isfinite(r->dr_m) && r->dr_m > 0 &&
+           std::isfinite(r->c_mps) && r->c_mps > 0;
+}
+
+bool axis_ok(const grft_axis &a) {
+    return a.count > 0 && std::isfinite(a.start) && std::isfinite(a.step);
+}
+
+bool dsgrid_ok(const grft_dsgrid *g, const grft_radar *r) {
+    return g && axis_ok(g->vc) && axis_ok(g->ac) && g->Fv > 0 && g->Fa > 0 && g->r0_count > 0 &&
+           g->r0_begin >= 0 && (long)g->r0_begin + g->r0_count <= (long)r->N &&
+           (long)g->vc.count * g->ac.count <= 0x7fffffffL && (long)g->Fv * g->Fa <= (1L << 20);
+}
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+void *workspace(const Ctx &ctx, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &d = g_dev[ctx.device];
+    if (bytes <= d.ws_size) return d.ws;
+    if (d.ws) {
+        cudaDeviceSynchronize();
+        cudaFree(d.ws);
+        d.ws = nullptr;
+        d.ws_size = 0;
+    }
+    size_t want = align_up(bytes, 64ull << 20);
+    if (cudaMalloc(&d.ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        d.ws = nullptr;
+        return nullptr;
+    }
+    d.ws_size = want;
+    return d.ws;
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRFT_OK : GRFT_ECUDA;
+}
+
+bool encode_tma_2d(CUtensorMap *map, CUtensorMapDataType dtype, void *base, uint64_t dim0,
+                   uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1,
+                   CUtensorMapSwizzle swizzle) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !ptr)
+            return false;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    cuuint64_t dims[2] = {dim0, dim1};
+    cuuint64_t strides[1] = {stride1_bytes};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, dtype, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace grft
+
+using namespace grft;
+
+extern "C" {
+
+int grft_version(void) { return GRFT_ABI_VERSION; }
+
+const char *grft_status_string(int s) {
+    switch (s) {
+        case GRFT_OK: return "ok";
+        case GRFT_EINVAL: return "invalid argument";
+        case GRFT_ENOMEM: return "out of device memory";
+        case GRFT_ECUDA: return "CUDA error";
+        case GRFT_ETIMEOUT: return "bounded device wait ran out";
+        case GRFT_EUNSUPPORTED: return "unsupported device or precision";
+        case GRFT_EOVERFLOW: return "detection candidate buffer overflow";
+        default: return "unknown status";
+    }
+}
+
+int grft_sync_status(void *stream) {
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return GRFT_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, c.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GRFT_ECUDA;
+    if (h != 0 && cudaMemset(c.status, 0, sizeof(int)) != cudaSuccess) return GRFT_ECUDA;
+    return h;
+}
+
+int grft_set_wait_limit(uint64_t cycles) {
+    g_wait_limit = cycles ? cycles : DEFAULT_WAIT_LIMIT;
+    return GRFT_OK;
+}
+
+int grft_release_workspace(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return GRFT_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &d = g_dev[dev];
+    if (d.ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return GRFT_ECUDA;
+        cudaFree(d.ws);
+    }
+    d.ws = nullptr;
+    d.ws_size = 0;
+    return GRFT_OK;
+}
+
+int grft_bins_phases(const grft_radar *radar, const double *v, const double *a, int32_t nh,
+                     int32_t *rho, grft_c32 *w, void *stream) {
+    if (!radar_ok(radar) || nh < 0 || (nh > 0 && (!v || !a || !rho || !w))) return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_bins_phases(c, radar_d(*radar), v, a, nh, rho, w);
+}
+
+int grft_plain(const grft_radar *radar, const grft_c32 *echo, const grft_grid *grid, grft_c32 *Y,
+               float *P, void *stream) {
+    if (!radar_ok(radar) || !echo || !grid || (!Y && !P) || !axis_ok(grid->v) || !axis_ok(grid->a) ||
+        grid->r0_count <= 0 || grid->r0_begin < 0 || (long)grid->r0_begin + grid->r0_count > radar->N)
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(*radar);
+    const long nh_total = (long)grid->v.count * grid->a.count;
+    long chunk = (long)(PLAIN_TABLE_BUDGET / ((size_t)R.M * (sizeof(int32_t) + sizeof(float2))));
+    chunk = chunk / 8 * 8;
+    if (chunk < 8) chunk = 8;
+    if (chunk > (1L << 18)) chunk = 1L << 18;
+    if (chunk > nh_total) chunk = nh_total;
+    const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
+    const size_t rho_bytes = align_up((size_t)chunk * R.M * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)chunk * R.M * sizeof(float2));
+    unsigned char *ws = (unsigned char *)workspace(c, e0_bytes + rho_bytes + w_bytes);
+    if (!ws) return GRFT_ENOMEM;
+    float2 *e0 = (float2 *)ws;
+    int32_t *rho = (int32_t *)(ws + e0_bytes);
+    float2 *w = (float2 *)(ws + e0_bytes + rho_bytes);
+    if ((e = launch_range_phase(c, R, grid->r0_begin, grid->r0_count, e0))) return e;
+    for (long h0 = 0; h0 < nh_total; h0 += chunk) {
+        const int nh = (int)(nh_total - h0 < chunk ? nh_total - h0 : chunk);
+        if ((e = launch_plain_tables(c, R, *grid, h0, nh, rho, w))) return e;
+        if ((e = launch_plain(c, R, (const float2 *)echo, *grid, h0, nh, rho, w, e0, (float2 *)Y, P)))
+            return e;
+    }
+    return GRFT_OK;
+}
+
+int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                     int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream) {
+    if (!radar_ok(radar) || !echo || !Z || !dsgrid_ok(grid, radar) || cell_begin < 0 ||
+        cell_count < 0 || (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count ||
+        cell_count > 65535)
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(*radar);
+    const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)cell_count * R.M * sizeof(float2));
+    unsigned char *ws = (unsigned char *)workspace(c, rho_bytes + w_bytes);
+    if (!ws) return GRFT_ENOMEM;
+    int32_t *rho = (int32_t *)ws;
+    float2 *w = (float2 *)(ws + rho_bytes);
+    if ((e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
+    return launch_coarse_rm(c, R, (const float2 *)echo, *grid, cell_count, rho, w, (float2 *)Z);
+}
+
+int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo,
+                    const grft_dsgrid *grid, int32_t cell_begin, int32_t cell_count,
+                    grft_precision precision, grft_c32 *Y, float *P, void *stream) {
+    if (!radar_ok(radar) || (!Z && !echo) || (!Y && !P) || !dsgrid_ok(grid, radar) ||
+        cell_begin < 0 || cell_count < 0 ||
+        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count || cell_count > 65535)
+        return GRFT_EINVAL;
+    if (precision != GRFT_FP32 && precision != GRFT_BF16X3 && precision != GRFT_FP16X3)
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(*radar);
+    const int F = grid->Fv * grid->Fa;
+    const int Fpad = (F + 127) / 128 * 128;
+    const int Mpad = (R.M + 31) / 32 * 32;
+    const bool tc = precision != GRFT_FP32;
+    const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)cell_count * R.M * sizeof(float2));
+    const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
+    const size_t d_bytes = tc ? align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t))
+                              : align_up((size_t)R.M * F * sizeof(float2));
+    unsigned char *ws =
+        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes : d_bytes));
+    if (!ws) return GRFT_ENOMEM;
+    int32_t *rho = (int32_t *)ws;
+    float2 *w = (float2 *)(ws + rho_bytes);
+    float2 *e0 = (float2 *)(ws + rho_bytes + w_bytes);
+    unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
+    if (!Z && (e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
+    if ((e = launch_range_phase(c, R, grid->r0_begin, grid->r0_count, e0))) return e;
+    DsOut out;
+    out.Y = (float2 *)Y;
+    out.P = P;
+    out.cell_begin = cell_begin;
+    out.i0 = cell_begin / grid->ac.count;
+    out.na_c = grid->ac.count;
+    out.Fv = grid->Fv;
+    out.Fa = grid->Fa;
+    if (!tc) {
+        float2 *D = (float2 *)dptr;
+        if ((e = launch_dechirp(c, R, *grid, D))) return e;
+        return launch_ds_simt(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w,
+                              D, e0, out);
+    }
+    uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
+    const bool fp16 = precision == GRFT_FP16X3;
+    if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
+    return launch_ds_tc(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w, Bhi,
+                        Blo, Mpad, fp16, e0, out);
+}
+
+int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
+                            const grft_batch_item *items, int32_t n_items, grft_precision precision,
+                            void *stream) {
+    (void)radar;
+    (void)grid;
+    (void)items;
+    (void)n_items;
+    (void)precision;
+    (void)stream;
+    return GRFT_EUNSUPPORTED;
+}
+
+int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft_cfar *cfar,
+                 const grft_grid *axes, double dr_m, int32_t K, grft_det *out, int32_t *n_out,
+                 void *stream) {
+    if (!P || !cfar || !n_out || nv <= 0 || na <= 0 || nr0 <= 0 || K < 0 || (K > 0 && !out))
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_detect(c, P, nv, na, nr0, *cfar, axes, dr_m, K, out, n_out);
+}
+
+int dsgrft_backward(const grft_radar *radar, const grft_c32 *echo, int32_t K, const double *theta,
+                    grft_gather gather, const float *grad_P, float *P, grft_c32 *Y,
+                    double *grad_theta, grft_c32 *grad_s, void *stream) {
+    if (!radar_ok(radar) || !echo || K < 0 || (K > 0 && !theta) ||
+        (gather != GRFT_GATHER_NEAREST && gather != GRFT_GATHER_LINEAR))
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_backward(c, radar_d(*radar), (const float2 *)echo, K, theta, (int)gather, grad_P, P,
+                           (float2 *)Y, grad_theta, (float2 *)grad_s);
+}
+
+int dsgrft_refine(const grft_radar *radar, const grft_c32 *echo, int32_t K, double *theta,
+                  const double *cell, int32_t steps, grft_gather gather, float *P_out,
+                  void *stream) {
+    if (!radar_ok(radar) || !echo || K < 0 || (K > 0 && (!theta || !P_out)) || !cell || steps < 0 ||
+        (gather != GRFT_GATHER_NEAREST && gather != GRFT_GATHER_LINEAR))
+        return GRFT_EINVAL;
+    for (int j = 0; j < 3; ++j)
+        if (!std::isfinite(cell[j]) || cell[j] <= 0) return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_refine(c, radar_d(*radar), (const float2 *)echo, K, theta, cell, steps, (int)gather,
+                         P_out);
+}
+
+}  // extern "C"

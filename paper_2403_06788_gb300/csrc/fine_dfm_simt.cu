@@ -1,0 +1,124 @@
+// Fine Doppler-migration correction in FP32 SIMT (the correctness twin of the tensor-core
+// path): per coarse cell a complex contraction over pulses (GFT of Def. 1 / Alg. 2 as a
+// dense product with the dechirp matrix, Alg. 3):
+//   Y(n0; c, f) = e0(n0) * sum_m Zc[m][n0] * D[m][f],  Zc[m][n0] = s[m][n0 + rho_c(m)] w_c(m)
+// Zc is gathered on the fly from the echo (or read from a materialised Z).
+// CTA tile: 128 bins x 64 fine hypotheses, 256 threads, thread tile 8 bins x 4 hypotheses,
+// pulses staged 16 at a time in shared memory ([m][n0] and [m][f], both contiguous in the
+// thread's direction).
+#include "internal.cuh"
+
+namespace grft {
+
+namespace {
+
+constexpr int SM_BN = 128;   // bins per CTA
+constexpr int SM_BF = 64;    // fine hypotheses per CTA
+constexpr int SM_BK = 16;    // pulses per stage
+constexpr int SM_TN = 8;
+constexpr int SM_TF = 4;
+
+__global__ __launch_bounds__(256) void k_ds_simt(
+    const float2 *__restrict__ echo, const float2 *__restrict__ Z, int M, int N,
+    const int32_t *__restrict__ rho_c, const float2 *__restrict__ w_c,
+    const float2 *__restrict__ D, const float2 *__restrict__ e0, int r0_begin, int r0_count,
+    int F, DsOut out) {
+    __shared__ alignas(16) float2 sA[SM_BK][SM_BN];
+    __shared__ alignas(16) float2 sB[SM_BK][SM_BF];
+
+    const int cl = blockIdx.z;
+    const int jt = blockIdx.x * SM_BN;
+    const int ft = blockIdx.y * SM_BF;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+
+    float2 acc[SM_TN][SM_TF];
+#pragma unroll
+    for (int a = 0; a < SM_TN; ++a)
+#pragma unroll
+        for (int b = 0; b < SM_TF; ++b) acc[a][b] = make_float2(0.f, 0.f);
+
+    for (int m0 = 0; m0 < M; m0 += SM_BK) {
+        for (int i = threadIdx.x; i < SM_BK * SM_BN; i += 256) {
+            const int mm = i / SM_BN, jn = i % SM_BN;
+            const int m = m0 + mm, j = jt + jn;
+            float2 v = make_float2(0.f, 0.f);
+            if (m < M && j < r0_count) {
+                const long o = (long)cl * M + m;
+                if (Z) {
+                    v = Z[o * r0_count + j];
+                } else {
+                    const int n = r0_begin + j + rho_c[o];
+                    if ((unsigned)n < (unsigned)N) v = cmul(__ldg(echo + (long)m * N + n), w_c[o]);
+                }
+            }
+            sA[mm][jn] = v;
+        }
+        for (int i = threadIdx.x; i < SM_BK * SM_BF; i += 256) {
+            const int mm = i / SM_BF, fn = i % SM_BF;
+            const int m = m0 + mm, f = ft + fn;
+            sB[mm][fn] = (m < M && f < F) ? D[(long)m * F + f] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int mm = 0; mm < SM_BK; ++mm) {
+            float2 a[SM_TN], b[SM_TF];
+            const float4 *pa = reinterpret_cast<const float4 *>(&sA[mm][tx * SM_TN]);
+#pragma unroll
+            for (int q = 0; q < SM_TN / 2; ++q) {
+                float4 t = pa[q];
+                a[2 * q] = make_float2(t.x, t.y);
+                a[2 * q + 1] = make_float2(t.z, t.w);
+            }
+            const float4 *pb = reinterpret_cast<const float4 *>(&sB[mm][ty * SM_TF]);
+#pragma unroll
+            for (int q = 0; q < SM_TF / 2; ++q) {
+                float4 t = pb[q];
+                b[2 * q] = make_float2(t.x, t.y);
+                b[2 * q + 1] = make_float2(t.z, t.w);
+            }
+#pragma unroll
+            for (int x = 0; x < SM_TN; ++x)
+#pragma unroll
+                for (int y = 0; y < SM_TF; ++y) {
+                    acc[x][y].x = fmaf(a[x].x, b[y].x, fmaf(-a[x].y, b[y].y, acc[x][y].x));
+                    acc[x][y].y = fmaf(a[x].x, b[y].y, fmaf(a[x].y, b[y].x, acc[x][y].y));
+                }
+        }
+        __syncthreads();
+    }
+
+    // epilogue: canonical v-slab layout
+    const int c = out.cell_begin + cl;
+    const int iv = c / out.na_c - out.i0, il = c % out.na_c;
+    const int na_full = out.na_c * out.Fa;
+#pragma unroll
+    for (int y = 0; y < SM_TF; ++y) {
+        const int f = ft + ty * SM_TF + y;
+        if (f >= F) break;
+        const int k = f / out.Fa, q = f % out.Fa;
+        const long rowo = ((long)(iv * out.Fv + k) * na_full + (il * out.Fa + q)) * r0_count;
+#pragma unroll
+        for (int x = 0; x < SM_TN; ++x) {
+            const int j = jt + tx * SM_TN + x;
+            if (j >= r0_count) break;
+            const float2 v = acc[x][y];
+            if (out.Y) out.Y[rowo + j] = cmul(e0[j], v);
+            if (out.P) out.P[rowo + j] = v.x * v.x + v.y * v.y;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_ds_simt(const Ctx &c, const RadarD &R, const float2 *echo, const float2 *Z,
+                   const grft_dsgrid &g, int cell_count, const int32_t *rho, const float2 *w,
+                   const float2 *D, const float2 *e0, const DsOut &out) {
+    if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
+    const int F = g.Fv * g.Fa;
+    dim3 grid((g.r0_count + SM_BN - 1) / SM_BN, (F + SM_BF - 1) / SM_BF, cell_count);
+    k_ds_simt<<<grid, 256, 0, c.stream>>>(echo, Z, R.M, R.N, rho, w, D, e0, g.r0_begin, g.r0_count,
+                                          F, out);
+    return check_launch();
+}
+
+}  // namespace grft

@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of libdsgrft.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dsgrft.h"
+
+namespace grft {
+
+// --------------------------------------------------------------------------- device math
+// Bin and phase of a displacement, written with explicit round-to-nearest FP64
+// intrinsics so that no operation is contracted into an FMA: the bins are bit-identical
+// to the IEEE definition d = (v*t) + ((0.5*a)*(t*t)), rho = floor(d/dr + 0.5).
+__device__ __forceinline__ double slow_time(int m, double prf) { return __ddiv_rn((double)m, prf); }
+
+__device__ __forceinline__ double displacement(double v, double a, double t) {
+    double vt = __dmul_rn(v, t);
+    double ha = __dmul_rn(0.5, a);
+    double tt = __dmul_rn(t, t);
+    return __dadd_rn(vt, __dmul_rn(ha, tt));
+}
+
+__device__ __forceinline__ int bin_shift(double d, double dr) {
+    return (int)floor(__dadd_rn(__ddiv_rn(d, dr), 0.5));
+}
+
+// exp(+j 4 pi x / lambda): FP64 cycle count 2x/lambda, reduced to [-1/2, 1/2] in FP64,
+// then an FP32 sincospi of the reduced angle.
+__device__ __forceinline__ float2 range_phase(double x, double lambda) {
+    double u = __ddiv_rn(__dmul_rn(2.0, x), lambda);
+    double f = __dsub_rn(u, rint(u));
+    float s, c;
+    sincospif(2.0f * (float)f, &s, &c);
+    return make_float2(c, s);
+}
+
+// Axis value start + i*step and the dual-scale fine offset (k - F/2) * (step_c / F).
+__device__ __forceinline__ double axis_value(double start, double step, int i) {
+    return __dadd_rn(start, __dmul_rn((double)i, step));
+}
+__device__ __forceinline__ double fine_offset(double step_c, int F, int k) {
+    double off = __dmul_rn((double)(2 * k - F), 0.5);
+    return __dmul_rn(off, __ddiv_rn(step_c, (double)F));
+}
+
+__device__ __forceinline__ float2 cmul(float2 x, float2 y) {
+    return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+}
+
+// Latch the first device-side error of this device (0 = no error).
+__device__ __forceinline__ void latch_error(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// --------------------------------------------------------------------------- host side
+struct RadarD {     // radar constants as the kernels use them
+    int M, N;
+    double prf, dr, lambda;
+};
+
+inline RadarD radar_d(const grft_radar &r) {
+    RadarD d;
+    d.M = r.M;
+    d.N = r.N;
+    d.prf = r.prf_hz;
+    d.dr = r.dr_m;
+    d.lambda = r.c_mps / r.fc_hz;
+    return d;
+}
+
+struct Ctx {                  // per-call device context
+    int device;
+    cudaStream_t stream;
+    int *status;              // device status word (latched errors)
+    uint64_t wait_limit;      // bounded-wait limit in SM cycles
+    int num_sms;
+};
+
+// Workspace of this device, grown to at least `bytes` (synchronises the device when it
+// grows).  Returns nullptr on allocation failure.
+void *workspace(const Ctx &ctx, size_t bytes);
+
+// Launchers (each returns a grft status; they only enqueue work).
+int launch_bins_phases(const Ctx &, const RadarD &, const double *v, const double *a, int nh,
+                       int32_t *rho, grft_c32 *w);
+int launch_plain_tables(const Ctx &, const RadarD &, const grft_grid &, long h0, int nh,
+                        int32_t *rho, float2 *w);
+int launch_coarse_tables(const Ctx &, const RadarD &, const grft_dsgrid &, int cell_begin,
+                         int cell_count, int32_t *rho, float2 *w);
+int launch_range_phase(const Ctx &, const RadarD &, int r0_begin, int r0_count, float2 *e0);
+int launch_dechirp(const Ctx &, const RadarD &, const grft_dsgrid &, float2 *D);
+// Dechirp matrix in the K-major real-GEMM operand layout of the tensor-core kernel.
+int launch_dechirp_split(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Fpad,
+                         bool fp16, uint16_t *Bhi, uint16_t *Blo);
+
+int launch_plain(const Ctx &, const RadarD &, const float2 *echo, const grft_grid &, long h0,
+                 int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,
+                 float *P);
+
+int launch_coarse_rm(const Ctx &, const RadarD &, const float2 *echo, const grft_dsgrid &,
+                     int cell_count, const int32_t *rho, const float2 *w, float2 *Z);
+
+struct DsOut {           // output placement of a DS call (v-slab of the canonical layout)
+    float2 *Y;
+    float *P;
+    int cell_begin;      // first coarse cell of the call
+    int i0;              // first coarse v row of the slab
+    int na_c;            // coarse a count
+    int Fv, Fa;
+};
+
+int launch_ds_simt(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
+                   const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
+                   const float2 *D, const float2 *e0, const DsOut &out);
+
+int launch_ds_tc(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
+                 const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
+                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, bool fp16,
+                 const float2 *e0, const DsOut &out);
+
+int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
+                  const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);
+
+int launch_backward(const Ctx &, const RadarD &, const float2 *echo, int K, const double *theta,
+                    int gather, const float *gP, float *P, float2 *Y, double *g, float2 *gs);
+
+int launch_refine(const Ctx &, const RadarD &, const float2 *echo, int K, double *theta,
+                  const double cell[3], int steps, int gather, float *P);
+
+int check_launch();   // GRFT_OK or GRFT_ECUDA from cudaGetLastError
+
+}  // namespace grft

@@ -1,0 +1,162 @@
+// Trajectory tables (FP64 argument, FP32/int32 output): bins and phases of the matched
+// filter (eq. standard-GRFT-TD's n(c, t_m); eqs. H-DFM and pre-DFM), the range phase of
+// r0, and the dechirp matrix of the fine stage (Def. 1 / Alg. 2).  O(#hypotheses x M)
+// work, never per r0: FP64 is scarce on GB300 and stays out of every inner loop.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+
+namespace grft {
+
+namespace {
+
+__global__ void k_bins_phases(RadarD R, const double *__restrict__ v, const double *__restrict__ a,
+                              int nh, int32_t *__restrict__ rho, float2 *__restrict__ w) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)nh * R.M) return;
+    int h = (int)(i / R.M), m = (int)(i % R.M);
+    double t = slow_time(m, R.prf);
+    double d = displacement(v[h], a[h], t);
+    rho[i] = bin_shift(d, R.dr);
+    w[i] = range_phase(d, R.lambda);
+}
+
+// Plain grid: hypothesis h = vi * na + ai (global index h0 + local).
+__global__ void k_plain_tables(RadarD R, double v0, double dv, double a0, double da, int na,
+                               long h0, int nh, int32_t *__restrict__ rho, float2 *__restrict__ w) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)nh * R.M) return;
+    long h = h0 + i / R.M;
+    int m = (int)(i % R.M);
+    double v = axis_value(v0, dv, (int)(h / na));
+    double a = axis_value(a0, da, (int)(h % na));
+    double t = slow_time(m, R.prf);
+    double d = displacement(v, a, t);
+    rho[i] = bin_shift(d, R.dr);
+    w[i] = range_phase(d, R.lambda);
+}
+
+// Coarse cells c = i * na_c + l: bins of the coarse trajectory and H_pre-DFM.
+__global__ void k_coarse_tables(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
+                                int32_t *__restrict__ rho, float2 *__restrict__ w) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)cell_count * R.M) return;
+    int c = cell_begin + (int)(idx / R.M), m = (int)(idx % R.M);
+    double vc = axis_value(g.vc.start, g.vc.step, c / g.ac.count);
+    double ac = axis_value(g.ac.start, g.ac.step, c % g.ac.count);
+    double t = slow_time(m, R.prf);
+    double d = displacement(vc, ac, t);
+    rho[idx] = bin_shift(d, R.dr);
+    w[idx] = range_phase(d, R.lambda);
+}
+
+__global__ void k_range_phase(RadarD R, int r0_begin, int r0_count, float2 *__restrict__ e0) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= r0_count) return;
+    e0[j] = range_phase(__dmul_rn((double)(r0_begin + j), R.dr), R.lambda);
+}
+
+__device__ __forceinline__ float2 dechirp_value(const RadarD &R, const grft_dsgrid &g, int m, int f) {
+    int k = f / g.Fa, q = f % g.Fa;
+    double dv = fine_offset(g.vc.step, g.Fv, k);
+    double da = fine_offset(g.ac.step, g.Fa, q);
+    double t = slow_time(m, R.prf);
+    return range_phase(displacement(dv, da, t), R.lambda);
+}
+
+// D[m][f], f = k * Fa + q (H_DFM of the fine offsets, Def. 1).
+__global__ void k_dechirp(RadarD R, grft_dsgrid g, float2 *__restrict__ D) {
+    int F = g.Fv * g.Fa;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)R.M * F) return;
+    int m = (int)(i / F), f = (int)(i % F);
+    D[i] = dechirp_value(R, g, m, f);
+}
+
+__device__ __forceinline__ uint16_t to_bits(float x, bool fp16) {
+    if (fp16) return __half_as_ushort(__float2half_rn(x));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float from_bits(uint16_t b, bool fp16) {
+    if (fp16) return __half2float(__ushort_as_half(b));
+    return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// Real-GEMM operand B' of the 4M complex product, K-major, rows n' = 2 f + ri (ri = 0
+// real output, 1 imaginary output), columns k' = (m / 32) * 64 + kri * 32 + m % 32
+// (kri = 0 multiplies Re Z, 1 multiplies Im Z):
+//   (ri, kri) = (0,0): Re D   (0,1): -Im D   (1,0): Im D   (1,1): Re D
+// split as hi = round(x), lo = round(x - hi) in BF16 or FP16.  Pulses m >= M and fine
+// hypotheses f >= F (padding up to Fpad) are zero.
+__global__ void k_dechirp_split(RadarD R, grft_dsgrid g, int Mpad, int Fpad, int fp16,
+                                uint16_t *__restrict__ Bhi, uint16_t *__restrict__ Blo) {
+    int F = g.Fv * g.Fa;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;     // over Fpad * Mpad
+    if (i >= (long)Fpad * Mpad) return;
+    int f = (int)(i / Mpad), m = (int)(i % Mpad);
+    float2 d = (m < R.M && f < F) ? dechirp_value(R, g, m, f) : make_float2(0.f, 0.f);
+    float vals[2][2] = {{d.x, -d.y}, {d.y, d.x}};
+    long kk = (long)(m / 32) * 64 + (m % 32);
+    for (int ri = 0; ri < 2; ++ri) {
+        long row = (long)(2 * f + ri) * (2L * Mpad);
+        for (int kri = 0; kri < 2; ++kri) {
+            float x = vals[ri][kri];
+            uint16_t hb = to_bits(x, fp16 != 0);
+            float hi = from_bits(hb, fp16 != 0);
+            uint16_t lb = to_bits(x - hi, fp16 != 0);
+            Bhi[row + kk + kri * 32] = hb;
+            Blo[row + kk + kri * 32] = lb;
+        }
+    }
+}
+
+inline unsigned blocks_for(long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int launch_bins_phases(const Ctx &c, const RadarD &R, const double *v, const double *a, int nh,
+                       int32_t *rho, grft_c32 *w) {
+    long n = (long)nh * R.M;
+    if (n == 0) return GRFT_OK;
+    k_bins_phases<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, v, a, nh, rho, (float2 *)w);
+    return check_launch();
+}
+
+int launch_plain_tables(const Ctx &c, const RadarD &R, const grft_grid &g, long h0, int nh,
+                        int32_t *rho, float2 *w) {
+    long n = (long)nh * R.M;
+    if (n == 0) return GRFT_OK;
+    k_plain_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g.v.start, g.v.step, g.a.start,
+                                                              g.a.step, g.a.count, h0, nh, rho, w);
+    return check_launch();
+}
+
+int launch_coarse_tables(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_begin,
+                         int cell_count, int32_t *rho, float2 *w) {
+    long n = (long)cell_count * R.M;
+    if (n == 0) return GRFT_OK;
+    k_coarse_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, cell_begin, cell_count, rho, w);
+    return check_launch();
+}
+
+int launch_range_phase(const Ctx &c, const RadarD &R, int r0_begin, int r0_count, float2 *e0) {
+    if (r0_count == 0) return GRFT_OK;
+    k_range_phase<<<blocks_for(r0_count, 256), 256, 0, c.stream>>>(R, r0_begin, r0_count, e0);
+    return check_launch();
+}
+
+int launch_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, float2 *D) {
+    long n = (long)R.M * g.Fv * g.Fa;
+    k_dechirp<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, D);
+    return check_launch();
+}
+
+int launch_dechirp_split(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int Mpad, int Fpad,
+                         bool fp16, uint16_t *Bhi, uint16_t *Blo) {
+    long n = (long)Fpad * Mpad;
+    k_dechirp_split<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, Mpad, Fpad, fp16 ? 1 : 0, Bhi, Blo);
+    return check_launch();
+}
+
+}  // namespace grft
