@@ -150,7 +150,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--topk", type=int, default=1000)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline and accuracy check")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="restrict to the first N coarse cells (small profiling case; not a bench line)")
+    ap.add_argument("--e2e-steps", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -178,15 +181,15 @@ def main():
     s = synth.make_echo(R, sc.targets, sc.seed)
     echo_host = torch.from_numpy(s).pin_memory()
     echo = echo_host.to(dev)
-    nv, na = ds.vc.count * ds.Fv, ds.ac.count * ds.Fa
+    ncell = ds.n_cells if args.cells <= 0 else min(args.cells, ds.n_cells)
+    units = ds.r0_count * ncell * ds.n_fine * R.M
+    nv, na = -(-ncell // ds.ac.count) * ds.Fv, ds.ac.count * ds.Fa    # v-slab holding the cells
     P = torch.empty((nv, na, ds.r0_count), dtype=torch.float32, device=dev)
     det_out = torch.zeros(args.topk * g._abi.DET_BYTES, dtype=torch.uint8, device=dev)
     n_out = torch.zeros(1, dtype=torch.int32, device=dev)
     cfar = synth.CFAR(2, 16, 1e-6)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
     stream = torch.cuda.current_stream()
-    ncell = ds.n_cells
-    units = ds.n_hyp * R.M
 
     def step():
         g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, args.precision, None, P)
@@ -231,7 +234,7 @@ def main():
     # ---------------------------------------------------------------- end to end (host buffers)
     det_host = torch.empty_like(det_out, device="cpu").pin_memory()
     n_host = torch.empty(1, dtype=torch.int32).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else max(3, args.steps // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
@@ -302,7 +305,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "hypotheses": ds.n_hyp, "pulses": R.M, "precision": args.precision,
+        "config": {"workload": WORKLOAD if ncell == ds.n_cells else f"{WORKLOAD}, first {ncell} coarse cells",
+                   "hypotheses": units // R.M, "pulses": R.M, "precision": args.precision,
                    "topk": args.topk, "cfar": "CA 2 guard / 16 train, pfa 1e-6",
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"{world} independent CPI(s), one per GPU"},

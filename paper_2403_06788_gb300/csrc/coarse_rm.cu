@@ -22,13 +22,15 @@ constexpr int CR_ROWS = 8;       // pulses per CTA
 constexpr int CR_SEG = 128;      // bins per TMA box (plus 2)
 constexpr int CR_NSEG = 4;       // segments per CTA -> 512 bins
 constexpr int CR_BOX = CR_SEG + 2;
+constexpr int CR_PITCH = 144;    // box padded to 1152 B: every TMA destination 128-byte aligned
 constexpr int CR_COLS = CR_SEG * CR_NSEG;
+static_assert((CR_PITCH * 8) % 128 == 0 && CR_PITCH >= CR_BOX, "TMA smem destinations need 128 B alignment");
 
 __global__ __launch_bounds__(CR_THREADS) void k_coarse_rm_tma(
     const __grid_constant__ CUtensorMap tmap, int M, int N, const int32_t *__restrict__ rho_c,
     const float2 *__restrict__ w_c, int r0_begin, int r0_count, float2 *__restrict__ Z,
     int *status, uint64_t wait_limit) {
-    __shared__ alignas(128) float2 buf[CR_ROWS][CR_NSEG][CR_BOX];
+    __shared__ alignas(128) float2 buf[CR_ROWS][CR_NSEG][CR_PITCH];
     __shared__ alignas(8) uint64_t bar;
     __shared__ int s_off[CR_ROWS];
     __shared__ float2 s_w[CR_ROWS];

@@ -43,34 +43,59 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
                                                      int nseg, int *__restrict__ count,
                                                      float *__restrict__ cand_p,
                                                      int64_t *__restrict__ cand_i, int *status) {
-    __shared__ float sv[CF_SEG + 2 * CF_MAXHALO];
+    // shared-memory index of bin n is n - seg0 + CF_MAXHALO (a multiple of 4, so the
+    // thread's 8 bins land 16-byte aligned)
+    __shared__ alignas(16) float sv[CF_SEG + 2 * CF_MAXHALO];
     const long row = blockIdx.x / nseg;
     const int seg0 = (int)(blockIdx.x % nseg) * CF_SEG;
     const int G = cp.guard, T = cp.train, nr0 = cp.nr0;
     const int halo = G + T + 1;
     const float *prow = P + row * nr0;
-    for (int i = threadIdx.x; i < CF_SEG + 2 * halo; i += CF_THREADS) {
-        const int n = seg0 - halo + i;
-        sv[i] = (n >= 0 && n < nr0) ? __ldg(prow + n) : 0.f;
+    const int nb = seg0 + threadIdx.x * CF_PER;     // first bin of this thread
+    // every load of the segment is issued before any is used (one memory latency per CTA)
+    float x[CF_PER];
+    const bool vec = ((((uintptr_t)(prow + nb)) & 15) == 0) && nb + CF_PER <= nr0;
+    if (vec) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(prow + nb));
+        const float4 b = __ldcs(reinterpret_cast<const float4 *>(prow + nb) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < CF_PER; ++q) x[q] = (nb + q < nr0) ? __ldcs(prow + nb + q) : 0.f;
+    }
+    float hl = 0.f, hr = 0.f;                      // halo bins left of / right of the segment
+    if (threadIdx.x < halo) {
+        const int nl = seg0 - halo + threadIdx.x, nrr = seg0 + CF_SEG + threadIdx.x;
+        hl = (nl >= 0 && nl < nr0) ? __ldg(prow + nl) : 0.f;
+        hr = (nrr < nr0) ? __ldg(prow + nrr) : 0.f;
+    }
+    {
+        float4 *dst = reinterpret_cast<float4 *>(&sv[CF_MAXHALO + threadIdx.x * CF_PER]);
+        dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+        dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
+    if (threadIdx.x < halo) {
+        sv[CF_MAXHALO - halo + threadIdx.x] = hl;
+        sv[CF_MAXHALO + CF_SEG + threadIdx.x] = hr;
     }
     __syncthreads();
-
+    const int sb = CF_MAXHALO - seg0;               // sv[n + sb] holds bin n
     const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
-    const int nb = seg0 + threadIdx.x * CF_PER;     // first bin of this thread
     float L = 0.f, Rr = 0.f;
-    // initial windows for bin nb (shared-memory index of bin n is n - seg0 + halo)
+    // initial windows for bin nb
     if (cp.mode == 0) {
-        for (int j = nb - G - T; j <= nb - G - 1; ++j) L += sv[j - seg0 + halo];
-        for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += sv[j - seg0 + halo];
+        for (int j = nb - G - T; j <= nb - G - 1; ++j) L += sv[j + sb];
+        for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += sv[j + sb];
     }
     for (int q = 0; q < CF_PER; ++q) {
         const int n = nb + q;
         const bool valid = n < nr0;      // no early exit: every lane reaches the ballot below
         if (q > 0 && cp.mode == 0) {
-            L += sv[n - G - 1 - seg0 + halo] - sv[n - G - T - 1 - seg0 + halo];
-            Rr += sv[n + G + T - seg0 + halo] - sv[n + G - seg0 + halo];
+            L += sv[n - G - 1 + sb] - sv[n - G - T - 1 + sb];
+            Rr += sv[n + G + T + sb] - sv[n + G + sb];
         }
-        const float p = sv[n - seg0 + halo];
+        const float p = sv[n + sb];
         bool pass = false;
         if (!valid) {
         } else if (cp.mode == 0) {
@@ -88,7 +113,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
                         const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
                         if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
                         const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
-                        const float po = (dv == 0 && da == 0) ? sv[n2 - seg0 + halo] : __ldg(P + o);
+                        const float po = (dv == 0 && da == 0) ? sv[n2 + sb] : __ldg(P + o);
                         if (po > p || (po == p && o < me)) pass = false;
                     }
         }

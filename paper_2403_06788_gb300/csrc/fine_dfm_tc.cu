@@ -41,6 +41,9 @@ constexpr uint32_t TC_B_BYTES = TC_BN * 128;   // 32 KB
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unwind path
+constexpr int TC_TAB_MAX = 2048;                     // pulses whose bins/phases fit in shared memory
+constexpr uint32_t TC_TAB_BYTES = TC_TAB_MAX * (4 + 8);
+constexpr size_t TC_SMEM_BYTES = (size_t)TC_STAGES * TC_STAGE_BYTES + TC_TAB_BYTES + 1024;
 
 struct TcParams {
     const float2 *echo;
@@ -129,6 +132,11 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+// Named barrier among `count` threads (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // A wait done by lane 0 of a warp, combined with the CTA abort flag and broadcast, so that
 // the whole warp takes the same decision (keeps .sync.aligned operations converged).
 // Returns false if the wait ran out or the CTA is unwinding; lane 0 then latches the error.
@@ -154,6 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
+    __shared__ long s_rowoff[128];
 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ------------------------------------------------------------ TMA producer (B)
         if (lane == 0) {
             int it = 0;
-            int issued[TC_STAGES] = {0, 0};
+            int last_it = -1;            // last issued stage use (its stage is last_it % TC_STAGES)
             for (int tile = blockIdx.x; tile < p.total_tiles && !abort_flag; tile += gridDim.x) {
                 const int nt = tile % p.tiles_n;
                 for (int kt = 0; kt < p.KT; ++kt, ++it) {
@@ -207,12 +216,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * TC_BK, nt * TC_BN, &full_b[s]);
                     tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &mapBlo, kt * TC_BK, nt * TC_BN,
                                 &full_b[s]);
-                    issued[s] = it + 1;
+                    last_it = it;
                 }
             }
-            // drain: every issued load has landed before shared memory can be released
-            for (int s = 0; s < TC_STAGES; ++s)
-                if (issued[s] > 0) mbar_wait(&full_b[s], ((issued[s] - 1) / TC_STAGES) & 1, TC_DRAIN_LIMIT);
+            // drain: every issued load has landed before shared memory can be released (the
+            // last use of each stage is last_it and, if issued, last_it - 1)
+            for (int u = last_it; u >= 0 && u >= last_it - (TC_STAGES - 1); --u)
+                mbar_wait(&full_b[u % TC_STAGES], (u / TC_STAGES) & 1, TC_DRAIN_LIMIT);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -263,9 +273,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp < 6) {
         // ------------------------------------------------------------ A producers
-        const int r = threadIdx.x - 64;        // tile row = range bin within the tile
+        // Thread r owns tile row r (one range bin).  The cell's bins and phases are staged in
+        // shared memory once per tile; the 32 echo samples of stage k+1 are requested before
+        // stage k is converted, so the L2 latency of the gather overlaps the conversion.
+        // Every producer warp runs every tile iteration (also after an abort) so that the
+        // named barriers always see all 128 threads.
+        const int r = threadIdx.x - 64;
         const bool fp16 = p.fp16 != 0;
         const uint32_t swz = (uint32_t)(r & 7);
+        int *s_rho = reinterpret_cast<int *>(smem + TC_STAGES * TC_STAGE_BYTES);
+        float2 *s_w = reinterpret_cast<float2 *>(smem + TC_STAGES * TC_STAGE_BYTES + TC_TAB_MAX * 4);
+        const bool tab_smem = p.M <= TC_TAB_MAX;
+        bool aborted = false;
         int it = 0;
         for (int tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
             const int nt_m = tile / p.tiles_n;
@@ -275,11 +294,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const bool jok = j < p.r0_count;
             const long tab = (long)cl * p.M;
             const int nbase = p.r0_begin + j;
-            bool ok = true;
+            named_bar_sync(1, 128);                        // previous tile's table no longer read
+            const int *rho_t = p.rho + tab;
+            const float2 *w_t = p.w + tab;
+            if (!p.Z && tab_smem) {
+                if (!aborted)
+                    for (int m = r; m < p.M; m += 128) {
+                        s_rho[m] = __ldg(p.rho + tab + m);
+                        s_w[m] = __ldg(p.w + tab + m);
+                    }
+                rho_t = s_rho;
+                w_t = s_w;
+            }
+            named_bar_sync(1, 128);
+            if (aborted) continue;
+
+            float2 cur[32];
+            auto load_stage = [&](int kt, float2 (&v)[32]) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int m = kt * 32 + i;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (m < p.M && jok) {
+                        if (p.Z) {
+                            x = __ldg(p.Z + (tab + m) * p.r0_count + j);
+                        } else {
+                            const int n = nbase + rho_t[m];
+                            if ((unsigned)n < (unsigned)p.N) x = __ldg(p.echo + (long)m * p.N + n);
+                        }
+                    }
+                    v[i] = x;
+                }
+            };
+            load_stage(0, cur);
             for (int kt = 0; kt < p.KT; ++kt, ++it) {
+                float2 nxt[32];
+                if (kt + 1 < p.KT) {
+                    load_stage(kt + 1, nxt);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) nxt[i] = make_float2(0.f, 0.f);
+                }
                 const int s = it % TC_STAGES;
                 if (!warp_wait(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim, &abort_flag, p.status)) {
-                    ok = false;
+                    aborted = true;
                     break;
                 }
                 const uint32_t a_hi = sbase + s * TC_STAGE_BYTES + r * 128;
@@ -290,16 +348,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int m = kt * 32 + g * 8 + i;
-                        float2 v = make_float2(0.f, 0.f);
-                        if (m < p.M && jok) {
-                            if (p.Z) {
-                                v = __ldg(p.Z + (tab + m) * p.r0_count + j);
-                            } else {
-                                const int n = nbase + __ldg(p.rho + tab + m);
-                                if ((unsigned)n < (unsigned)p.N)
-                                    v = cmul(__ldg(p.echo + (long)m * p.N + n), __ldg(p.w + tab + m));
-                            }
-                        }
+                        float2 v = cur[g * 8 + i];
+                        if (!p.Z && m < p.M) v = cmul(v, w_t[m]);
                         re[i] = v.x;
                         im[i] = v.y;
                     }
@@ -318,28 +368,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 fence_proxy_async_shared();
                 mbar_arrive(&full_a[s]);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
             }
-            if (!ok) break;
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q4 = warp & 3;                 // TMEM lane quarter of this warp
+        // Thread (warp q4, lane) owns TMEM lane r = 32 q4 + lane = tile row (range bin).
+        // Per tile the 128 output row offsets (one per fine hypothesis of the tile) go to a
+        // shared table; stores are streaming (evict-first) so that the output does not push
+        // the echo and the dechirp operand out of L2.
+        const int q4 = warp & 3;
         const int r = q4 * 32 + lane;
+        const int er = threadIdx.x - 192;        // 0..127 over the epilogue warps
         const DsOut o = p.out;
         const int na_full = o.na_c * o.Fa;
+        bool aborted = false;
         int tcount = 0;
         for (int tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x, ++tcount) {
             const int b = tcount & 1;
-            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, p.status)) break;
-            tc_fence_after();
             const int nt = tile % p.tiles_n;
             const int nt_m = tile / p.tiles_n;
             const int mt = nt_m % p.tiles_m;
             const int cl = nt_m / p.tiles_m;
-            const int j = mt * TC_BM + r;
-            const bool jok = j < p.r0_count;
             const int c = o.cell_begin + cl;
             const int iv = c / o.na_c - o.i0, il = c % o.na_c;
+            named_bar_sync(2, 128);                  // previous tile's offsets no longer read
+            if (!aborted) {
+                const int f = nt * (TC_BN / 2) + er;
+                long off = -1;
+                if (f < p.F) {
+                    const int k = f / o.Fa, q = f % o.Fa;
+                    off = ((long)(iv * o.Fv + k) * na_full + (il * o.Fa + q)) * p.r0_count;
+                }
+                s_rowoff[er] = off;
+            }
+            named_bar_sync(2, 128);
+            if (aborted) continue;
+            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, p.status)) {
+                aborted = true;
+                continue;
+            }
+            tc_fence_after();
+            const int j = mt * TC_BM + r;
+            const bool jok = j < p.r0_count;
             const float2 e = (jok && o.Y) ? p.e0[j] : make_float2(1.f, 0.f);
             const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * TC_BN);
 #pragma unroll 1
@@ -350,15 +422,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (jok) {
 #pragma unroll
                     for (int pp = 0; pp < 16; ++pp) {
-                        const int f = nt * (TC_BN / 2) + ch * 16 + pp;
-                        if (f < p.F) {
+                        const long ro = s_rowoff[ch * 16 + pp];
+                        if (ro >= 0) {
                             const float yr = __uint_as_float(v[2 * pp]);
                             const float yi = __uint_as_float(v[2 * pp + 1]);
-                            const int k = f / o.Fa, q = f % o.Fa;
-                            const long row = (long)(iv * o.Fv + k) * na_full + (il * o.Fa + q);
-                            const long idx = row * p.r0_count + j;
-                            if (o.P) o.P[idx] = yr * yr + yi * yi;
-                            if (o.Y) o.Y[idx] = make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr);
+                            if (o.P) __stcs(o.P + ro + j, yr * yr + yi * yi);
+                            if (o.Y) __stcs(o.Y + ro + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
                         }
                     }
                 }
@@ -419,7 +488,7 @@ int launch_ds_tc(const Ctx &c, const RadarD &R, const float2 *echo, const float2
     const uint32_t fmt = fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
     p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
               ((uint32_t)(TC_BM >> 4) << 24);
-    const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+    const size_t smem = TC_SMEM_BYTES;
     static bool attr_set[64] = {false};
     if (c.device < 64 && !attr_set[c.device]) {
         if (cudaFuncSetAttribute(k_ds_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

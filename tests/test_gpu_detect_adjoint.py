@@ -114,8 +114,13 @@ def test_adjoint_matches_oracle_gradient(cuda_lib, gather):
     assert np.abs(P.cpu().numpy() - Po).max() <= 1e-4 * Po.max()
     assert np.abs(Y.cpu().numpy() - Yo).max() <= TOL_FP32 * 10 * np.abs(Yo).max()
     gg = gt.cpu().numpy()
+    k4 = 4 * np.pi / R.wavelength
     for j in range(3):
         scale = np.abs(go[:, j]).max()
+        if gather == 0 and j == 0:
+            # nearest gather: dP/dr0 = 2 Re(conj(Y) j k4 Y) = 0 exactly; the FP32 sums leave
+            # rounding of the size of the terms 2 k4 |Y|^2 they cancel
+            scale = 2 * k4 * Po.max()
         assert np.abs(gg[:, j] - go[:, j]).max() <= 1e-4 * scale, (j, np.abs(gg[:, j] - go[:, j]).max() / scale)
 
 
