@@ -17,6 +17,7 @@ namespace {
 constexpr int MAX_DEV = 64;
 constexpr uint64_t DEFAULT_WAIT_LIMIT = 2000000000ull;   // ~1 s of SM cycles
 constexpr size_t PLAIN_TABLE_BUDGET = 256ull << 20;
+constexpr size_t SPLIT_OPERAND_BUDGET = 4ull << 30;   // both planes of the split coarse-RM output
 
 struct DevState {
     bool init = false;
@@ -258,8 +259,17 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
     const size_t d_bytes = tc ? align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t))
                               : align_up((size_t)R.M * F * sizeof(float2));
-    unsigned char *ws =
-        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes : d_bytes));
+    size_t z_plane = 0;
+    int chunk_cells = cell_count;
+    if (tc) {
+        const size_t per_cell = ds_tc_split_plane_bytes_per_cell(grid->r0_count, Mpad);
+        chunk_cells = (int)(SPLIT_OPERAND_BUDGET / (2 * per_cell));
+        if (chunk_cells < 1) chunk_cells = 1;
+        if (chunk_cells > cell_count) chunk_cells = cell_count;
+        z_plane = align_up(per_cell * chunk_cells);
+    }
+    unsigned char *ws = (unsigned char *)workspace(
+        c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 2 * z_plane : d_bytes));
     if (!ws) return GRFT_ENOMEM;
     int32_t *rho = (int32_t *)ws;
     float2 *w = (float2 *)(ws + rho_bytes);
@@ -282,10 +292,11 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
                               D, e0, out);
     }
     uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
+    uint16_t *Zhi = (uint16_t *)(dptr + 2 * d_bytes), *Zlo = (uint16_t *)(dptr + 2 * d_bytes + z_plane);
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
     return launch_ds_tc(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w, Bhi,
-                        Blo, Mpad, fp16, e0, out);
+                        Blo, Mpad, fp16, e0, out, Zhi, Zlo, chunk_cells);
 }
 
 int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,

@@ -3,8 +3,9 @@
 // the on-grid estimate of eq. MLE-GRFT-FD).
 //
 // k_cfar: one CTA per 2048-bin row segment.  The segment and a halo of guard+train+1
-// bins are staged in shared memory with coalesced loads; each thread scans 8
-// consecutive bins with a sliding training-window sum held in registers.  Cells that pass
+// bins are staged in shared memory (all loads in flight at once, float4 where aligned,
+// padded one float per 8 so that a warp's 8-bin-strided reads hit distinct banks); each
+// thread scans 8 consecutive bins with a sliding training-window sum held in registers.  Cells that pass
 // the threshold test compare themselves with their 26 neighbours and are appended to a
 // candidate list with a warp-aggregated atomic (one atomicAdd per warp via __ballot_sync).
 // HBM-bound: P is read once.
@@ -39,19 +40,24 @@ __device__ __forceinline__ int window_count(int lo, int hi, int nr0) {
     return hi >= lo ? hi - lo + 1 : 0;
 }
 
+// Shared-memory slot of staged position i >= 0: one pad float after every 8, so that the
+// lanes of a warp, each scanning 8 consecutive bins, read distinct banks.
+__device__ __forceinline__ int cf_slot(int i) { return i + (i >> 3); }
+constexpr int CF_STAGE = CF_SEG + 2 * CF_MAXHALO;
+
 __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P, CfarParams cp,
                                                      int nseg, int *__restrict__ count,
                                                      float *__restrict__ cand_p,
                                                      int64_t *__restrict__ cand_i, int *status) {
-    // shared-memory index of bin n is n - seg0 + CF_MAXHALO (a multiple of 4, so the
-    // thread's 8 bins land 16-byte aligned)
-    __shared__ alignas(16) float sv[CF_SEG + 2 * CF_MAXHALO];
+    // staged position of bin n is n - seg0 + CF_MAXHALO (always >= 0)
+    __shared__ float sv[CF_STAGE + CF_STAGE / 8 + 1];
     const long row = blockIdx.x / nseg;
     const int seg0 = (int)(blockIdx.x % nseg) * CF_SEG;
     const int G = cp.guard, T = cp.train, nr0 = cp.nr0;
     const int halo = G + T + 1;
     const float *prow = P + row * nr0;
     const int nb = seg0 + threadIdx.x * CF_PER;     // first bin of this thread
+    const int sb = CF_MAXHALO - seg0;               // staged position of bin n is n + sb
     // every load of the segment is issued before any is used (one memory latency per CTA)
     float x[CF_PER];
     const bool vec = ((((uintptr_t)(prow + nb)) & 15) == 0) && nb + CF_PER <= nr0;
@@ -70,32 +76,30 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
         hl = (nl >= 0 && nl < nr0) ? __ldg(prow + nl) : 0.f;
         hr = (nrr < nr0) ? __ldg(prow + nrr) : 0.f;
     }
-    {
-        float4 *dst = reinterpret_cast<float4 *>(&sv[CF_MAXHALO + threadIdx.x * CF_PER]);
-        dst[0] = make_float4(x[0], x[1], x[2], x[3]);
-        dst[1] = make_float4(x[4], x[5], x[6], x[7]);
-    }
+#pragma unroll
+    for (int q = 0; q < CF_PER; ++q) sv[cf_slot(nb + q + sb)] = x[q];
     if (threadIdx.x < halo) {
-        sv[CF_MAXHALO - halo + threadIdx.x] = hl;
-        sv[CF_MAXHALO + CF_SEG + threadIdx.x] = hr;
+        sv[cf_slot(CF_MAXHALO - halo + threadIdx.x)] = hl;
+        sv[cf_slot(CF_MAXHALO + CF_SEG + threadIdx.x)] = hr;
     }
     __syncthreads();
-    const int sb = CF_MAXHALO - seg0;               // sv[n + sb] holds bin n
+#define SV(n) sv[cf_slot((n) + sb)]
+
     const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
     float L = 0.f, Rr = 0.f;
     // initial windows for bin nb
     if (cp.mode == 0) {
-        for (int j = nb - G - T; j <= nb - G - 1; ++j) L += sv[j + sb];
-        for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += sv[j + sb];
+        for (int j = nb - G - T; j <= nb - G - 1; ++j) L += SV(j);
+        for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += SV(j);
     }
     for (int q = 0; q < CF_PER; ++q) {
         const int n = nb + q;
         const bool valid = n < nr0;      // no early exit: every lane reaches the ballot below
         if (q > 0 && cp.mode == 0) {
-            L += sv[n - G - 1 + sb] - sv[n - G - T - 1 + sb];
-            Rr += sv[n + G + T + sb] - sv[n + G + sb];
+            L += SV(n - G - 1) - SV(n - G - T - 1);
+            Rr += SV(n + G + T) - SV(n + G);
         }
-        const float p = sv[n + sb];
+        const float p = SV(n);
         bool pass = false;
         if (!valid) {
         } else if (cp.mode == 0) {
@@ -113,7 +117,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
                         const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
                         if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
                         const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
-                        const float po = (dv == 0 && da == 0) ? sv[n2 + sb] : __ldg(P + o);
+                        const float po = (dv == 0 && da == 0) ? SV(n2) : __ldg(P + o);
                         if (po > p || (po == p && o < me)) pass = false;
                     }
         }
@@ -135,6 +139,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
             }
         }
     }
+#undef SV
 }
 
 // (p, idx) ordering: larger p first, then smaller idx.

@@ -1,26 +1,32 @@
-// Fine Doppler-migration correction on the 5th-generation tensor cores (tcgen05 + TMEM).
+// The dual-scale cascade on the tensor cores (Alg. 3): coarse range-migration correction
+// in split form (kernel a) feeding the fine Doppler-migration contraction on the
+// 5th-generation tensor cores (kernel b).
 //
-// Per coarse cell (Alg. 3) the GFT of Def. 1 / Alg. 2 is a dense complex contraction over
-// pulses against the shared dechirp matrix D[m][f] (eq. H-DFM of the fine offsets):
+// Per coarse cell the GFT of Def. 1 / Alg. 2 is a dense complex contraction over pulses
+// against the dechirp matrix D[m][f] (eq. H-DFM of the fine offsets) shared by every cell:
 //   Y(n0; c, f) = e0(n0) * sum_m Zc[m][n0] D[m][f],   Zc[m][n0] = s[m][n0 + rho_c(m)] w_c(m)
 // It runs as one real GEMM (the "4M" form) with K' = 2M and N' = 2F:
 //   [Re Zc | Im Zc] (rows n0)  x  [[Re D, Im D], [-Im D, Re D]]  =  [Re Y~ | Im Y~]
 // and each real operand x is split as hi = round16(x), lo = round16(x - hi) (BF16 or FP16),
 // accumulating hi*hi + hi*lo + lo*hi in FP32 (three tcgen05.mma per K step).
 //
-// Kernel organisation (one persistent CTA per SM, 320 threads):
-//   warp 0      TMA producer: the split dechirp operand tiles (K-major, 128-byte swizzle)
-//   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warps 2..5  A producers: gather the coarse-cell echo rows (L2-resident), multiply by the
-//               coarse phase w_c(m), split hi/lo and write the 128-byte-swizzled K-major
-//               A tile (row = range bin) straight from registers
-//   warps 6..9  epilogue: TMEM -> registers (tcgen05.ld 32x32b), |Y|^2 (and Y = e0 * Y~),
-//               coalesced stores along r0 (one TMEM lane = one range bin)
-// Tile: 128 bins x 256 real columns (128 fine hypotheses) x 64 real k (32 pulses) per
-// stage; a 2-stage shared-memory ring (96 KB per stage) and two TMEM accumulators of 256
-// columns so that the epilogue of one tile overlaps the main loop of the next.  Every
-// mbarrier wait is bounded: a wait that runs out latches GRFT_ETIMEOUT, the CTA unwinds
-// (draining its own TMA copies and MMAs with a bounded wait) and frees its TMEM.
+// k_coarse_split (kernel a, the mGIFT of Alg. 1 in the time domain): one CTA per (cell,
+//   128-bin tile).  It gathers every bin's samples at n0 + rho_c(m) from the L2-resident
+//   echo, multiplies by the coarse phase w_c(m), splits hi/lo and writes the K-major
+//   operand Zs[cell][bin][k'] (two 16-bit planes) in whole-sector runs; the TMA loads of
+//   kernel b apply the 128-byte swizzle.  Done once per (cell, bin) instead of once per
+//   fine-hypothesis tile.
+// k_ds_tc (kernel b): one persistent CTA per SM, 192 threads:
+//   warp 0      TMA producer: Zs tile (A, 128 x 64) and dechirp tile (B, 256 x 64), hi and
+//               lo planes, 128-byte swizzle, into a 2-stage ring (96 KB per stage)
+//   warp 1      TMEM allocation (two 128 x 256 FP32 accumulators) and the single thread that
+//               issues tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16)
+//   warps 2..5  epilogue: tcgen05.ld 32x32b (one TMEM lane = one range bin), |Y|^2 and
+//               e0 * Y~, evict-first stores along r0
+// The tiles of one (cell, bin tile) for consecutive fine-hypothesis tiles go to
+// consecutive CTAs, so the A tile is read from HBM once and from L2 by the others.
+// Every mbarrier wait is bounded: a wait that runs out latches GRFT_ETIMEOUT, the CTA
+// unwinds (draining its TMA copies and MMAs with a bounded wait) and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,30 +41,34 @@ constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;                     // real columns per tile
 constexpr int TC_BK = 64;                      // real k per stage (32 pulses x re/im)
 constexpr int TC_STAGES = 2;
-constexpr int TC_THREADS = 320;
-constexpr uint32_t TC_A_BYTES = TC_BM * 128;   // 16 KB
-constexpr uint32_t TC_B_BYTES = TC_BN * 128;   // 32 KB
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_A_BYTES = TC_BM * 128;   // 16 KB per plane
+constexpr uint32_t TC_B_BYTES = TC_BN * 128;   // 32 KB per plane
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unwind path
-constexpr int TC_TAB_MAX = 2048;                     // pulses whose bins/phases fit in shared memory
-constexpr uint32_t TC_TAB_BYTES = TC_TAB_MAX * (4 + 8);
-constexpr size_t TC_SMEM_BYTES = (size_t)TC_STAGES * TC_STAGE_BYTES + TC_TAB_BYTES + 1024;
+constexpr size_t TC_SMEM_BYTES = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 
-struct TcParams {
-    const float2 *echo;
-    const float2 *Z;
-    const int32_t *rho;
-    const float2 *w;
-    const float2 *e0;
-    int M, N, Mpad, KT;
-    int r0_begin, r0_count;
-    int F, tiles_m, tiles_n, total_tiles;
+constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
+constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
+
+struct SplitParams {
+    const float2 *echo;     // [M][N], or nullptr when Z is given
+    const float2 *Z;        // [cells][M][r0_count] (already gathered and phased), or nullptr
+    const int32_t *rho;     // [cells][M]
+    const float2 *w;        // [cells][M]
+    int M, N, KT;
+    int r0_begin, r0_count, tiles_m, r0_pad;
+    int fp16;
+};
+
+struct GemmParams {
+    const float2 *e0;       // [r0_count]
+    int KT, tiles_m, tiles_n, total_tiles, r0_pad, r0_count, F;
     DsOut out;
     int *status;
     uint64_t wait_limit;
     uint32_t idesc;
-    int fp16;
 };
 
 // ----------------------------------------------------------------------- tcgen05 wrappers
@@ -126,13 +136,7 @@ __device__ __forceinline__ void split2(float x0, float x1, bool fp16, uint32_t &
     }
 }
 
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
-// Named barrier among `count` threads (ids 1 and 2; 0 is __syncthreads).
+// Named barrier among `count` threads (id 1; 0 is __syncthreads).
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -141,10 +145,10 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
 // the whole warp takes the same decision (keeps .sync.aligned operations converged).
 // Returns false if the wait ran out or the CTA is unwinding; lane 0 then latches the error.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit,
-                                          volatile int *abort_flag, int *status) {
+                                          volatile int *abort_flag, int *status, unsigned sleep_ns) {
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
-        ok = (!*abort_flag && mbar_wait(bar, parity, limit)) ? 1 : 0;
+        ok = (!*abort_flag && mbar_wait_backoff(bar, parity, limit, sleep_ns)) ? 1 : 0;
         if (!ok) {
             latch_error(status, GRFT_ETIMEOUT);
             *abort_flag = 1;
@@ -154,11 +158,102 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64
     return ok != 0;
 }
 
+// =========================================================================== kernel a
+__device__ __forceinline__ void st_global_v4(uint16_t *dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const SplitParams p, uint16_t *__restrict__ Zhi,
+                                                                uint16_t *__restrict__ Zlo) {
+    // One CTA per (cell, 128-bin tile).  Lane l of warp w owns bin r = 8w + l/4 and the
+    // 8-pulse group g = l%4 of every 32-pulse stage: its gathers are 8-bin runs (whole
+    // sectors) and its stores complete 64-byte runs of the K-major output rows
+    // (k' = (m/32)*64 + (re|im)*32 + m%32, hi and lo planes).  The cell's bins and phases
+    // are staged in shared memory; the next stage's samples are requested before the
+    // current stage is converted.
+    __shared__ int s_rho[SP_TAB_MAX];
+    __shared__ float2 s_w[SP_TAB_MAX];
+    const int mt = blockIdx.x % p.tiles_m;
+    const int cl = blockIdx.x / p.tiles_m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = warp * 8 + (lane >> 2);
+    const int g = lane & 3;
+    const bool fp16 = p.fp16 != 0;
+    const int j = mt * TC_BM + r;
+    const bool jok = j < p.r0_count;
+    const long tab = (long)cl * p.M;
+    const int nbase = p.r0_begin + j;
+    const bool tab_smem = !p.Z && p.M <= SP_TAB_MAX;
+    if (tab_smem) {
+        for (int m = tid; m < p.M; m += SP_THREADS) {
+            s_rho[m] = __ldg(p.rho + tab + m);
+            s_w[m] = __ldg(p.w + tab + m);
+        }
+        __syncthreads();
+    }
+    const int *rho_t = tab_smem ? s_rho : p.rho + tab;
+    const float2 *w_t = tab_smem ? s_w : p.w + tab;
+    const size_t row = (size_t)cl * p.r0_pad + j;
+    uint16_t *zh = Zhi + row * (size_t)(TC_BK * p.KT) + g * 8;
+    uint16_t *zl = Zlo + row * (size_t)(TC_BK * p.KT) + g * 8;
+
+    auto load8 = [&](int kt, float2 (&v)[8]) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = kt * 32 + g * 8 + i;
+            float2 x = make_float2(0.f, 0.f);
+            if (m < p.M && jok) {
+                if (p.Z) {
+                    x = __ldg(p.Z + (tab + m) * p.r0_count + j);
+                } else {
+                    const int n = nbase + rho_t[m];
+                    if ((unsigned)n < (unsigned)p.N) x = __ldg(p.echo + (long)m * p.N + n);
+                }
+            }
+            v[i] = x;
+        }
+    };
+    auto store8 = [&](int kt, const float2 (&v)[8]) {
+        float re[8], im[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = kt * 32 + g * 8 + i;
+            float2 x = v[i];
+            if (!p.Z && m < p.M) x = cmul(x, w_t[m]);
+            re[i] = x.x;
+            im[i] = x.y;
+        }
+        uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
+            split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
+        }
+        const int o = kt * TC_BK;
+        st_global_v4(zh + o, rh[0], rh[1], rh[2], rh[3]);
+        st_global_v4(zl + o, rl[0], rl[1], rl[2], rl[3]);
+        st_global_v4(zh + o + 32, ih[0], ih[1], ih[2], ih[3]);
+        st_global_v4(zl + o + 32, il[0], il[1], il[2], il[3]);
+    };
+    float2 va[8], vb[8];
+    load8(0, va);
+    for (int kt = 0; kt < p.KT; kt += 2) {      // the two buffers alternate
+        if (kt + 1 < p.KT) load8(kt + 1, vb);
+        store8(kt, va);
+        if (kt + 1 >= p.KT) break;
+        if (kt + 2 < p.KT) load8(kt + 2, va);
+        store8(kt + 1, vb);
+    }
+}
+
+// =========================================================================== kernel b
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_ds_tc(const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
-            const TcParams p) {
+    k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+            const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+            const GemmParams p) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ alignas(8) uint64_t full_a[TC_STAGES], full_b[TC_STAGES], empty[TC_STAGES];
+    __shared__ alignas(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
@@ -169,11 +264,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
+        tma_prefetch_desc(&mapAhi);
+        tma_prefetch_desc(&mapAlo);
         tma_prefetch_desc(&mapBhi);
         tma_prefetch_desc(&mapBlo);
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full_a[s], 128);
-            mbar_init(&full_b[s], 1);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -198,31 +294,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint64_t lim = p.wait_limit;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ TMA producer (B)
+        // ------------------------------------------------------------ TMA producer (A and B)
         if (lane == 0) {
             int it = 0;
-            int last_it = -1;            // last issued stage use (its stage is last_it % TC_STAGES)
+            int last_it = -1;
             for (int tile = blockIdx.x; tile < p.total_tiles && !abort_flag; tile += gridDim.x) {
                 const int nt = tile % p.tiles_n;
+                const int nt_m = tile / p.tiles_n;
+                const int mt = nt_m % p.tiles_m;
+                const int cl = nt_m / p.tiles_m;
+                const int arow = cl * p.r0_pad + mt * TC_BM;
                 for (int kt = 0; kt < p.KT; ++kt, ++it) {
                     const int s = it % TC_STAGES;
-                    if (!mbar_wait(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim)) {
+                    if (!mbar_wait_backoff(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim, 32)) {
                         latch_error(p.status, GRFT_ETIMEOUT);
                         abort_flag = 1;
                         break;
                     }
                     unsigned char *st = smem + s * TC_STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full_b[s], 2 * TC_B_BYTES);
-                    tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * TC_BK, nt * TC_BN, &full_b[s]);
+                    mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+                    tma_load_2d(st, &mapAhi, kt * TC_BK, arow, &full[s]);
+                    tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * TC_BK, arow, &full[s]);
+                    tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * TC_BK, nt * TC_BN, &full[s]);
                     tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &mapBlo, kt * TC_BK, nt * TC_BN,
-                                &full_b[s]);
+                                &full[s]);
                     last_it = it;
                 }
             }
             // drain: every issued load has landed before shared memory can be released (the
             // last use of each stage is last_it and, if issued, last_it - 1)
             for (int u = last_it; u >= 0 && u >= last_it - (TC_STAGES - 1); --u)
-                mbar_wait(&full_b[u % TC_STAGES], (u / TC_STAGES) & 1, TC_DRAIN_LIMIT);
+                mbar_wait(&full[u % TC_STAGES], (u / TC_STAGES) & 1, TC_DRAIN_LIMIT);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -241,8 +343,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 bool ok = true;
                 for (int kt = 0; kt < p.KT; ++kt, ++it) {
                     const int s = it % TC_STAGES;
-                    const uint32_t ph = (it / TC_STAGES) & 1;
-                    if (!mbar_wait(&full_a[s], ph, lim) || !mbar_wait(&full_b[s], ph, lim)) {
+                    if (!mbar_wait(&full[s], (it / TC_STAGES) & 1, lim)) {
                         latch_error(p.status, GRFT_ETIMEOUT);
                         abort_flag = 1;
                         ok = false;
@@ -271,116 +372,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_wait(&drain_bar, 0, TC_DRAIN_LIMIT);
             }
         }
-    } else if (warp < 6) {
-        // ------------------------------------------------------------ A producers
-        // Thread r owns tile row r (one range bin).  The cell's bins and phases are staged in
-        // shared memory once per tile; the 32 echo samples of stage k+1 are requested before
-        // stage k is converted, so the L2 latency of the gather overlaps the conversion.
-        // Every producer warp runs every tile iteration (also after an abort) so that the
-        // named barriers always see all 128 threads.
-        const int r = threadIdx.x - 64;
-        const bool fp16 = p.fp16 != 0;
-        const uint32_t swz = (uint32_t)(r & 7);
-        int *s_rho = reinterpret_cast<int *>(smem + TC_STAGES * TC_STAGE_BYTES);
-        float2 *s_w = reinterpret_cast<float2 *>(smem + TC_STAGES * TC_STAGE_BYTES + TC_TAB_MAX * 4);
-        const bool tab_smem = p.M <= TC_TAB_MAX;
-        bool aborted = false;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
-            const int nt_m = tile / p.tiles_n;
-            const int mt = nt_m % p.tiles_m;
-            const int cl = nt_m / p.tiles_m;
-            const int j = mt * TC_BM + r;                  // local r0 index
-            const bool jok = j < p.r0_count;
-            const long tab = (long)cl * p.M;
-            const int nbase = p.r0_begin + j;
-            named_bar_sync(1, 128);                        // previous tile's table no longer read
-            const int *rho_t = p.rho + tab;
-            const float2 *w_t = p.w + tab;
-            if (!p.Z && tab_smem) {
-                if (!aborted)
-                    for (int m = r; m < p.M; m += 128) {
-                        s_rho[m] = __ldg(p.rho + tab + m);
-                        s_w[m] = __ldg(p.w + tab + m);
-                    }
-                rho_t = s_rho;
-                w_t = s_w;
-            }
-            named_bar_sync(1, 128);
-            if (aborted) continue;
-
-            float2 cur[32];
-            auto load_stage = [&](int kt, float2 (&v)[32]) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int m = kt * 32 + i;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (m < p.M && jok) {
-                        if (p.Z) {
-                            x = __ldg(p.Z + (tab + m) * p.r0_count + j);
-                        } else {
-                            const int n = nbase + rho_t[m];
-                            if ((unsigned)n < (unsigned)p.N) x = __ldg(p.echo + (long)m * p.N + n);
-                        }
-                    }
-                    v[i] = x;
-                }
-            };
-            load_stage(0, cur);
-            for (int kt = 0; kt < p.KT; ++kt, ++it) {
-                float2 nxt[32];
-                if (kt + 1 < p.KT) {
-                    load_stage(kt + 1, nxt);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) nxt[i] = make_float2(0.f, 0.f);
-                }
-                const int s = it % TC_STAGES;
-                if (!warp_wait(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim, &abort_flag, p.status)) {
-                    aborted = true;
-                    break;
-                }
-                const uint32_t a_hi = sbase + s * TC_STAGE_BYTES + r * 128;
-                const uint32_t a_lo = a_hi + TC_A_BYTES;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {       // 8 pulses per 16-byte chunk
-                    float re[8], im[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int m = kt * 32 + g * 8 + i;
-                        float2 v = cur[g * 8 + i];
-                        if (!p.Z && m < p.M) v = cmul(v, w_t[m]);
-                        re[i] = v.x;
-                        im[i] = v.y;
-                    }
-                    uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
-                        split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
-                    }
-                    const uint32_t cre = ((uint32_t)g ^ swz) << 4;         // chunk g     (Re)
-                    const uint32_t cim = ((uint32_t)(g + 4) ^ swz) << 4;   // chunk g + 4 (Im)
-                    st_shared_v4(a_hi + cre, rh[0], rh[1], rh[2], rh[3]);
-                    st_shared_v4(a_lo + cre, rl[0], rl[1], rl[2], rl[3]);
-                    st_shared_v4(a_hi + cim, ih[0], ih[1], ih[2], ih[3]);
-                    st_shared_v4(a_lo + cim, il[0], il[1], il[2], il[3]);
-                }
-                fence_proxy_async_shared();
-                mbar_arrive(&full_a[s]);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
-            }
-        }
     } else {
         // ------------------------------------------------------------ epilogue
         // Thread (warp q4, lane) owns TMEM lane r = 32 q4 + lane = tile row (range bin).
         // Per tile the 128 output row offsets (one per fine hypothesis of the tile) go to a
-        // shared table; stores are streaming (evict-first) so that the output does not push
-        // the echo and the dechirp operand out of L2.
+        // shared table; stores are evict-first so that the 4 GB output does not push the
+        // operands out of L2.  Every epilogue warp runs every tile iteration (also after an
+        // abort) so that the named barrier always sees all 128 threads.
         const int q4 = warp & 3;
         const int r = q4 * 32 + lane;
-        const int er = threadIdx.x - 192;        // 0..127 over the epilogue warps
+        const int er = threadIdx.x - 64;         // 0..127 over the epilogue warps
         const DsOut o = p.out;
         const int na_full = o.na_c * o.Fa;
         bool aborted = false;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int cl = nt_m / p.tiles_m;
             const int c = o.cell_begin + cl;
             const int iv = c / o.na_c - o.i0, il = c % o.na_c;
-            named_bar_sync(2, 128);                  // previous tile's offsets no longer read
+            named_bar_sync(1, 128);                  // previous tile's offsets no longer read
             if (!aborted) {
                 const int f = nt * (TC_BN / 2) + er;
                 long off = -1;
@@ -403,9 +404,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 s_rowoff[er] = off;
             }
-            named_bar_sync(2, 128);
+            named_bar_sync(1, 128);
             if (aborted) continue;
-            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, p.status)) {
+            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, p.status, 256)) {
                 aborted = true;
                 continue;
             }
@@ -447,58 +448,91 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+bool set_smem_attr(const void *fn, size_t bytes, int device, bool *done) {
+    if (device < 64 && done[device]) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    if (device < 64) done[device] = true;
+    return true;
+}
+
 }  // namespace
+
+size_t ds_tc_split_plane_bytes_per_cell(int r0_count, int Mpad) {
+    const size_t r0_pad = (size_t)(r0_count + TC_BM - 1) / TC_BM * TC_BM;
+    return r0_pad * 2 * (size_t)Mpad * sizeof(uint16_t);
+}
 
 int launch_ds_tc(const Ctx &c, const RadarD &R, const float2 *echo, const float2 *Z,
                  const grft_dsgrid &g, int cell_count, const int32_t *rho, const float2 *w,
                  const uint16_t *Bhi, const uint16_t *Blo, int Mpad, bool fp16, const float2 *e0,
-                 const DsOut &out) {
+                 const DsOut &out, uint16_t *Zhi, uint16_t *Zlo, int chunk_cells) {
     if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
+    if (chunk_cells < 1) return GRFT_EINVAL;
     const int F = g.Fv * g.Fa;
     const int Fpad = (F + 127) / 128 * 128;
-    CUtensorMap mh, ml;
-    const uint64_t kdim = 2ull * Mpad, ndim = 2ull * Fpad;
-    if (!encode_tma_2d(&mh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, ndim, kdim * 2, TC_BK,
-                       TC_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_tma_2d(&ml, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, ndim, kdim * 2, TC_BK,
-                       TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    const int tiles_m = (g.r0_count + TC_BM - 1) / TC_BM;
+    const int r0_pad = tiles_m * TC_BM;
+    const uint64_t kdim = 2ull * Mpad;
+    static bool attr_gemm[64] = {false};
+    if (!set_smem_attr((const void *)k_ds_tc, TC_SMEM_BYTES, c.device, attr_gemm)) return GRFT_ECUDA;
+    CUtensorMap mbh, mbl;
+    if (!encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
+                       TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2,
+                       TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
         return GRFT_ECUDA;
-    TcParams p;
-    p.echo = echo;
-    p.Z = Z;
-    p.rho = rho;
-    p.w = w;
-    p.e0 = e0;
-    p.M = R.M;
-    p.N = R.N;
-    p.Mpad = Mpad;
-    p.KT = Mpad / 32;
-    p.r0_begin = g.r0_begin;
-    p.r0_count = g.r0_count;
-    p.F = F;
-    p.tiles_m = (g.r0_count + TC_BM - 1) / TC_BM;
-    p.tiles_n = Fpad / 128;
-    const long total = (long)cell_count * p.tiles_m * p.tiles_n;
-    if (total > 0x7fffffffL) return GRFT_EINVAL;
-    p.total_tiles = (int)total;
-    p.out = out;
-    p.status = c.status;
-    p.wait_limit = c.wait_limit;
-    p.fp16 = fp16 ? 1 : 0;
     const uint32_t fmt = fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
-    p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-              ((uint32_t)(TC_BM >> 4) << 24);
-    const size_t smem = TC_SMEM_BYTES;
-    static bool attr_set[64] = {false};
-    if (c.device < 64 && !attr_set[c.device]) {
-        if (cudaFuncSetAttribute(k_ds_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                           ((uint32_t)(TC_BM >> 4) << 24);
+    for (int c0 = 0; c0 < cell_count; c0 += chunk_cells) {
+        const int cc = cell_count - c0 < chunk_cells ? cell_count - c0 : chunk_cells;
+        CUtensorMap mzh, mzl;
+        const uint64_t rows = (uint64_t)cc * r0_pad;
+        if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, rows, kdim * 2, TC_BK,
+                           TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, rows, kdim * 2, TC_BK,
+                           TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
             return GRFT_ECUDA;
-        attr_set[c.device] = true;
+        SplitParams sp;
+        sp.echo = echo;
+        sp.Z = Z ? Z + (size_t)c0 * R.M * g.r0_count : nullptr;
+        sp.rho = rho + (size_t)c0 * R.M;
+        sp.w = w + (size_t)c0 * R.M;
+        sp.M = R.M;
+        sp.N = R.N;
+        sp.KT = Mpad / 32;
+        sp.r0_begin = g.r0_begin;
+        sp.r0_count = g.r0_count;
+        sp.tiles_m = tiles_m;
+        sp.r0_pad = r0_pad;
+        sp.fp16 = fp16 ? 1 : 0;
+        k_coarse_split<<<cc * tiles_m, SP_THREADS, 0, c.stream>>>(sp, Zhi, Zlo);
+        int e = check_launch();
+        if (e) return e;
+
+        GemmParams p;
+        p.e0 = e0;
+        p.KT = Mpad / 32;
+        p.tiles_m = tiles_m;
+        p.tiles_n = Fpad / 128;
+        p.r0_pad = r0_pad;
+        p.r0_count = g.r0_count;
+        p.F = F;
+        const long total = (long)cc * tiles_m * p.tiles_n;
+        if (total > 0x7fffffffL) return GRFT_EINVAL;
+        p.total_tiles = (int)total;
+        p.out = out;
+        p.out.cell_begin = out.cell_begin + c0;
+        p.status = c.status;
+        p.wait_limit = c.wait_limit;
+        p.idesc = idesc;
+        const int grid = (int)(total < c.num_sms ? total : c.num_sms);
+        k_ds_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, c.stream>>>(mzh, mzl, mbh, mbl, p);
+        e = check_launch();
+        if (e) return e;
     }
-    const int grid = (int)(total < c.num_sms ? total : c.num_sms);
-    k_ds_tc<<<grid, TC_THREADS, smem, c.stream>>>(mh, ml, p);
-    return check_launch();
+    return GRFT_OK;
 }
 
 }  // namespace grft

@@ -114,10 +114,13 @@ int launch_ds_simt(const Ctx &, const RadarD &, const float2 *echo, const float2
                    const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
                    const float2 *D, const float2 *e0, const DsOut &out);
 
+// Split coarse-RM pre-pass + tensor-core contraction, in chunks of `chunk_cells` cells whose
+// split operand (two planes of ds_tc_split_plane_bytes_per_cell each per cell) lives in Zhi/Zlo.
+size_t ds_tc_split_plane_bytes_per_cell(int r0_count, int Mpad);
 int launch_ds_tc(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
                  const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
                  const uint16_t *Bhi, const uint16_t *Blo, int Mpad, bool fp16,
-                 const float2 *e0, const DsOut &out);
+                 const float2 *e0, const DsOut &out, uint16_t *Zhi, uint16_t *Zlo, int chunk_cells);
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);

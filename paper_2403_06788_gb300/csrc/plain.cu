@@ -20,7 +20,7 @@ constexpr int PL_H = 8;
 constexpr int PL_MCHUNK = 128;
 constexpr int PL_TILE = PL_THREADS * PL_J;
 
-__global__ __launch_bounds__(PL_THREADS) void k_plain(
+__global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     const float2 *__restrict__ echo, int M, int N, const int32_t *__restrict__ rho_tab,
     const float2 *__restrict__ w_tab, int nh, int r0_begin, int r0_count,
     const float2 *__restrict__ e0, float2 *__restrict__ Y, float *__restrict__ P) {
@@ -49,23 +49,35 @@ __global__ __launch_bounds__(PL_THREADS) void k_plain(
             s_w[mm][h] = ok ? w_tab[o] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int mm = 0; mm < mn; ++mm) {
+        // The samples of pulse mm+1 at the first hypothesis' shift are requested before
+        // pulse mm is accumulated, hiding the L2 latency of the gather.
+        auto load_row = [&](int mm, int r, float2 (&v)[PL_J]) {
             const float2 *row = echo + (long)(mc + mm) * N;
-            int prev = INT_MIN;
+            const int base = n0 + r;
+#pragma unroll
+            for (int j = 0; j < PL_J; ++j) {
+                const int n = base + j;
+                v[j] = ((unsigned)n < (unsigned)N) ? __ldg(row + n) : make_float2(0.f, 0.f);
+            }
+        };
+        int pre_r = s_rho[0][0];
+        float2 pre[PL_J];
+        load_row(0, pre_r, pre);
+        for (int mm = 0; mm < mn; ++mm) {
+            int prev = pre_r;
             float2 sv[PL_J];
 #pragma unroll
-            for (int j = 0; j < PL_J; ++j) sv[j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < PL_J; ++j) sv[j] = pre[j];
+            if (mm + 1 < mn) {
+                pre_r = s_rho[mm + 1][0];
+                load_row(mm + 1, pre_r, pre);
+            }
 #pragma unroll
             for (int h = 0; h < PL_H; ++h) {
                 const int r = s_rho[mm][h];
                 if (r != prev) {             // CTA-uniform branch
                     prev = r;
-                    const int base = n0 + r;
-#pragma unroll
-                    for (int j = 0; j < PL_J; ++j) {
-                        int n = base + j;
-                        sv[j] = ((unsigned)n < (unsigned)N) ? __ldg(row + n) : make_float2(0.f, 0.f);
-                    }
+                    load_row(mm, r, sv);
                 }
                 const float2 w = s_w[mm][h];
 #pragma unroll
