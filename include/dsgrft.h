@@ -132,6 +132,28 @@ int grft_bins_phases(const grft_radar *radar, const double *v, const double *a, 
 int grft_plain(const grft_radar *radar, const grft_c32 *echo, const grft_grid *grid,
                grft_c32 *Y, float *P, void *stream);
 
+/* Size of the fixed device scratch of grft_plain_static (8 MiB). */
+#define GRFT_PLAIN_STATIC_SCRATCH_BYTES (8u << 20)
+
+/* grft_plain without any device allocation (the paper has no counterpart; this is for
+ * callers that cannot call cudaMalloc, e.g. a processing loop with a fixed memory budget,
+ * code running during stream capture, or a process whose device memory belongs to another
+ * pool).  Same arguments, results and output layout as grft_plain (bit-identical); the
+ * bin/phase tables live in a fixed array of GRFT_PLAIN_STATIC_SCRATCH_BYTES inside the
+ * library image (held by every GPU that loads the library until the process exits)
+ * instead of the library workspace, and the grid is processed in chunks that fit it.
+ *   - Size limit: returns GRFT_EINVAL, before enqueueing anything, if
+ *     r0_count * 8 (rounded up to 256) + 8 * M * 12 + 512 > GRFT_PLAIN_STATIC_SCRATCH_BYTES
+ *     (the range phases plus one group of 8 hypotheses' tables must fit).
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array: calls that overlap on the GPU (other
+ *     streams, other threads) race on it and must be serialised by the caller.  Each call
+ *     writes the part it reads, so nothing needs to be cleared between calls. */
+int grft_plain_static(const grft_radar *radar, const grft_c32 *echo, const grft_grid *grid,
+                      grft_c32 *Y, float *P, void *stream);
+
 /* Coarse range-migration correction, time-domain mGIFT (Def. 2 + eq. pre-DFM, Alg. 1):
  *   Z[c - cell_begin][m][j] = s[m][r0_begin + j + rho_c(m)] * exp(j 4 pi d_c(t_m) / lambda)
  * for coarse cells c in [cell_begin, cell_begin + cell_count), j in [0, r0_count).

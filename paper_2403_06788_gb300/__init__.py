@@ -19,7 +19,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
-           "grft_bins_phases", "grft_plain", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
+           "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
            "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
@@ -108,6 +108,14 @@ def grft_plain(radar, echo, grid, Y=None, P=None, stream=None):
     check(load().grft_plain(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
                             _ptr(Y, torch.complex64, "Y"), _ptr(P, torch.float32, "P"),
                             _stream(stream)), "grft_plain")
+
+
+def grft_plain_static(radar, echo, grid, Y=None, P=None, stream=None):
+    """grft_plain without any device allocation (fixed in-library scratch; see the header)."""
+    R, G = _radar(radar), _grid(grid)
+    check(load().grft_plain_static(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
+                                   _ptr(Y, torch.complex64, "Y"), _ptr(P, torch.float32, "P"),
+                                   _stream(stream)), "grft_plain_static")
 
 
 def dsgrft_coarse_rm(radar, echo, grid, cell_begin, cell_count, Z, stream=None):

@@ -64,6 +64,7 @@ SIGNATURES = {
     "grft_release_workspace": (C.c_int, []),
     "grft_bins_phases": (C.c_int, [C.POINTER(grft_radar), _P, _P, C.c_int32, _P, _P, _P]),
     "grft_plain": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),
+    "grft_plain_static": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),
     "dsgrft_coarse_rm": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                    C.c_int32, _P, _P]),
     "dsgrft_fine_dfm": (C.c_int, [C.POINTER(grft_radar), _P, _P, C.POINTER(grft_dsgrid), C.c_int32,
