@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -17,7 +18,22 @@ namespace {
 constexpr int MAX_DEV = 64;
 constexpr uint64_t DEFAULT_WAIT_LIMIT = 2000000000ull;   // ~1 s of SM cycles
 constexpr size_t PLAIN_TABLE_BUDGET = 256ull << 20;
-constexpr size_t SPLIT_OPERAND_BUDGET = 4ull << 30;   // both planes of the split coarse-RM output
+constexpr size_t SPLIT_OPERAND_DEFAULT = 4ull << 30;  // both planes of the split coarse-RM output
+
+// Workspace budget of the split operand of the tensor-core DS path (both planes).  The
+// environment variable DSGRFT_SPLIT_BUDGET_BYTES overrides it (read once; smaller values
+// make large problems run in more rounds, which the tests use to exercise chunking).
+size_t split_budget() {
+    static size_t v = [] {
+        const char *e = getenv("DSGRFT_SPLIT_BUDGET_BYTES");
+        if (e && *e) {
+            const unsigned long long x = strtoull(e, nullptr, 10);
+            if (x > 0) return (size_t)x;
+        }
+        return SPLIT_OPERAND_DEFAULT;
+    }();
+    return v;
+}
 
 struct DevState {
     bool init = false;
@@ -259,15 +275,17 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
     const size_t d_bytes = tc ? align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t))
                               : align_up((size_t)R.M * F * sizeof(float2));
-    size_t z_plane = 0;
-    int chunk_cells = cell_count;
+    // split operand: as many whole cells as fit the budget (at least one)
+    const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
+    const long r0_pad = tc ? ds_tc_r0_pad(grid->r0_count) : 0;
+    long z_rows = 0;
     if (tc) {
-        const size_t per_cell = ds_tc_split_plane_bytes_per_cell(grid->r0_count, Mpad);
-        chunk_cells = (int)(SPLIT_OPERAND_BUDGET / (2 * per_cell));
-        if (chunk_cells < 1) chunk_cells = 1;
-        if (chunk_cells > cell_count) chunk_cells = cell_count;
-        z_plane = align_up(per_cell * chunk_cells);
+        long cells_fit = (long)(split_budget() / (2 * r0_pad * row_bytes));
+        if (cells_fit < 1) cells_fit = 1;
+        if (cells_fit > cell_count) cells_fit = cell_count;
+        z_rows = cells_fit * r0_pad;
     }
+    const size_t z_plane = align_up((size_t)z_rows * row_bytes);
     unsigned char *ws = (unsigned char *)workspace(
         c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 2 * z_plane : d_bytes));
     if (!ws) return GRFT_ENOMEM;
@@ -277,15 +295,15 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
     if (!Z && (e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
     if ((e = launch_range_phase(c, R, grid->r0_begin, grid->r0_count, e0))) return e;
-    DsOut out;
-    out.Y = (float2 *)Y;
-    out.P = P;
-    out.cell_begin = cell_begin;
-    out.i0 = cell_begin / grid->ac.count;
-    out.na_c = grid->ac.count;
-    out.Fv = grid->Fv;
-    out.Fa = grid->Fa;
     if (!tc) {
+        DsOut out;
+        out.Y = (float2 *)Y;
+        out.P = P;
+        out.cell_begin = cell_begin;
+        out.i0 = cell_begin / grid->ac.count;
+        out.na_c = grid->ac.count;
+        out.Fv = grid->Fv;
+        out.Fa = grid->Fa;
         float2 *D = (float2 *)dptr;
         if ((e = launch_dechirp(c, R, *grid, D))) return e;
         return launch_ds_simt(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w,
@@ -295,20 +313,92 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     uint16_t *Zhi = (uint16_t *)(dptr + 2 * d_bytes), *Zlo = (uint16_t *)(dptr + 2 * d_bytes + z_plane);
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
-    return launch_ds_tc(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w, Bhi,
-                        Blo, Mpad, fp16, e0, out, Zhi, Zlo, chunk_cells);
+    DsTcItem it;
+    it.echo = (const float2 *)echo;
+    it.Z = (const float2 *)Z;
+    it.P = P;
+    it.Y = (float2 *)Y;
+    it.e0 = e0;
+    it.M = R.M;
+    it.N = R.N;
+    it.r0_begin = grid->r0_begin;
+    it.r0_count = grid->r0_count;
+    it.cell_begin = cell_begin;
+    it.cell_count = cell_count;
+    it.i0 = cell_begin / grid->ac.count;
+    return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
 }
 
 int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
                             const grft_batch_item *items, int32_t n_items, grft_precision precision,
                             void *stream) {
-    (void)radar;
-    (void)grid;
-    (void)items;
-    (void)n_items;
-    (void)precision;
-    (void)stream;
-    return GRFT_EUNSUPPORTED;
+    if (!radar || !grid || !items || n_items <= 0 || n_items > 256) return GRFT_EINVAL;
+    if (precision != GRFT_BF16X3 && precision != GRFT_FP16X3) return GRFT_EINVAL;
+    int Mmax = 0, Nmax = 0;
+    long rpad_max = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const grft_batch_item &b = items[i];
+        if (!b.echo || (!b.P && !b.Y) || b.M <= 0 || b.N <= 0 || b.r0_begin < 0 || b.r0_count <= 0 ||
+            (long)b.r0_begin + b.r0_count > b.N)
+            return GRFT_EINVAL;
+        if (b.M > Mmax) Mmax = b.M;
+        if (b.N > Nmax) Nmax = b.N;
+        if (ds_tc_r0_pad(b.r0_count) > rpad_max) rpad_max = ds_tc_r0_pad(b.r0_count);
+    }
+    grft_radar rmax = *radar;
+    rmax.M = Mmax;
+    rmax.N = Nmax;
+    grft_dsgrid g = *grid;
+    g.r0_begin = 0;
+    g.r0_count = Nmax;
+    if (!radar_ok(&rmax) || !dsgrid_ok(&g, &rmax)) return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(rmax);            // tables for Mmax pulses and bins [0, Nmax)
+    const int ncell = g.vc.count * g.ac.count;
+    const int F = g.Fv * g.Fa;
+    const int Fpad = (F + 127) / 128 * 128;
+    const int Mpad = (Mmax + 31) / 32 * 32;
+    const size_t rho_bytes = align_up((size_t)ncell * Mmax * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)ncell * Mmax * sizeof(float2));
+    const size_t e0_bytes = align_up((size_t)Nmax * sizeof(float2));
+    const size_t d_bytes = align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t));
+    const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
+    long z_rows = (long)(split_budget() / (2 * row_bytes));
+    if (z_rows < rpad_max) z_rows = rpad_max;
+    const size_t z_plane = align_up((size_t)z_rows * row_bytes);
+    unsigned char *ws =
+        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + 2 * d_bytes + 2 * z_plane);
+    if (!ws) return GRFT_ENOMEM;
+    int32_t *rho = (int32_t *)ws;
+    float2 *w = (float2 *)(ws + rho_bytes);
+    float2 *e0 = (float2 *)(ws + rho_bytes + w_bytes);
+    unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
+    uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
+    uint16_t *Zhi = (uint16_t *)(dptr + 2 * d_bytes), *Zlo = (uint16_t *)(dptr + 2 * d_bytes + z_plane);
+    const bool fp16 = precision == GRFT_FP16X3;
+    if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
+    if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;
+    if ((e = launch_dechirp_split(c, R, g, Mpad, Fpad, fp16, Bhi, Blo))) return e;
+    DsTcItem list[256];
+    for (int i = 0; i < n_items; ++i) {
+        const grft_batch_item &b = items[i];
+        DsTcItem &it = list[i];
+        it.echo = (const float2 *)b.echo;
+        it.Z = nullptr;
+        it.P = b.P;
+        it.Y = (float2 *)b.Y;
+        it.e0 = e0 + b.r0_begin;
+        it.M = b.M;
+        it.N = b.N;
+        it.r0_begin = b.r0_begin;
+        it.r0_count = b.r0_count;
+        it.cell_begin = 0;
+        it.cell_count = ncell;
+        it.i0 = 0;
+    }
+    return launch_ds_tc(c, list, n_items, g, rho, w, 0, Mmax, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
 }
 
 int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft_cfar *cfar,

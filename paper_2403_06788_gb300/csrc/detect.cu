@@ -2,10 +2,10 @@
 // maximum over (v, a, r0), and the K strongest detections (Alg. 3's threshold scan plus
 // the on-grid estimate of eq. MLE-GRFT-FD).
 //
-// k_cfar: one CTA per 2048-bin row segment.  The segment and a halo of guard+train+1
+// k_cfar: one CTA per 4096-bin row segment.  The segment and a halo of guard+train+1
 // bins are staged in shared memory (all loads in flight at once, float4 where aligned,
-// padded one float per 8 so that a warp's 8-bin-strided reads hit distinct banks); each
-// thread scans 8 consecutive bins with a sliding training-window sum held in registers.  Cells that pass
+// padded one float per 16 so that a warp's 16-bin-strided reads hit distinct banks); each
+// thread scans 16 consecutive bins with a sliding training-window sum held in registers.  Cells that pass
 // the threshold test compare themselves with their 26 neighbours and are appended to a
 // candidate list with a warp-aggregated atomic (one atomicAdd per warp via __ballot_sync).
 // HBM-bound: P is read once.
@@ -21,7 +21,7 @@ namespace grft {
 namespace {
 
 constexpr int CF_THREADS = 256;
-constexpr int CF_PER = 8;
+constexpr int CF_PER = 16;
 constexpr int CF_SEG = CF_THREADS * CF_PER;
 constexpr int CF_MAXHALO = 80;
 constexpr int TOPK_SORT = 8192;
@@ -40,9 +40,9 @@ __device__ __forceinline__ int window_count(int lo, int hi, int nr0) {
     return hi >= lo ? hi - lo + 1 : 0;
 }
 
-// Shared-memory slot of staged position i >= 0: one pad float after every 8, so that the
-// lanes of a warp, each scanning 8 consecutive bins, read distinct banks.
-__device__ __forceinline__ int cf_slot(int i) { return i + (i >> 3); }
+// Shared-memory slot of staged position i >= 0: one pad float after every 16, so that the
+// lanes of a warp, each scanning 16 consecutive bins, read distinct banks.
+__device__ __forceinline__ int cf_slot(int i) { return i + (i >> 4); }
 constexpr int CF_STAGE = CF_SEG + 2 * CF_MAXHALO;
 
 __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P, CfarParams cp,
@@ -50,7 +50,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
                                                      float *__restrict__ cand_p,
                                                      int64_t *__restrict__ cand_i, int *status) {
     // staged position of bin n is n - seg0 + CF_MAXHALO (always >= 0)
-    __shared__ float sv[CF_STAGE + CF_STAGE / 8 + 1];
+    __shared__ float sv[CF_STAGE + CF_STAGE / 16 + 1];
     const long row = blockIdx.x / nseg;
     const int seg0 = (int)(blockIdx.x % nseg) * CF_SEG;
     const int G = cp.guard, T = cp.train, nr0 = cp.nr0;
@@ -62,10 +62,12 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
     float x[CF_PER];
     const bool vec = ((((uintptr_t)(prow + nb)) & 15) == 0) && nb + CF_PER <= nr0;
     if (vec) {
-        const float4 a = __ldcs(reinterpret_cast<const float4 *>(prow + nb));
-        const float4 b = __ldcs(reinterpret_cast<const float4 *>(prow + nb) + 1);
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        const float4 *src = reinterpret_cast<const float4 *>(prow + nb);
+#pragma unroll
+        for (int q = 0; q < CF_PER / 4; ++q) {
+            const float4 t = __ldcs(src + q);
+            x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
     } else {
 #pragma unroll
         for (int q = 0; q < CF_PER; ++q) x[q] = (nb + q < nr0) ? __ldcs(prow + nb + q) : 0.f;
@@ -86,12 +88,15 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
 #define SV(n) sv[cf_slot((n) + sb)]
 
     const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
+    // all 16 bins' training windows inside the row: the training-cell count is 2T
+    const bool interior = nb - G - T >= 0 && nb + CF_PER - 1 + G + T < nr0;
+    const float alpha_in = cp.alpha[2 * T];
     float L = 0.f, Rr = 0.f;
-    // initial windows for bin nb
     if (cp.mode == 0) {
         for (int j = nb - G - T; j <= nb - G - 1; ++j) L += SV(j);
         for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += SV(j);
     }
+#pragma unroll
     for (int q = 0; q < CF_PER; ++q) {
         const int n = nb + q;
         const bool valid = n < nr0;      // no early exit: every lane reaches the ballot below
@@ -99,12 +104,16 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
             L += SV(n - G - 1) - SV(n - G - T - 1);
             Rr += SV(n + G + T) - SV(n + G);
         }
-        const float p = SV(n);
+        const float p = x[q];
         bool pass = false;
         if (!valid) {
         } else if (cp.mode == 0) {
-            const int nt = window_count(n - G - T, n - G - 1, nr0) + window_count(n + G + 1, n + G + T, nr0);
-            pass = nt > 0 && p > cp.alpha[nt] * (L + Rr);
+            if (interior) {
+                pass = p > alpha_in * (L + Rr);
+            } else {
+                const int nt = window_count(n - G - T, n - G - 1, nr0) + window_count(n + G + 1, n + G + T, nr0);
+                pass = nt > 0 && p > cp.alpha[nt] * (L + Rr);
+            }
         } else {
             pass = p > cp.fixed;
         }

@@ -52,24 +52,49 @@ constexpr size_t TC_SMEM_BYTES = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
 constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
 constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
 
-struct SplitParams {
+constexpr int TC_MAX_ITEMS = 64;                     // CPIs per launch (kernel-parameter table)
+
+// One CPI (or one call's cell range) inside a launch.
+struct TcItem {
     const float2 *echo;     // [M][N], or nullptr when Z is given
-    const float2 *Z;        // [cells][M][r0_count] (already gathered and phased), or nullptr
-    const int32_t *rho;     // [cells][M]
-    const float2 *w;        // [cells][M]
+    const float2 *Z;        // [cells][M][r0_count] (gathered and phased), or nullptr
+    float *P;               // output planes (canonical v-slab layout), either may be null
+    float2 *Y;
+    const float2 *e0;       // e0[j] = range phase of bin r0_begin + j
     int M, N, KT;
     int r0_begin, r0_count, tiles_m, r0_pad;
-    int fp16;
+    int cell0, ncell;       // absolute coarse cells [cell0, cell0 + ncell) of this launch
+    int i0;                 // first coarse v row of the output slab
+    long zrow0;             // first row of this item in the launch's split operand
+    int cta0, tile0;        // first split CTA / first GEMM tile of this item
 };
 
-struct GemmParams {
-    const float2 *e0;       // [r0_count]
-    int KT, tiles_m, tiles_n, total_tiles, r0_pad, r0_count, F;
-    DsOut out;
+struct TcBatch {
+    const int32_t *rho;     // coarse bins   [cell - tab_cell0][Mtab]
+    const float2 *w;        // coarse phases [cell - tab_cell0][Mtab]
+    int tab_cell0, Mtab;
+    int zld;                // row length of the split operand (elements) = 2 * Mpad
+    int n_items, total_ctas, total_tiles;
+    int tiles_n, F, Fv, Fa, na_c;
+    int fp16;
+    uint32_t idesc;
     int *status;
     uint64_t wait_limit;
-    uint32_t idesc;
+    TcItem it[TC_MAX_ITEMS];
 };
+
+// Item of a CTA / tile index: the last item whose prefix start is <= idx (items are few
+// and the scan is uniform across the CTA).
+__device__ __forceinline__ int find_item_cta(const TcBatch &b, int idx) {
+    int i = 0;
+    while (i + 1 < b.n_items && b.it[i + 1].cta0 <= idx) ++i;
+    return i;
+}
+__device__ __forceinline__ int find_item_tile(const TcBatch &b, int idx) {
+    int i = 0;
+    while (i + 1 < b.n_items && b.it[i + 1].tile0 <= idx) ++i;
+    return i;
+}
 
 // ----------------------------------------------------------------------- tcgen05 wrappers
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
@@ -164,39 +189,44 @@ __device__ __forceinline__ void st_global_v4(uint16_t *dst, uint32_t a, uint32_t
                  : "memory");
 }
 
-__global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const SplitParams p, uint16_t *__restrict__ Zhi,
+__global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_constant__ TcBatch B,
+                                                                uint16_t *__restrict__ Zhi,
                                                                 uint16_t *__restrict__ Zlo) {
-    // One CTA per (cell, 128-bin tile).  Lane l of warp w owns bin r = 8w + l/4 and the
-    // 8-pulse group g = l%4 of every 32-pulse stage: its gathers are 8-bin runs (whole
+    // One CTA per (item, cell, 128-bin tile).  Lane l of warp w owns bin r = 8w + l/4 and
+    // the 8-pulse group g = l%4 of every 32-pulse stage: its gathers are 8-bin runs (whole
     // sectors) and its stores complete 64-byte runs of the K-major output rows
     // (k' = (m/32)*64 + (re|im)*32 + m%32, hi and lo planes).  The cell's bins and phases
     // are staged in shared memory; the next stage's samples are requested before the
     // current stage is converted.
     __shared__ int s_rho[SP_TAB_MAX];
     __shared__ float2 s_w[SP_TAB_MAX];
-    const int mt = blockIdx.x % p.tiles_m;
-    const int cl = blockIdx.x / p.tiles_m;
+    const TcItem &p = B.it[find_item_cta(B, blockIdx.x)];
+    const int local = blockIdx.x - p.cta0;
+    const int mt = local % p.tiles_m;
+    const int cl = local / p.tiles_m;
+    const int c = p.cell0 + cl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = warp * 8 + (lane >> 2);
     const int g = lane & 3;
-    const bool fp16 = p.fp16 != 0;
+    const bool fp16 = B.fp16 != 0;
     const int j = mt * TC_BM + r;
     const bool jok = j < p.r0_count;
-    const long tab = (long)cl * p.M;
+    const long tab = (long)(c - B.tab_cell0) * B.Mtab;
+    const long ztab = (long)(c - B.tab_cell0) * p.M;     // cell offset inside Z (M pulses per cell)
     const int nbase = p.r0_begin + j;
     const bool tab_smem = !p.Z && p.M <= SP_TAB_MAX;
     if (tab_smem) {
         for (int m = tid; m < p.M; m += SP_THREADS) {
-            s_rho[m] = __ldg(p.rho + tab + m);
-            s_w[m] = __ldg(p.w + tab + m);
+            s_rho[m] = __ldg(B.rho + tab + m);
+            s_w[m] = __ldg(B.w + tab + m);
         }
         __syncthreads();
     }
-    const int *rho_t = tab_smem ? s_rho : p.rho + tab;
-    const float2 *w_t = tab_smem ? s_w : p.w + tab;
-    const size_t row = (size_t)cl * p.r0_pad + j;
-    uint16_t *zh = Zhi + row * (size_t)(TC_BK * p.KT) + g * 8;
-    uint16_t *zl = Zlo + row * (size_t)(TC_BK * p.KT) + g * 8;
+    const int *rho_t = tab_smem ? s_rho : B.rho + tab;
+    const float2 *w_t = tab_smem ? s_w : B.w + tab;
+    const size_t row = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j;
+    uint16_t *zh = Zhi + row * (size_t)B.zld + g * 8;
+    uint16_t *zl = Zlo + row * (size_t)B.zld + g * 8;
 
     auto load8 = [&](int kt, float2 (&v)[8]) {
 #pragma unroll
@@ -205,7 +235,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const SplitParam
             float2 x = make_float2(0.f, 0.f);
             if (m < p.M && jok) {
                 if (p.Z) {
-                    x = __ldg(p.Z + (tab + m) * p.r0_count + j);
+                    x = __ldg(p.Z + (ztab + m) * p.r0_count + j);
                 } else {
                     const int n = nbase + rho_t[m];
                     if ((unsigned)n < (unsigned)p.N) x = __ldg(p.echo + (long)m * p.N + n);
@@ -251,7 +281,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const SplitParam
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
             const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
-            const GemmParams p) {
+            const __grid_constant__ TcBatch B) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
@@ -291,23 +321,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_holder;
-    const uint64_t lim = p.wait_limit;
+    const uint64_t lim = B.wait_limit;
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer (A and B)
         if (lane == 0) {
             int it = 0;
             int last_it = -1;
-            for (int tile = blockIdx.x; tile < p.total_tiles && !abort_flag; tile += gridDim.x) {
-                const int nt = tile % p.tiles_n;
-                const int nt_m = tile / p.tiles_n;
+            for (int tile = blockIdx.x; tile < B.total_tiles && !abort_flag; tile += gridDim.x) {
+                const TcItem &p = B.it[find_item_tile(B, tile)];
+                const int local = tile - p.tile0;
+                const int nt = local % B.tiles_n;
+                const int nt_m = local / B.tiles_n;
                 const int mt = nt_m % p.tiles_m;
                 const int cl = nt_m / p.tiles_m;
-                const int arow = cl * p.r0_pad + mt * TC_BM;
+                const int arow = (int)(p.zrow0 + (long)cl * p.r0_pad + mt * TC_BM);
                 for (int kt = 0; kt < p.KT; ++kt, ++it) {
                     const int s = it % TC_STAGES;
                     if (!mbar_wait_backoff(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim, 32)) {
-                        latch_error(p.status, GRFT_ETIMEOUT);
+                        latch_error(B.status, GRFT_ETIMEOUT);
                         abort_flag = 1;
                         break;
                     }
@@ -331,20 +363,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             int it = 0, tcount = 0;
             bool issued_any = false;
-            for (int tile = blockIdx.x; tile < p.total_tiles && !abort_flag; tile += gridDim.x, ++tcount) {
+            for (int tile = blockIdx.x; tile < B.total_tiles && !abort_flag; tile += gridDim.x, ++tcount) {
                 const int b = tcount & 1;
+                const int KT = B.it[find_item_tile(B, tile)].KT;
                 if (!mbar_wait(&tmem_empty[b], ((tcount >> 1) & 1) ^ 1, lim)) {
-                    latch_error(p.status, GRFT_ETIMEOUT);
+                    latch_error(B.status, GRFT_ETIMEOUT);
                     abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_BN);
                 bool ok = true;
-                for (int kt = 0; kt < p.KT; ++kt, ++it) {
+                for (int kt = 0; kt < KT; ++kt, ++it) {
                     const int s = it % TC_STAGES;
                     if (!mbar_wait(&full[s], (it / TC_STAGES) & 1, lim)) {
-                        latch_error(p.status, GRFT_ETIMEOUT);
+                        latch_error(B.status, GRFT_ETIMEOUT);
                         abort_flag = 1;
                         ok = false;
                         break;
@@ -356,10 +389,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk) {
                         const uint32_t off = kk * 32;   // 16 elements x 2 bytes inside the swizzle row
-                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_hi + off), p.idesc,
+                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_hi + off), B.idesc,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_lo + off), p.idesc, 1u);
-                        umma_f16(d_tmem, umma_desc(a_lo + off), umma_desc(b_hi + off), p.idesc, 1u);
+                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_lo + off), B.idesc, 1u);
+                        umma_f16(d_tmem, umma_desc(a_lo + off), umma_desc(b_hi + off), B.idesc, 1u);
                     }
                     issued_any = true;
                     umma_commit(&empty[s]);
@@ -382,38 +415,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int q4 = warp & 3;
         const int r = q4 * 32 + lane;
         const int er = threadIdx.x - 64;         // 0..127 over the epilogue warps
-        const DsOut o = p.out;
-        const int na_full = o.na_c * o.Fa;
+        const int na_full = B.na_c * B.Fa;
         bool aborted = false;
         int tcount = 0;
-        for (int tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x, ++tcount) {
+        for (int tile = blockIdx.x; tile < B.total_tiles; tile += gridDim.x, ++tcount) {
             const int b = tcount & 1;
-            const int nt = tile % p.tiles_n;
-            const int nt_m = tile / p.tiles_n;
+            const TcItem &p = B.it[find_item_tile(B, tile)];
+            const int local = tile - p.tile0;
+            const int nt = local % B.tiles_n;
+            const int nt_m = local / B.tiles_n;
             const int mt = nt_m % p.tiles_m;
             const int cl = nt_m / p.tiles_m;
-            const int c = o.cell_begin + cl;
-            const int iv = c / o.na_c - o.i0, il = c % o.na_c;
+            const int c = p.cell0 + cl;
+            const int iv = c / B.na_c - p.i0, il = c % B.na_c;
             named_bar_sync(1, 128);                  // previous tile's offsets no longer read
             if (!aborted) {
                 const int f = nt * (TC_BN / 2) + er;
                 long off = -1;
-                if (f < p.F) {
-                    const int k = f / o.Fa, q = f % o.Fa;
-                    off = ((long)(iv * o.Fv + k) * na_full + (il * o.Fa + q)) * p.r0_count;
+                if (f < B.F) {
+                    const int k = f / B.Fa, q = f % B.Fa;
+                    off = ((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * p.r0_count;
                 }
                 s_rowoff[er] = off;
             }
             named_bar_sync(1, 128);
             if (aborted) continue;
-            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, p.status, 256)) {
+            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, B.status, 256)) {
                 aborted = true;
                 continue;
             }
             tc_fence_after();
             const int j = mt * TC_BM + r;
             const bool jok = j < p.r0_count;
-            const float2 e = (jok && o.Y) ? p.e0[j] : make_float2(1.f, 0.f);
+            float *const P = p.P;
+            float2 *const Y = p.Y;
+            const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
             const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * TC_BN);
 #pragma unroll 1
             for (int ch = 0; ch < TC_BN / 32; ++ch) {
@@ -427,8 +463,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (ro >= 0) {
                             const float yr = __uint_as_float(v[2 * pp]);
                             const float yi = __uint_as_float(v[2 * pp + 1]);
-                            if (o.P) __stcs(o.P + ro + j, yr * yr + yi * yi);
-                            if (o.Y) __stcs(o.Y + ro + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                            if (P) __stcs(P + ro + j, yr * yr + yi * yi);
+                            if (Y) __stcs(Y + ro + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
                         }
                     }
                 }
@@ -458,81 +494,114 @@ bool set_smem_attr(const void *fn, size_t bytes, int device, bool *done) {
 
 }  // namespace
 
-size_t ds_tc_split_plane_bytes_per_cell(int r0_count, int Mpad) {
-    const size_t r0_pad = (size_t)(r0_count + TC_BM - 1) / TC_BM * TC_BM;
-    return r0_pad * 2 * (size_t)Mpad * sizeof(uint16_t);
-}
+int ds_tc_r0_pad(int r0_count) { return (r0_count + TC_BM - 1) / TC_BM * TC_BM; }
 
-int launch_ds_tc(const Ctx &c, const RadarD &R, const float2 *echo, const float2 *Z,
-                 const grft_dsgrid &g, int cell_count, const int32_t *rho, const float2 *w,
-                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, bool fp16, const float2 *e0,
-                 const DsOut &out, uint16_t *Zhi, uint16_t *Zlo, int chunk_cells) {
-    if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
-    if (chunk_cells < 1) return GRFT_EINVAL;
-    const int F = g.Fv * g.Fa;
-    const int Fpad = (F + 127) / 128 * 128;
-    const int tiles_m = (g.r0_count + TC_BM - 1) / TC_BM;
-    const int r0_pad = tiles_m * TC_BM;
+namespace {
+
+// Launch one round: the split kernel over every (item, cell, bin tile) of the batch, then
+// the persistent GEMM over every (item, cell, bin tile, hypothesis tile).
+int launch_round(const Ctx &c, TcBatch &b, long rows_used, int Mpad, int Fpad, const uint16_t *Bhi,
+                 const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo) {
+    if (b.n_items == 0) return GRFT_OK;
     const uint64_t kdim = 2ull * Mpad;
-    static bool attr_gemm[64] = {false};
-    if (!set_smem_attr((const void *)k_ds_tc, TC_SMEM_BYTES, c.device, attr_gemm)) return GRFT_ECUDA;
-    CUtensorMap mbh, mbl;
-    if (!encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
+    CUtensorMap mzh, mzl, mbh, mbl;
+    if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)rows_used,
+                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)rows_used,
+                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
                        TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2,
                        TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
         return GRFT_ECUDA;
-    const uint32_t fmt = fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
-    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                           ((uint32_t)(TC_BM >> 4) << 24);
-    for (int c0 = 0; c0 < cell_count; c0 += chunk_cells) {
-        const int cc = cell_count - c0 < chunk_cells ? cell_count - c0 : chunk_cells;
-        CUtensorMap mzh, mzl;
-        const uint64_t rows = (uint64_t)cc * r0_pad;
-        if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, rows, kdim * 2, TC_BK,
-                           TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, rows, kdim * 2, TC_BK,
-                           TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
-            return GRFT_ECUDA;
-        SplitParams sp;
-        sp.echo = echo;
-        sp.Z = Z ? Z + (size_t)c0 * R.M * g.r0_count : nullptr;
-        sp.rho = rho + (size_t)c0 * R.M;
-        sp.w = w + (size_t)c0 * R.M;
-        sp.M = R.M;
-        sp.N = R.N;
-        sp.KT = Mpad / 32;
-        sp.r0_begin = g.r0_begin;
-        sp.r0_count = g.r0_count;
-        sp.tiles_m = tiles_m;
-        sp.r0_pad = r0_pad;
-        sp.fp16 = fp16 ? 1 : 0;
-        k_coarse_split<<<cc * tiles_m, SP_THREADS, 0, c.stream>>>(sp, Zhi, Zlo);
-        int e = check_launch();
-        if (e) return e;
+    k_coarse_split<<<b.total_ctas, SP_THREADS, 0, c.stream>>>(b, Zhi, Zlo);
+    int e = check_launch();
+    if (e) return e;
+    const int grid = b.total_tiles < c.num_sms ? b.total_tiles : c.num_sms;
+    k_ds_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, c.stream>>>(mzh, mzl, mbh, mbl, b);
+    return check_launch();
+}
 
-        GemmParams p;
-        p.e0 = e0;
-        p.KT = Mpad / 32;
-        p.tiles_m = tiles_m;
-        p.tiles_n = Fpad / 128;
-        p.r0_pad = r0_pad;
-        p.r0_count = g.r0_count;
-        p.F = F;
-        const long total = (long)cc * tiles_m * p.tiles_n;
-        if (total > 0x7fffffffL) return GRFT_EINVAL;
-        p.total_tiles = (int)total;
-        p.out = out;
-        p.out.cell_begin = out.cell_begin + c0;
-        p.status = c.status;
-        p.wait_limit = c.wait_limit;
-        p.idesc = idesc;
-        const int grid = (int)(total < c.num_sms ? total : c.num_sms);
-        k_ds_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, c.stream>>>(mzh, mzl, mbh, mbl, p);
-        e = check_launch();
-        if (e) return e;
+}  // namespace
+
+int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
+                 const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
+                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *Zhi, uint16_t *Zlo, long z_rows_cap) {
+    static bool attr_gemm[64] = {false};
+    if (!set_smem_attr((const void *)k_ds_tc, TC_SMEM_BYTES, c.device, attr_gemm)) return GRFT_ECUDA;
+    const int F = g.Fv * g.Fa;
+    const int Fpad = (F + 127) / 128 * 128;
+    TcBatch b;
+    b.rho = rho;
+    b.w = w;
+    b.tab_cell0 = tab_cell0;
+    b.Mtab = Mtab;
+    b.zld = 2 * Mpad;
+    b.tiles_n = Fpad / 128;
+    b.F = F;
+    b.Fv = g.Fv;
+    b.Fa = g.Fa;
+    b.na_c = g.ac.count;
+    b.fp16 = fp16 ? 1 : 0;
+    const uint32_t fmt = fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
+    b.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+              ((uint32_t)(TC_BM >> 4) << 24);
+    b.status = c.status;
+    b.wait_limit = c.wait_limit;
+    auto reset = [&]() {
+        b.n_items = 0;
+        b.total_ctas = 0;
+        b.total_tiles = 0;
+    };
+    reset();
+    long rows_used = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const DsTcItem &d = items[i];
+        if (d.cell_count <= 0 || d.r0_count <= 0) continue;
+        const int tiles_m = (d.r0_count + TC_BM - 1) / TC_BM;
+        const int r0_pad = tiles_m * TC_BM;
+        if (r0_pad > z_rows_cap || d.M > Mtab || (d.M + 31) / 32 * 32 > Mpad) return GRFT_EINVAL;
+        int cell = d.cell_begin;
+        const int cell_end = d.cell_begin + d.cell_count;
+        while (cell < cell_end) {
+            long fit = (z_rows_cap - rows_used) / r0_pad;
+            if (fit <= 0 || b.n_items == TC_MAX_ITEMS) {
+                int e = launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo);
+                if (e) return e;
+                reset();
+                rows_used = 0;
+                continue;
+            }
+            const int take = (int)(fit < cell_end - cell ? fit : cell_end - cell);
+            const long ctas = (long)take * tiles_m;
+            const long tiles = ctas * b.tiles_n;
+            if ((long)b.total_tiles + tiles > 0x7fffffffL) return GRFT_EINVAL;
+            TcItem &t = b.it[b.n_items++];
+            t.echo = d.echo;
+            t.Z = d.Z;
+            t.P = d.P;
+            t.Y = d.Y;
+            t.e0 = d.e0;
+            t.M = d.M;
+            t.N = d.N;
+            t.KT = (d.M + 31) / 32;
+            t.r0_begin = d.r0_begin;
+            t.r0_count = d.r0_count;
+            t.tiles_m = tiles_m;
+            t.r0_pad = r0_pad;
+            t.cell0 = cell;
+            t.ncell = take;
+            t.i0 = d.i0;
+            t.zrow0 = rows_used;
+            t.cta0 = b.total_ctas;
+            t.tile0 = b.total_tiles;
+            b.total_ctas += (int)ctas;
+            b.total_tiles += (int)tiles;
+            rows_used += (long)take * r0_pad;
+            cell += take;
+        }
     }
-    return GRFT_OK;
+    return launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo);
 }
 
 }  // namespace grft

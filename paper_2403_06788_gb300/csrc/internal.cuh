@@ -114,13 +114,23 @@ int launch_ds_simt(const Ctx &, const RadarD &, const float2 *echo, const float2
                    const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
                    const float2 *D, const float2 *e0, const DsOut &out);
 
-// Split coarse-RM pre-pass + tensor-core contraction, in chunks of `chunk_cells` cells whose
-// split operand (two planes of ds_tc_split_plane_bytes_per_cell each per cell) lives in Zhi/Zlo.
-size_t ds_tc_split_plane_bytes_per_cell(int r0_count, int Mpad);
-int launch_ds_tc(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
-                 const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
-                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, bool fp16,
-                 const float2 *e0, const DsOut &out, uint16_t *Zhi, uint16_t *Zlo, int chunk_cells);
+// One CPI (or one call's cell range) for the tensor-core DS path.
+struct DsTcItem {
+    const float2 *echo;      // [M][N] (or nullptr when Z is given)
+    const float2 *Z;         // [cells][M][r0_count] materialised coarse-RM output, or nullptr
+    float *P;                // outputs, canonical v-slab layout (either may be null)
+    float2 *Y;
+    const float2 *e0;        // e0[j] = range phase of bin r0_begin + j
+    int M, N, r0_begin, r0_count;
+    int cell_begin, cell_count, i0;
+};
+int ds_tc_r0_pad(int r0_count);
+// Split coarse-RM pre-pass + tensor-core contraction for a list of items, in rounds whose
+// split operand (z_rows_cap rows of 2*Mpad 16-bit values per plane) fits Zhi/Zlo.  Tables
+// rho/w are indexed [cell - tab_cell0][Mtab]; B planes are [2 Fpad][2 Mpad].
+int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
+                 const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
+                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *Zhi, uint16_t *Zlo, long z_rows_cap);
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);
