@@ -96,18 +96,18 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
         for (int j = nb - G - T; j <= nb - G - 1; ++j) L += SV(j);
         for (int j = nb + G + 1; j <= nb + G + T; ++j) Rr += SV(j);
     }
+    // threshold test of the 16 bins (hot, unrolled): a bit per passing bin
+    unsigned pmask = 0;
 #pragma unroll
     for (int q = 0; q < CF_PER; ++q) {
         const int n = nb + q;
-        const bool valid = n < nr0;      // no early exit: every lane reaches the ballot below
         if (q > 0 && cp.mode == 0) {
             L += SV(n - G - 1) - SV(n - G - T - 1);
             Rr += SV(n + G + T) - SV(n + G);
         }
         const float p = x[q];
-        bool pass = false;
-        if (!valid) {
-        } else if (cp.mode == 0) {
+        bool pass;
+        if (cp.mode == 0) {
             if (interior) {
                 pass = p > alpha_in * (L + Rr);
             } else {
@@ -117,38 +117,166 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
         } else {
             pass = p > cp.fixed;
         }
-        if (pass) {
-            const long me = row * nr0 + n;
-            for (int dv = -1; dv <= 1 && pass; ++dv)
-                for (int da = -1; da <= 1 && pass; ++da)
-                    for (int dn = -1; dn <= 1 && pass; ++dn) {
-                        if (!dv && !da && !dn) continue;
-                        const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
-                        if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
-                        const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
-                        const float po = (dv == 0 && da == 0) ? SV(n2) : __ldg(P + o);
-                        if (po > p || (po == p && o < me)) pass = false;
-                    }
-        }
-        // warp-aggregated append
-        const unsigned ballot = __ballot_sync(0xffffffffu, pass);
-        if (ballot) {
-            const int lane = threadIdx.x & 31;
-            int base = 0;
-            if (lane == __ffs(ballot) - 1) base = atomicAdd(count, __popc(ballot));
-            base = __shfl_sync(0xffffffffu, base, __ffs(ballot) - 1);
+        if (pass && n < nr0) pmask |= 1u << q;
+    }
+    // local-maximum test and append (rare, compact): only warps with a candidate enter,
+    // and every lane of such a warp runs all 16 iterations so the ballot is convergent
+    if (__any_sync(0xffffffffu, pmask != 0)) {
+#pragma unroll 1
+        for (int q = 0; q < CF_PER; ++q) {
+            const int n = nb + q;
+            bool pass = (pmask >> q) & 1u;
+            float p = 0.f;
             if (pass) {
-                const long pos = (long)base + __popc(ballot & ((1u << lane) - 1));
-                if (pos < CAND_CAP) {
-                    cand_p[pos] = p;
-                    cand_i[pos] = row * nr0 + n;
-                } else {
-                    latch_error(status, GRFT_EOVERFLOW);
+                p = SV(n);
+                const long me = row * nr0 + n;
+                for (int dv = -1; dv <= 1 && pass; ++dv)
+                    for (int da = -1; da <= 1 && pass; ++da)
+                        for (int dn = -1; dn <= 1 && pass; ++dn) {
+                            if (!dv && !da && !dn) continue;
+                            const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
+                            if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
+                            const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
+                            const float po = (dv == 0 && da == 0) ? SV(n2) : __ldg(P + o);
+                            if (po > p || (po == p && o < me)) pass = false;
+                        }
+            }
+            // warp-aggregated append
+            const unsigned ballot = __ballot_sync(0xffffffffu, pass);
+            if (ballot) {
+                const int lane = threadIdx.x & 31;
+                int base = 0;
+                if (lane == __ffs(ballot) - 1) base = atomicAdd(count, __popc(ballot));
+                base = __shfl_sync(0xffffffffu, base, __ffs(ballot) - 1);
+                if (pass) {
+                    const long pos = (long)base + __popc(ballot & ((1u << lane) - 1));
+                    if (pos < CAND_CAP) {
+                        cand_p[pos] = p;
+                        cand_i[pos] = row * nr0 + n;
+                    } else {
+                        latch_error(status, GRFT_EOVERFLOW);
+                    }
                 }
             }
         }
     }
 #undef SV
+}
+
+// Specialisation for compile-time guard/train counts (the default 2/16): the positions
+// read around the thread's 16 bins are known at compile time, so reads inside the thread's
+// own bins come from registers and the others use immediate shared-memory offsets.
+template <int G, int T>
+__global__ __launch_bounds__(CF_THREADS, 4) void k_cfar_fixed(const float *__restrict__ P, CfarParams cp,
+                                                           int nseg, int *__restrict__ count,
+                                                           float *__restrict__ cand_p,
+                                                           int64_t *__restrict__ cand_i, int *status) {
+    static_assert(G + T + 1 <= CF_MAXHALO && CF_MAXHALO % 16 == 0, "halo");
+    constexpr int HALO = G + T + 1;
+    __shared__ float sv[CF_STAGE + CF_STAGE / 16 + 1];
+    const long row = blockIdx.x / nseg;
+    const int seg0 = (int)(blockIdx.x % nseg) * CF_SEG;
+    const int nr0 = cp.nr0;
+    const float *prow = P + row * nr0;
+    const int nb = seg0 + threadIdx.x * CF_PER;
+    const int sb = CF_MAXHALO - seg0;
+    float x[CF_PER];
+    const bool vec = ((((uintptr_t)(prow + nb)) & 15) == 0) && nb + CF_PER <= nr0;
+    if (vec) {
+        const float4 *src = reinterpret_cast<const float4 *>(prow + nb);
+#pragma unroll
+        for (int q = 0; q < CF_PER / 4; ++q) {
+            const float4 t = __ldcs(src + q);
+            x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CF_PER; ++q) x[q] = (nb + q < nr0) ? __ldcs(prow + nb + q) : 0.f;
+    }
+    float hl = 0.f, hr = 0.f;
+    if (threadIdx.x < HALO) {
+        const int nl = seg0 - HALO + threadIdx.x, nrr = seg0 + CF_SEG + threadIdx.x;
+        hl = (nl >= 0 && nl < nr0) ? __ldg(prow + nl) : 0.f;
+        hr = (nrr < nr0) ? __ldg(prow + nrr) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < CF_PER; ++q) sv[cf_slot(nb + q + sb)] = x[q];
+    if (threadIdx.x < HALO) {
+        sv[cf_slot(CF_MAXHALO - HALO + threadIdx.x)] = hl;
+        sv[cf_slot(CF_MAXHALO + CF_SEG + threadIdx.x)] = hr;
+    }
+    __syncthreads();
+    // staged position of bin nb + c is 16 (threadIdx.x + CF_MAXHALO/16) + c
+    const float *base = sv + 17 * (threadIdx.x + CF_MAXHALO / 16);
+    auto at = [&](int c) -> float {   // value of bin nb + c (c compile-time after unrolling)
+        return (c >= 0 && c < CF_PER) ? x[c < 0 ? 0 : (c >= CF_PER ? CF_PER - 1 : c)]
+                                      : base[c + (c >> 4)];
+    };
+
+    const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
+    const bool interior = nb - G - T >= 0 && nb + CF_PER - 1 + G + T < nr0;
+    const float alpha_in = cp.alpha[2 * T];
+    float L = 0.f, Rr = 0.f;
+#pragma unroll
+    for (int c = -G - T; c <= -G - 1; ++c) L += at(c);
+#pragma unroll
+    for (int c = G + 1; c <= G + T; ++c) Rr += at(c);
+    unsigned pmask = 0;
+#pragma unroll
+    for (int q = 0; q < CF_PER; ++q) {
+        const int n = nb + q;
+        if (q > 0) {
+            L += at(q - G - 1) - at(q - G - T - 1);
+            Rr += at(q + G + T) - at(q + G);
+        }
+        const float p = x[q];
+        bool pass;
+        if (interior) {
+            pass = p > alpha_in * (L + Rr);
+        } else {
+            const int nt = window_count(n - G - T, n - G - 1, nr0) + window_count(n + G + 1, n + G + T, nr0);
+            pass = nt > 0 && p > cp.alpha[nt] * (L + Rr);
+        }
+        if (pass && n < nr0) pmask |= 1u << q;
+    }
+    if (__any_sync(0xffffffffu, pmask != 0)) {
+#pragma unroll 1
+        for (int q = 0; q < CF_PER; ++q) {
+            const int n = nb + q;
+            bool pass = (pmask >> q) & 1u;
+            float p = 0.f;
+            if (pass) {
+                p = sv[cf_slot(n + sb)];
+                const long me = row * nr0 + n;
+                for (int dv = -1; dv <= 1 && pass; ++dv)
+                    for (int da = -1; da <= 1 && pass; ++da)
+                        for (int dn = -1; dn <= 1 && pass; ++dn) {
+                            if (!dv && !da && !dn) continue;
+                            const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
+                            if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
+                            const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
+                            const float po = (dv == 0 && da == 0) ? sv[cf_slot(n2 + sb)] : __ldg(P + o);
+                            if (po > p || (po == p && o < me)) pass = false;
+                        }
+            }
+            const unsigned ballot = __ballot_sync(0xffffffffu, pass);
+            if (ballot) {
+                const int lane = threadIdx.x & 31;
+                int b0 = 0;
+                if (lane == __ffs(ballot) - 1) b0 = atomicAdd(count, __popc(ballot));
+                b0 = __shfl_sync(0xffffffffu, b0, __ffs(ballot) - 1);
+                if (pass) {
+                    const long pos = (long)b0 + __popc(ballot & ((1u << lane) - 1));
+                    if (pos < CAND_CAP) {
+                        cand_p[pos] = p;
+                        cand_i[pos] = row * nr0 + n;
+                    } else {
+                        latch_error(status, GRFT_EOVERFLOW);
+                    }
+                }
+            }
+        }
+    }
 }
 
 // (p, idx) ordering: larger p first, then smaller idx.
@@ -305,8 +433,12 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
     const long rows = (long)nv * na;
     const int nseg = (nr0 + CF_SEG - 1) / CF_SEG;
     if (rows > 0 && nr0 > 0) {
-        k_cfar<<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p, cand_i,
-                                                                    c.status);
+        if (cfar.mode == 0 && cfar.guard == 2 && cfar.train == 16)
+            k_cfar_fixed<2, 16><<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p,
+                                                                                    cand_i, c.status);
+        else
+            k_cfar<<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p, cand_i,
+                                                                        c.status);
         int e = check_launch();
         if (e) return e;
     }

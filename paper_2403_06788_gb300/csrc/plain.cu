@@ -1,7 +1,8 @@
 // Plain (single-scale) TD-GRFT (Sec. III-A, eq. standard-GRFT-TD; Table III row TD-GRFT):
 //   Y[h][n0] = e0(n0) * sum_m s[m][n0 + rho_h(m)] * w_h(m)
 // FP32 SIMT.  A CTA owns a group of PL_H hypotheses and a tile of PL_THREADS*PL_J range
-// bins; each thread accumulates PL_J consecutive bins for all PL_H hypotheses.  Bins and
+// bins; each thread accumulates PL_J bins (32 apart, so warp accesses are contiguous) for
+// all PL_H hypotheses.  Bins and
 // phases come from a per-chunk table (FP64-built).  Consecutive hypotheses of a group are
 // neighbouring accelerations, whose bin shift is nearly always the same at a given pulse:
 // the echo samples are reloaded only when the (CTA-uniform) shift changes, so the inner
@@ -29,7 +30,9 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
 
     const int h0 = blockIdx.y * PL_H;
     const int nhl = min(PL_H, nh - h0);
-    const int j0 = blockIdx.x * PL_TILE + threadIdx.x * PL_J;   // local r0 index
+    // bins of this thread: j0 + 32 q, q = 0..PL_J-1 (a warp covers 128 consecutive bins, so
+    // every load and store instruction of the warp is one contiguous 256-byte run)
+    const int j0 = blockIdx.x * PL_TILE + (threadIdx.x >> 5) * (32 * PL_J) + (threadIdx.x & 31);
     const int n0 = r0_begin + j0;
 
     float2 acc[PL_H][PL_J];
@@ -49,28 +52,33 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
             s_w[mm][h] = ok ? w_tab[o] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // The samples of pulse mm+1 at the first hypothesis' shift are requested before
-        // pulse mm is accumulated, hiding the L2 latency of the gather.
         auto load_row = [&](int mm, int r, float2 (&v)[PL_J]) {
             const float2 *row = echo + (long)(mc + mm) * N;
             const int base = n0 + r;
 #pragma unroll
             for (int j = 0; j < PL_J; ++j) {
-                const int n = base + j;
+                const int n = base + 32 * j;
                 v[j] = ((unsigned)n < (unsigned)N) ? __ldg(row + n) : make_float2(0.f, 0.f);
             }
         };
-        int pre_r = s_rho[0][0];
-        float2 pre[PL_J];
-        load_row(0, pre_r, pre);
+        // two pulses of look-ahead: the samples of pulses mm+1 and mm+2 (at the first
+        // hypothesis' shift) are in flight while pulse mm is accumulated
+        int r1 = s_rho[0][0], r2 = mn > 1 ? s_rho[1][0] : 0;
+        float2 pre1[PL_J], pre2[PL_J];
+        load_row(0, r1, pre1);
+        if (mn > 1) load_row(1, r2, pre2);
         for (int mm = 0; mm < mn; ++mm) {
-            int prev = pre_r;
+            int prev = r1;
             float2 sv[PL_J];
 #pragma unroll
-            for (int j = 0; j < PL_J; ++j) sv[j] = pre[j];
-            if (mm + 1 < mn) {
-                pre_r = s_rho[mm + 1][0];
-                load_row(mm + 1, pre_r, pre);
+            for (int j = 0; j < PL_J; ++j) {
+                sv[j] = pre1[j];
+                pre1[j] = pre2[j];
+            }
+            r1 = r2;
+            if (mm + 2 < mn) {
+                r2 = s_rho[mm + 2][0];
+                load_row(mm + 2, r2, pre2);
             }
 #pragma unroll
             for (int h = 0; h < PL_H; ++h) {
@@ -91,7 +99,7 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
 
 #pragma unroll
     for (int j = 0; j < PL_J; ++j) {
-        const int jj = j0 + j;
+        const int jj = j0 + 32 * j;
         if (jj >= r0_count) break;
         const float2 e = e0[jj];
 #pragma unroll
