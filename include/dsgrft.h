@@ -118,6 +118,11 @@ int grft_set_wait_limit(uint64_t cycles);
 /* Free this device's cached workspace (the next call reallocates it). */
 int grft_release_workspace(void);
 
+/* Failure-path self test: one CTA waits on a barrier that nothing completes, for `cycles`
+ * SM cycles (0 = the current wait limit), then latches GRFT_ETIMEOUT and returns; read it
+ * with grft_sync_status().  The context stays usable. */
+int grft_selftest_wait(uint64_t cycles, void *stream);
+
 /* ---------------------------------------------------------------- the hot path */
 
 /* Trajectory tables (eq. standard-GRFT-TD's n(c,t_m); eqs. H-DFM / pre-DFM phases).

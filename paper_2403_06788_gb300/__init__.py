@@ -19,6 +19,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
+           "grft_selftest_wait",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
@@ -93,6 +94,10 @@ def grft_set_wait_limit(cycles: int) -> None:
 
 def grft_release_workspace() -> None:
     check(load().grft_release_workspace(), "grft_release_workspace")
+
+
+def grft_selftest_wait(cycles: int, stream=None) -> None:
+    check(load().grft_selftest_wait(int(cycles), _stream(stream)), "grft_selftest_wait")
 
 
 def grft_bins_phases(radar, v, a, rho, w, stream=None):

@@ -62,6 +62,7 @@ SIGNATURES = {
     "grft_sync_status": (C.c_int, [_P]),
     "grft_set_wait_limit": (C.c_int, [C.c_uint64]),
     "grft_release_workspace": (C.c_int, []),
+    "grft_selftest_wait": (C.c_int, [C.c_uint64, _P]),
     "grft_bins_phases": (C.c_int, [C.POINTER(grft_radar), _P, _P, C.c_int32, _P, _P, _P]),
     "grft_plain": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),
     "grft_plain_static": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),

@@ -5,8 +5,9 @@
 //   Y = sum_m s~ exp(j 4 pi r_m / lambda),  P = |Y|^2
 //   dY/dth_j = sum_m [ (ds~/dx)(dr/dth_j)/dr + j (4 pi/lambda)(dr/dth_j) s~ ] exp(j4pi r_m/lambda)
 //   dP/dth_j = 2 Re(conj(Y) dY/dth_j);  grad_s[m][n] += gP * 2 Y conj(weight * exp(...))
-// Ranges, bins and phases are recomputed in FP64 per pulse (never stored); the sums are
-// FP32.  One CTA per trajectory: a strided loop over pulses, then a block reduction.
+// Ranges, bins and phases are recomputed in FP64 per pulse (never stored); the per-pulse
+// terms are FP32 and their sums are accumulated in FP64 (a few thousand additions per
+// trajectory).  One CTA per trajectory: a strided loop over pulses, then a block reduction.
 #include "internal.cuh"
 
 namespace grft {
@@ -16,7 +17,10 @@ namespace {
 constexpr int AD_THREADS = 256;
 
 struct Sums {
-    float v[8];   // Y.re, Y.im, dY0.re, dY0.im, dY1.re, dY1.im, dY2.re, dY2.im
+    // Y.re, Y.im, dY0.re, dY0.im, dY1.re, dY1.im, dY2.re, dY2.im, accumulated in FP64.
+    // dY0 omits the term j (4 pi/lambda) Y of dY/dr0: Re(conj(Y) j c Y) = 0 exactly, and in
+    // finite precision that large term would swamp the small real part that remains.
+    double v[8];
 };
 
 __device__ __forceinline__ float2 echo_at(const float2 *__restrict__ s, int N, int m, long n) {
@@ -28,7 +32,7 @@ __device__ Sums traj_partial(const RadarD &R, const float2 *__restrict__ s, cons
                              int gather) {
     Sums acc;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc.v[i] = 0.f;
+    for (int i = 0; i < 8; ++i) acc.v[i] = 0.0;
     const float k4 = (float)(4.0 * 3.141592653589793 / R.lambda);
     const float inv_dr = (float)(1.0 / R.dr);
     for (int m = threadIdx.x; m < R.M; m += blockDim.x) {
@@ -53,7 +57,7 @@ __device__ Sums traj_partial(const RadarD &R, const float2 *__restrict__ s, cons
         const float drdth[3] = {1.f, tf, 0.5f * tf * tf};
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const float c = drdth[j] * inv_dr, q = k4 * drdth[j];
+            const float c = drdth[j] * inv_dr, q = j == 0 ? 0.f : k4 * drdth[j];
             const float2 term = make_float2(ds.x * c - q * st.y, ds.y * c + q * st.x);
             const float2 tw = cmul(term, w);
             acc.v[2 + 2 * j] += tw.x;
@@ -65,11 +69,11 @@ __device__ Sums traj_partial(const RadarD &R, const float2 *__restrict__ s, cons
 
 // Block-wide sum of the 8 partials; every thread gets the total.
 __device__ Sums block_sum(Sums a) {
-    __shared__ float red[AD_THREADS / 32][8];
-    __shared__ float tot[8];
+    __shared__ double red[AD_THREADS / 32][8];
+    __shared__ double tot[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float x = a.v[i];
+        double x = a.v[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         a.v[i] = x;
@@ -80,7 +84,7 @@ __device__ Sums block_sum(Sums a) {
         for (int i = 0; i < 8; ++i) red[w][i] = a.v[i];
     __syncthreads();
     if (threadIdx.x < 8) {
-        float x = 0.f;
+        double x = 0.0;
         for (int q = 0; q < (int)(blockDim.x / 32); ++q) x += red[q][threadIdx.x];
         tot[threadIdx.x] = x;
     }
@@ -92,10 +96,10 @@ __device__ Sums block_sum(Sums a) {
     return r;
 }
 
-__device__ __forceinline__ void power_and_grad(const Sums &S, float &P, double g[3]) {
+__device__ __forceinline__ void power_and_grad(const Sums &S, double &P, double g[3]) {
     P = S.v[0] * S.v[0] + S.v[1] * S.v[1];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) g[j] = 2.0 * ((double)S.v[0] * S.v[2 + 2 * j] + (double)S.v[1] * S.v[3 + 2 * j]);
+    for (int j = 0; j < 3; ++j) g[j] = 2.0 * (S.v[0] * S.v[2 + 2 * j] + S.v[1] * S.v[3 + 2 * j]);
 }
 
 __global__ __launch_bounds__(AD_THREADS) void k_backward(RadarD R, const float2 *__restrict__ s,
@@ -108,16 +112,16 @@ __global__ __launch_bounds__(AD_THREADS) void k_backward(RadarD R, const float2 
     const Sums S = block_sum(traj_partial(R, s, th, gather));
     const float scale = gP ? gP[k] : 1.f;
     if (threadIdx.x == 0) {
-        float p;
+        double p;
         double gr[3];
         power_and_grad(S, p, gr);
-        if (P) P[k] = p;
-        if (Y) Y[k] = make_float2(S.v[0], S.v[1]);
+        if (P) P[k] = (float)p;
+        if (Y) Y[k] = make_float2((float)S.v[0], (float)S.v[1]);
         if (g)
             for (int j = 0; j < 3; ++j) g[3 * k + j] = scale * gr[j];
     }
     if (!grad_s) return;
-    const float2 Yk = make_float2(S.v[0], S.v[1]);
+    const float2 Yk = make_float2((float)S.v[0], (float)S.v[1]);
     for (int m = threadIdx.x; m < R.M; m += blockDim.x) {
         const double t = slow_time(m, R.prf);
         const double r = __dadd_rn(th[0], displacement(th[1], th[2], t));
@@ -157,7 +161,7 @@ __global__ __launch_bounds__(AD_THREADS) void k_refine(RadarD R, const float2 *_
     const int k = blockIdx.x;
     const double cell[3] = {c0, c1, c2};
     double th[3] = {theta[3 * k], theta[3 * k + 1], theta[3 * k + 2]};
-    float P;
+    double P;
     double g[3];
     power_and_grad(block_sum(traj_partial(R, s, th, gather)), P, g);
     double gmax = 0.0;
@@ -167,7 +171,7 @@ __global__ __launch_bounds__(AD_THREADS) void k_refine(RadarD R, const float2 *_
         for (int it = 0; it < steps; ++it) {
             double tn[3];
             for (int j = 0; j < 3; ++j) tn[j] = th[j] + eta * cell[j] * cell[j] * g[j];
-            float Pn;
+            double Pn;
             double gn[3];
             power_and_grad(block_sum(traj_partial(R, s, tn, gather)), Pn, gn);
             if (Pn >= P) {       // block-uniform decision (every thread holds the same sums)
@@ -183,7 +187,7 @@ __global__ __launch_bounds__(AD_THREADS) void k_refine(RadarD R, const float2 *_
     }
     if (threadIdx.x == 0) {
         for (int j = 0; j < 3; ++j) theta[3 * k + j] = th[j];
-        P_out[k] = P;
+        P_out[k] = (float)P;
     }
 }
 

@@ -140,11 +140,35 @@ bool encode_tma_2d(CUtensorMap *map, CUtensorMapDataType dtype, void *base, uint
     return r == CUDA_SUCCESS;
 }
 
+namespace {
+
+// Waits on an mbarrier phase that nothing completes, bounded by `limit` SM cycles: the
+// timeout path of every warp-specialised kernel, exercised without any copy or MMA in flight.
+__global__ void k_selftest_wait(int *status, uint64_t limit) {
+    __shared__ alignas(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) latch_error(status, GRFT_ETIMEOUT);
+}
+
+}  // namespace
+
 }  // namespace grft
 
 using namespace grft;
 
 extern "C" {
+
+int grft_selftest_wait(uint64_t cycles, void *stream) {
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    k_selftest_wait<<<1, 32, 0, c.stream>>>(c.status, cycles ? cycles : c.wait_limit);
+    return check_launch();
+}
 
 int grft_version(void) { return GRFT_ABI_VERSION; }
 

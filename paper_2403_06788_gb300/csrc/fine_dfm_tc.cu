@@ -30,6 +30,13 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -38,16 +45,15 @@ namespace grft {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BN = 256;                     // real columns per tile
 constexpr int TC_BK = 64;                      // real k per stage (32 pulses x re/im)
-constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * 128;   // 16 KB per plane
-constexpr uint32_t TC_B_BYTES = TC_BN * 128;   // 32 KB per plane
-constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
-constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unwind path
-constexpr size_t TC_SMEM_BYTES = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+// Tile-shape variants of kernel b (chosen per problem shape by the autotuner):
+// BN real columns per tile (BN/2 fine hypotheses) and ST pipeline stages.
+constexpr size_t tc_smem_bytes(int BN, int ST) {
+    return (size_t)ST * (2 * TC_A_BYTES + 2 * (size_t)BN * 128) + 1024;
+}
 
 constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
 constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
@@ -278,10 +284,17 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
 }
 
 // =========================================================================== kernel b
+template <int BN, int ST>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
             const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
             const __grid_constant__ TcBatch B) {
+    constexpr int TC_BN = BN;                          // real columns per tile
+    constexpr int TC_STAGES = ST;
+    constexpr uint32_t TC_B_BYTES = BN * 128;          // per plane
+    constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+    constexpr uint32_t TC_TMEM_COLS = 2 * BN;          // two accumulators
+    static_assert(BN % 32 == 0 && BN <= 256 && TC_TMEM_COLS >= 32, "tile");
     extern __shared__ unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
@@ -500,26 +513,153 @@ namespace {
 
 // Launch one round: the split kernel over every (item, cell, bin tile) of the batch, then
 // the persistent GEMM over every (item, cell, bin tile, hypothesis tile).
+// ------------------------------------------------------------------------ autotuner
+// Tile-shape choice per problem bucket (Mpad, Fpad, largest r0 tile count rounded up to a
+// power of two, FP16 or BF16): the first uncaptured call of a bucket times every variant
+// of kernel b on its first round (the split operand is already in place and kernel b is
+// idempotent, so the timed reruns change nothing) and keeps the fastest.  The choice is
+// cached per process and, if DSGRFT_TUNE_CACHE names a file, appended to it as JSON lines
+// {"Mpad":..,"Fpad":..,"r0":..,"fp16":..,"variant":..} that later processes read back.
+// DSGRFT_AUTOTUNE=0 disables timing (the default variant is used); DSGRFT_TILE_VARIANT=v
+// forces variant v.  Variants give
+// bit-identical results: only the N tiling changes, not the order of the K accumulation.
+constexpr int TC_VARIANTS = 2;     // 0: BN 256, 2 stages; 1: BN 128, 3 stages
+using TuneKey = std::tuple<int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+bool g_tune_loaded = false;
+
+const char *tune_path() {
+    const char *p = getenv("DSGRFT_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+bool tune_enabled() {
+    const char *p = getenv("DSGRFT_AUTOTUNE");
+    return !(p && p[0] == '0');
+}
+int json_int(const char *line, const char *key) {
+    const char *q = strstr(line, key);
+    return q ? atoi(q + strlen(key)) : -1;
+}
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = tune_path();
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        const int a = json_int(line, "\"Mpad\":"), b = json_int(line, "\"Fpad\":");
+        const int r = json_int(line, "\"r0\":"), h = json_int(line, "\"fp16\":");
+        const int v = json_int(line, "\"variant\":");
+        if (a > 0 && b > 0 && r > 0 && h >= 0 && v >= 0 && v < TC_VARIANTS) g_tune[TuneKey(a, b, r, h)] = v;
+    }
+    fclose(f);
+}
+int tune_lookup(const TuneKey &k) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(k);
+    return it == g_tune.end() ? -1 : it->second;
+}
+void tune_store(const TuneKey &k, int v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[k] = v;
+    const char *path = tune_path();
+    if (!path) return;
+    if (FILE *f = fopen(path, "a")) {
+        fprintf(f, "{\"Mpad\":%d,\"Fpad\":%d,\"r0\":%d,\"fp16\":%d,\"variant\":%d}\n", std::get<0>(k),
+                std::get<1>(k), std::get<2>(k), std::get<3>(k), v);
+        fclose(f);
+    }
+}
+
+// Time each variant (one warm run, one timed run) with CUDA events on the call's stream.
+template <class Run>
+int tune_variant(const Ctx &c, const TcBatch &, Run run) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1;
+    }
+    int best = 0;
+    float best_ms = 3.4e38f;
+    for (int v = 0; v < TC_VARIANTS; ++v) {
+        if (run(v) != GRFT_OK) continue;
+        cudaEventRecord(e0, c.stream);
+        if (run(v) != GRFT_OK) continue;
+        cudaEventRecord(e1, c.stream);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+template <int BN, int ST>
+int launch_gemm(const Ctx &c, const TcBatch &b, const CUtensorMap &mzh, const CUtensorMap &mzl,
+                const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    static bool attr[64] = {false};
+    if (!set_smem_attr((const void *)k_ds_tc<BN, ST>, tc_smem_bytes(BN, ST), c.device, attr))
+        return GRFT_ECUDA;
+    const uint64_t kdim = 2ull * Mpad;
+    CUtensorMap mbh, mbl;
+    if (!encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
+                       TC_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2,
+                       TC_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
+        return GRFT_ECUDA;
+    TcBatch bb = b;
+    bb.tiles_n = 2 * Fpad / BN;
+    long tiles = 0;
+    for (int i = 0; i < bb.n_items; ++i) {
+        bb.it[i].tile0 = (int)tiles;
+        tiles += (long)bb.it[i].ncell * bb.it[i].tiles_m * bb.tiles_n;
+    }
+    if (tiles > 0x7fffffffL) return GRFT_EINVAL;
+    bb.total_tiles = (int)tiles;
+    const uint32_t fmt = bb.fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
+    bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+               ((uint32_t)(TC_BM >> 4) << 24);
+    const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
+    k_ds_tc<BN, ST><<<grid, TC_THREADS, tc_smem_bytes(BN, ST), c.stream>>>(mzh, mzl, mbh, mbl, bb);
+    return check_launch();
+}
+
+int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const CUtensorMap &mzh,
+                        const CUtensorMap &mzl, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    if (variant == 1) return launch_gemm<128, 3>(c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+    return launch_gemm<256, 2>(c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+}
+
 int launch_round(const Ctx &c, TcBatch &b, long rows_used, int Mpad, int Fpad, const uint16_t *Bhi,
-                 const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo) {
+                 const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
     if (b.n_items == 0) return GRFT_OK;
     const uint64_t kdim = 2ull * Mpad;
-    CUtensorMap mzh, mzl, mbh, mbl;
+    CUtensorMap mzh, mzl;
     if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)rows_used,
                        kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)rows_used,
-                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
-                       TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2,
-                       TC_BK, TC_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
         return GRFT_ECUDA;
     k_coarse_split<<<b.total_ctas, SP_THREADS, 0, c.stream>>>(b, Zhi, Zlo);
     int e = check_launch();
     if (e) return e;
-    const int grid = b.total_tiles < c.num_sms ? b.total_tiles : c.num_sms;
-    k_ds_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, c.stream>>>(mzh, mzl, mbh, mbl, b);
-    return check_launch();
+    if (variant < 0) {   // autotune: time the tile shapes on this round, keep the fastest
+        variant = tune_variant(c, b, [&](int v) { return launch_gemm_variant(v, c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad); });
+        if (variant < 0) return GRFT_ECUDA;
+        tune_store(key, variant);
+    }
+    return launch_gemm_variant(variant, c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
 }
 
 }  // namespace
@@ -527,8 +667,6 @@ int launch_round(const Ctx &c, TcBatch &b, long rows_used, int Mpad, int Fpad, c
 int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, uint16_t *Zhi, uint16_t *Zlo, long z_rows_cap) {
-    static bool attr_gemm[64] = {false};
-    if (!set_smem_attr((const void *)k_ds_tc, TC_SMEM_BYTES, c.device, attr_gemm)) return GRFT_ECUDA;
     const int F = g.Fv * g.Fa;
     const int Fpad = (F + 127) / 128 * 128;
     TcBatch b;
@@ -537,15 +675,13 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     b.tab_cell0 = tab_cell0;
     b.Mtab = Mtab;
     b.zld = 2 * Mpad;
-    b.tiles_n = Fpad / 128;
+    b.tiles_n = Fpad / 128;          // 256-column tiles; launch_gemm recounts for its variant
     b.F = F;
     b.Fv = g.Fv;
     b.Fa = g.Fa;
     b.na_c = g.ac.count;
     b.fp16 = fp16 ? 1 : 0;
-    const uint32_t fmt = fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
-    b.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-              ((uint32_t)(TC_BM >> 4) << 24);
+    b.idesc = 0;                     // set per variant by launch_gemm
     b.status = c.status;
     b.wait_limit = c.wait_limit;
     auto reset = [&]() {
@@ -555,6 +691,18 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     };
     reset();
     long rows_used = 0;
+    int rmax = 1;
+    for (int i = 0; i < n_items; ++i) {
+        const int tm = (items[i].r0_count + TC_BM - 1) / TC_BM;
+        while (rmax < tm) rmax <<= 1;
+    }
+    const TuneKey key(Mpad, Fpad, rmax, fp16 ? 1 : 0);
+    int variant = tune_lookup(key);
+    if (variant < 0 && !tune_enabled()) variant = 0;
+    if (const char *fv = getenv("DSGRFT_TILE_VARIANT")) {   // explicit choice (tests, experiments)
+        const int v = atoi(fv);
+        if (v >= 0 && v < TC_VARIANTS) variant = v;
+    }
     for (int i = 0; i < n_items; ++i) {
         const DsTcItem &d = items[i];
         if (d.cell_count <= 0 || d.r0_count <= 0) continue;
@@ -566,7 +714,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         while (cell < cell_end) {
             long fit = (z_rows_cap - rows_used) / r0_pad;
             if (fit <= 0 || b.n_items == TC_MAX_ITEMS) {
-                int e = launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo);
+                int e = launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo, variant, key);
                 if (e) return e;
                 reset();
                 rows_used = 0;
@@ -601,7 +749,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
             cell += take;
         }
     }
-    return launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo);
+    return launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo, variant, key);
 }
 
 }  // namespace grft
