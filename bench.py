@@ -12,11 +12,13 @@ sample on the host cores.  Prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -42,7 +44,10 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms by a reader thread.  The
+    sampler starts before the warm-up (nvidia-smi takes a while to print its first line);
+    mark() brackets the timed region and summary() keeps the samples taken inside it (the
+    first one after it if the region is shorter than the period)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -50,35 +55,59 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.lines = []
+        self.samples = []              # (monotonic time, line)
+        self.t0 = self.t1 = None
+        self.thread = None
 
-    def __enter__(self):
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.monotonic(), line))
+
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
         return self
 
-    def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
+
+    def stop(self):
+        if self.proc is None or self.proc.poll() is not None:
+            return
+        time.sleep(0.15)               # one more period, for a region shorter than it
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.proc.wait()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        lines = [l for t, l in self.samples if self.t0 is not None and self.t0 <= t <= self.t1]
+        if not lines and self.t0 is not None:
+            after = [l for t, l in self.samples if t > self.t1]
+            lines = after[:1]
+        for l in lines:
             f = [x.strip() for x in l.split(",")]
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except (ValueError, IndexError):
                 continue
             for n, v in zip(names, f[5:9]):
@@ -87,7 +116,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_max": max(pw)}
 
 
 def _cpu_oracle_sample(sc, s, target_s: float, warm_rows: int = 8):
@@ -195,6 +224,8 @@ def main():
         g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, args.precision, None, P)
         g.detect_peaks(P, cfar, args.topk, axes=pg, dr_m=R.dr_m, out=det_out, n_out=n_out)
 
+    clk = ClockSampler(local).start()
+    atexit.register(clk.stop)          # never leave nvidia-smi running
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -208,18 +239,23 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(i & 255)                                      # L2 flush, not timed
-            e0, e1, e2 = ev[i]
-            e0.record(stream)
-            g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, args.precision, None, P)
-            e1.record(stream)
-            g.detect_peaks(P, cfar, args.topk, axes=pg, dr_m=R.dr_m, out=det_out, n_out=n_out)
-            e2.record(stream)
-        torch.cuda.synchronize()
+    g.grft_timing(True)             # per-kernel CUDA events on the launching stream
+    clk.begin()
+    for i in range(args.steps):
+        flush.fill_(i & 255)                                          # L2 flush, not timed
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, args.precision, None, P)
+        e1.record(stream)
+        g.detect_peaks(P, cfar, args.topk, axes=pg, dr_m=R.dr_m, out=det_out, n_out=n_out)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    clk.end()
+    clk.stop()
     if world > 1:
         dist.barrier()
+    ktime = {k: g.grft_timing_get(k) for k in ("tables", "split", "contract", "cfar", "topk")}
+    g.grft_timing(False)
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     gemm_ms = [a.elapsed_time(b) for a, b, c in ev]
     det_ms = [b.elapsed_time(c) for a, b, c in ev]
@@ -297,8 +333,16 @@ def main():
         return 0
 
     peaks, src = _peaks()
-    gemm_avg_s = 1e-3 * sum(gemm_ms) / len(gemm_ms)
-    alg_flops = FLOP_PER_HYP_PULSE * units
+    # the dominant kernel: the contraction (kernel b), timed by the library's per-kernel events
+    # (the call runs it in rounds: per launch = the step's flops / launches per step)
+    n_c, ms_c = ktime["contract"] if args.precision != "fp32" else (0, 0.0)
+    if n_c > 0:
+        gemm_avg_s = 1e-3 * ms_c / n_c
+        launches_per_step = n_c / args.steps
+    else:
+        gemm_avg_s = 1e-3 * sum(gemm_ms) / len(gemm_ms)
+        launches_per_step = 1
+    alg_flops = FLOP_PER_HYP_PULSE * units / launches_per_step
     achieved = alg_flops / gemm_avg_s / 1e12
     exec_factor = 3 if args.precision != "fp32" else 1
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
@@ -316,13 +360,18 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"{world} independent CPI(s), one per GPU"},
         "roofline": {"bound": "tensor" if args.precision != "fp32" else "alu",
-                     "kernel": "k_ds_tc (fused gather + split GEMM + |Y|^2 epilogue), timed with its table kernels",
+                     "kernel": ("k_ds_tc (tcgen05 split-operand contraction + |Y|^2 epilogue), CUDA events "
+                                "around each launch on its stream" if n_c > 0 else
+                                "dsgrft_fine_dfm call (tables + FP32 contraction)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{src} {'bf16_tflops_sustained' if args.precision != 'fp32' else 'FP32 FFMA from SM count and max clock'}",
                      "algorithmic_flop_per_launch": alg_flops, "executed_flop_per_launch": alg_flops * exec_factor,
                      "tensor_pipe_frac": alg_flops * exec_factor / gemm_avg_s / 1e12 / peak,
-                     "traffic": DRAM_TRAFFIC_PER_LAUNCH, "ms": 1e3 * gemm_avg_s},
-        "stages_ms": {"tables+fused_ds_gemm": 1e3 * gemm_avg_s, "cfar+topk": sum(det_ms) / len(det_ms)},
+                     "traffic": DRAM_TRAFFIC_PER_LAUNCH, "ms": 1e3 * gemm_avg_s,
+                     "launches_per_step": launches_per_step},
+        "stages_ms": dict({"dsgrft_fine_dfm call": sum(gemm_ms) / len(gemm_ms),
+                           "detect_peaks call": sum(det_ms) / len(det_ms)},
+                          **{f"{k} kernel": (v[1] / args.steps) for k, v in ktime.items() if v[0] > 0}),
         "plain_grft": None if plain_ms is None else {
             "value": plain_units / (1e-3 * plain_ms), "ms_per_step": plain_ms,
             "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units)},
@@ -332,7 +381,7 @@ def main():
         "e2e": {"value": world * units / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(echo.numel() * 8),
                 "d2h_bytes_per_step": int(det_out.numel() + 4)},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": sum(v[0] for v in ktime.values()),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }

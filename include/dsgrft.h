@@ -118,6 +118,26 @@ int grft_set_wait_limit(uint64_t cycles);
 /* Free this device's cached workspace (the next call reallocates it). */
 int grft_release_workspace(void);
 
+/* Per-kernel timing on the GPU (tracing): while enabled, every kernel the library launches
+ * outside stream capture is bracketed by a pair of CUDA events recorded on the call's
+ * stream.  grft_timing(1) enables and clears the totals, grft_timing(0) disables;
+ * grft_timing_get synchronises the recorded events and returns, for one kernel class, the
+ * number of launches and their summed duration in milliseconds. */
+enum {
+    GRFT_KERNEL_TABLES = 0,        /* bins, phases, dechirp operands (tables.cu) */
+    GRFT_KERNEL_PLAIN = 1,         /* plain GRFT */
+    GRFT_KERNEL_COARSE_RM = 2,     /* standalone coarse-RM gather (TMA) */
+    GRFT_KERNEL_SPLIT = 3,         /* split coarse-RM operand of the tensor-core path */
+    GRFT_KERNEL_CONTRACT = 4,      /* tensor-core fine-DFM contraction */
+    GRFT_KERNEL_CONTRACT_FP32 = 5, /* FP32 SIMT fine-DFM contraction */
+    GRFT_KERNEL_CFAR = 6,
+    GRFT_KERNEL_TOPK = 7,
+    GRFT_KERNEL_ADJOINT = 8,       /* trajectory sum, adjoint, refinement */
+    GRFT_KERNEL_COUNT = 9
+};
+int grft_timing(int enable);
+int grft_timing_get(int kernel, int32_t *launches, double *total_ms);
+
 /* Failure-path self test: one CTA waits on a barrier that nothing completes, for `cycles`
  * SM cycles (0 = the current wait limit), then latches GRFT_ETIMEOUT and returns; read it
  * with grft_sync_status().  The context stays usable. */

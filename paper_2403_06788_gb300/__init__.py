@@ -19,7 +19,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
-           "grft_selftest_wait",
+           "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
@@ -94,6 +94,19 @@ def grft_set_wait_limit(cycles: int) -> None:
 
 def grft_release_workspace() -> None:
     check(load().grft_release_workspace(), "grft_release_workspace")
+
+
+def grft_timing(enable: bool) -> None:
+    """Per-kernel CUDA-event timing on (clears the totals) or off."""
+    check(load().grft_timing(1 if enable else 0), "grft_timing")
+
+
+def grft_timing_get(kernel):
+    """(launches, total_ms) of a kernel class ('contract', 'split', 'cfar', ...); synchronises."""
+    k = _abi.KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    n, ms = C.c_int32(0), C.c_double(0.0)
+    check(load().grft_timing_get(k, C.byref(n), C.byref(ms)), "grft_timing_get")
+    return int(n.value), float(ms.value)
 
 
 def grft_selftest_wait(cycles: int, stream=None) -> None:

@@ -16,6 +16,8 @@ GRFT_OK, GRFT_EINVAL, GRFT_ENOMEM, GRFT_ECUDA, GRFT_ETIMEOUT, GRFT_EUNSUPPORTED,
 GRFT_FP32, GRFT_BF16X3, GRFT_FP16X3 = 0, 1, 2
 GRFT_GATHER_NEAREST, GRFT_GATHER_LINEAR = 0, 1
 PRECISIONS = {"fp32": GRFT_FP32, "bf16x3": GRFT_BF16X3, "fp16x3": GRFT_FP16X3}
+KERNELS = {"tables": 0, "plain": 1, "coarse_rm": 2, "split": 3, "contract": 4, "contract_fp32": 5,
+           "cfar": 6, "topk": 7, "adjoint": 8}
 
 
 class grft_axis(C.Structure):
@@ -63,6 +65,8 @@ SIGNATURES = {
     "grft_set_wait_limit": (C.c_int, [C.c_uint64]),
     "grft_release_workspace": (C.c_int, []),
     "grft_selftest_wait": (C.c_int, [C.c_uint64, _P]),
+    "grft_timing": (C.c_int, [C.c_int]),
+    "grft_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "grft_bins_phases": (C.c_int, [C.POINTER(grft_radar), _P, _P, C.c_int32, _P, _P, _P]),
     "grft_plain": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),
     "grft_plain_static": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_grid), _P, _P, _P]),

@@ -196,6 +196,7 @@ __global__ __launch_bounds__(AD_THREADS) void k_refine(RadarD R, const float2 *_
 int launch_backward(const Ctx &c, const RadarD &R, const float2 *echo, int K, const double *theta,
                     int gather, const float *gP, float *P, float2 *Y, double *g, float2 *gs) {
     if (K == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_ADJOINT);
     k_backward<<<K, AD_THREADS, 0, c.stream>>>(R, echo, theta, gather, gP, P, Y, g, gs);
     return check_launch();
 }
@@ -203,6 +204,7 @@ int launch_backward(const Ctx &c, const RadarD &R, const float2 *echo, int K, co
 int launch_refine(const Ctx &c, const RadarD &R, const float2 *echo, int K, double *theta,
                   const double cell[3], int steps, int gather, float *P) {
     if (K == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_ADJOINT);
     k_refine<<<K, AD_THREADS, 0, c.stream>>>(R, echo, theta, cell[0], cell[1], cell[2], steps, gather, P);
     return check_launch();
 }

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 #include "tma.cuh"
@@ -113,6 +114,57 @@ void *workspace(const Ctx &ctx, size_t bytes) {
     return d.ws;
 }
 
+namespace {
+struct TimingRec {
+    int kernel;
+    cudaEvent_t a, b;
+};
+std::mutex g_timing_mu;
+bool g_timing_on = false;
+std::vector<TimingRec> g_timing_pending;
+int g_timing_count[GRFT_KERNEL_COUNT] = {0};
+double g_timing_ms[GRFT_KERNEL_COUNT] = {0.0};
+
+void timing_drain_locked() {
+    for (const TimingRec &r : g_timing_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_timing_count[r.kernel] += 1;
+            g_timing_ms[r.kernel] += ms;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_timing_pending.clear();
+}
+}  // namespace
+
+KernelTimer::KernelTimer(const Ctx &c, int kernel) : stream_(c.stream), kernel_(kernel) {
+    {
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        if (!g_timing_on) return;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventCreate(&a_) != cudaSuccess) {
+        a_ = nullptr;
+        return;
+    }
+    if (cudaEventCreate(&b_) != cudaSuccess) {
+        cudaEventDestroy(a_);
+        a_ = b_ = nullptr;
+        return;
+    }
+    cudaEventRecord(a_, stream_);
+}
+
+KernelTimer::~KernelTimer() {
+    if (!a_) return;
+    cudaEventRecord(b_, stream_);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timing_pending.push_back(TimingRec{kernel_, a_, b_});
+}
+
 int check_launch() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GRFT_OK : GRFT_ECUDA;
@@ -161,6 +213,26 @@ __global__ void k_selftest_wait(int *status, uint64_t limit) {
 using namespace grft;
 
 extern "C" {
+
+int grft_timing(int enable) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    timing_drain_locked();
+    for (int i = 0; i < GRFT_KERNEL_COUNT; ++i) {
+        g_timing_count[i] = 0;
+        g_timing_ms[i] = 0.0;
+    }
+    g_timing_on = enable != 0;
+    return GRFT_OK;
+}
+
+int grft_timing_get(int kernel, int32_t *launches, double *total_ms) {
+    if (kernel < 0 || kernel >= GRFT_KERNEL_COUNT || !launches || !total_ms) return GRFT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    timing_drain_locked();
+    *launches = g_timing_count[kernel];
+    *total_ms = g_timing_ms[kernel];
+    return GRFT_OK;
+}
 
 int grft_selftest_wait(uint64_t cycles, void *stream) {
     Ctx c;
@@ -302,16 +374,16 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     // split operand: as many whole cells as fit the budget (at least one)
     const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
     const long r0_pad = tc ? ds_tc_r0_pad(grid->r0_count) : 0;
-    long z_rows = 0;
+    long z_rows = 0;                 // rows per buffer (two buffers of two planes)
     if (tc) {
-        long cells_fit = (long)(split_budget() / (2 * r0_pad * row_bytes));
+        long cells_fit = (long)(split_budget() / (4 * r0_pad * row_bytes));
         if (cells_fit < 1) cells_fit = 1;
         if (cells_fit > cell_count) cells_fit = cell_count;
         z_rows = cells_fit * r0_pad;
     }
     const size_t z_plane = align_up((size_t)z_rows * row_bytes);
     unsigned char *ws = (unsigned char *)workspace(
-        c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 2 * z_plane : d_bytes));
+        c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 4 * z_plane : d_bytes));
     if (!ws) return GRFT_ENOMEM;
     int32_t *rho = (int32_t *)ws;
     float2 *w = (float2 *)(ws + rho_bytes);
@@ -334,7 +406,9 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
                               D, e0, out);
     }
     uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
-    uint16_t *Zhi = (uint16_t *)(dptr + 2 * d_bytes), *Zlo = (uint16_t *)(dptr + 2 * d_bytes + z_plane);
+    unsigned char *zp = dptr + 2 * d_bytes;
+    uint16_t *const Zhi[2] = {(uint16_t *)zp, (uint16_t *)(zp + 2 * z_plane)};
+    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), (uint16_t *)(zp + 3 * z_plane)};
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
     DsTcItem it;
@@ -389,18 +463,20 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     const size_t e0_bytes = align_up((size_t)Nmax * sizeof(float2));
     const size_t d_bytes = align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t));
     const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
-    long z_rows = (long)(split_budget() / (2 * row_bytes));
+    long z_rows = (long)(split_budget() / (4 * row_bytes));      // rows per buffer
     if (z_rows < rpad_max) z_rows = rpad_max;
     const size_t z_plane = align_up((size_t)z_rows * row_bytes);
     unsigned char *ws =
-        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + 2 * d_bytes + 2 * z_plane);
+        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + 2 * d_bytes + 4 * z_plane);
     if (!ws) return GRFT_ENOMEM;
     int32_t *rho = (int32_t *)ws;
     float2 *w = (float2 *)(ws + rho_bytes);
     float2 *e0 = (float2 *)(ws + rho_bytes + w_bytes);
     unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
     uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
-    uint16_t *Zhi = (uint16_t *)(dptr + 2 * d_bytes), *Zlo = (uint16_t *)(dptr + 2 * d_bytes + z_plane);
+    unsigned char *zp = dptr + 2 * d_bytes;
+    uint16_t *const Zhi[2] = {(uint16_t *)zp, (uint16_t *)(zp + 2 * z_plane)};
+    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), (uint16_t *)(zp + 3 * z_plane)};
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
     if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;

@@ -111,12 +111,14 @@ int launch_coarse_rm(const Ctx &c, const RadarD &R, const float2 *echo, const gr
         if (encode_tma_2d(&map, CU_TENSOR_MAP_DATA_TYPE_INT64, (void *)echo, (uint64_t)R.N,
                           (uint64_t)R.M, (uint64_t)R.N * 8, CR_BOX, 1, CU_TENSOR_MAP_SWIZZLE_NONE)) {
             dim3 grid((g.r0_count + CR_COLS - 1) / CR_COLS, (R.M + CR_ROWS - 1) / CR_ROWS, cell_count);
+            KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
             k_coarse_rm_tma<<<grid, CR_THREADS, 0, c.stream>>>(map, R.M, R.N, rho, w, g.r0_begin,
                                                                g.r0_count, Z, c.status, c.wait_limit);
             return check_launch();
         }
     }
     dim3 grid((g.r0_count + 255) / 256 < 8 ? (g.r0_count + 255) / 256 : 8, R.M, cell_count);
+    KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
     k_coarse_rm_ld<<<grid, 256, 0, c.stream>>>(echo, R.M, R.N, rho, w, g.r0_begin, g.r0_count, Z);
     return check_launch();
 }

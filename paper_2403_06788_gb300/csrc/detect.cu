@@ -433,6 +433,7 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
     const long rows = (long)nv * na;
     const int nseg = (nr0 + CF_SEG - 1) / CF_SEG;
     if (rows > 0 && nr0 > 0) {
+        KernelTimer kt(c, GRFT_KERNEL_CFAR);
         if (cfar.mode == 0 && cfar.guard == 2 && cfar.train == 16)
             k_cfar_fixed<2, 16><<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p,
                                                                                     cand_i, c.status);
@@ -457,6 +458,7 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
             return GRFT_ECUDA;
         attr_set[c.device] = true;
     }
+    KernelTimer kt(c, GRFT_KERNEL_TOPK);
     k_topk<<<1, TOPK_THREADS, smem, c.stream>>>(count, cand_p, cand_i, tp, out, n_out, c.status);
     return check_launch();
 }

@@ -116,6 +116,7 @@ int launch_ds_simt(const Ctx &c, const RadarD &R, const float2 *echo, const floa
     if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
     const int F = g.Fv * g.Fa;
     dim3 grid((g.r0_count + SM_BN - 1) / SM_BN, (F + SM_BF - 1) / SM_BF, cell_count);
+    KernelTimer kt(c, GRFT_KERNEL_CONTRACT_FP32);
     k_ds_simt<<<grid, 256, 0, c.stream>>>(echo, Z, R.M, R.N, rho, w, D, e0, g.r0_begin, g.r0_count,
                                           F, out);
     return check_launch();

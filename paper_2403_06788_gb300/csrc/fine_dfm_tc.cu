@@ -36,6 +36,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "internal.cuh"
 #include "tma.cuh"
@@ -59,6 +60,8 @@ constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128
 constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
 
 constexpr int TC_MAX_ITEMS = 64;                     // CPIs per launch (kernel-parameter table)
+constexpr int TC_ROUNDS = 1;                         // rounds beyond what the buffer forces (1: none)
+constexpr long TC_MIN_ROUND_ROWS = 65536;            // 512 bin tiles: several GEMM waves per round
 
 // One CPI (or one call's cell range) inside a launch.
 struct TcItem {
@@ -511,8 +514,6 @@ int ds_tc_r0_pad(int r0_count) { return (r0_count + TC_BM - 1) / TC_BM * TC_BM; 
 
 namespace {
 
-// Launch one round: the split kernel over every (item, cell, bin tile) of the batch, then
-// the persistent GEMM over every (item, cell, bin tile, hypothesis tile).
 // ------------------------------------------------------------------------ autotuner
 // Tile-shape choice per problem bucket (Mpad, Fpad, largest r0 tile count rounded up to a
 // power of two, FP16 or BF16): the first uncaptured call of a bucket times every variant
@@ -631,6 +632,7 @@ int launch_gemm(const Ctx &c, const TcBatch &b, const CUtensorMap &mzh, const CU
     bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TC_BM >> 4) << 24);
     const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
+    KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
     k_ds_tc<BN, ST><<<grid, TC_THREADS, tc_smem_bytes(BN, ST), c.stream>>>(mzh, mzl, mbh, mbl, bb);
     return check_launch();
 }
@@ -641,32 +643,70 @@ int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const CUten
     return launch_gemm<256, 2>(c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
 }
 
-int launch_round(const Ctx &c, TcBatch &b, long rows_used, int Mpad, int Fpad, const uint16_t *Bhi,
-                 const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
-    if (b.n_items == 0) return GRFT_OK;
+// One round = the split kernel over every (item, cell, bin tile) of the batch, then the
+// persistent GEMM over every (item, cell, bin tile, hypothesis tile).
+struct Round {
+    TcBatch b;
+    long rows;
+};
+
+bool encode_split_maps(uint16_t *Zhi, uint16_t *Zlo, long rows, int Mpad, CUtensorMap &mzh, CUtensorMap &mzl) {
     const uint64_t kdim = 2ull * Mpad;
-    CUtensorMap mzh, mzl;
-    if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)rows_used,
-                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)rows_used,
-                       kdim * 2, TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B))
-        return GRFT_ECUDA;
+    return encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)rows, kdim * 2,
+                         TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)rows, kdim * 2,
+                         TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
+    KernelTimer kt(c, GRFT_KERNEL_SPLIT);
     k_coarse_split<<<b.total_ctas, SP_THREADS, 0, c.stream>>>(b, Zhi, Zlo);
-    int e = check_launch();
-    if (e) return e;
+    return check_launch();
+}
+
+int launch_round_gemm(const Ctx &c, const Round &rd, int Mpad, int Fpad, const uint16_t *Bhi,
+                      const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
+    CUtensorMap mzh, mzl;
+    if (!encode_split_maps(Zhi, Zlo, rd.rows, Mpad, mzh, mzl)) return GRFT_ECUDA;
     if (variant < 0) {   // autotune: time the tile shapes on this round, keep the fastest
-        variant = tune_variant(c, b, [&](int v) { return launch_gemm_variant(v, c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad); });
+        variant = tune_variant(c, rd.b, [&](int v) {
+            return launch_gemm_variant(v, c, rd.b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+        });
         if (variant < 0) return GRFT_ECUDA;
         tune_store(key, variant);
     }
-    return launch_gemm_variant(variant, c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+    return launch_gemm_variant(variant, c, rd.b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+}
+
+// Side stream and events of the split/contraction pipeline, created once per device.
+struct Pipe {
+    bool init = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, split_done[2] = {nullptr, nullptr}, gemm_done[2] = {nullptr, nullptr};
+};
+Pipe g_pipe[64];
+std::mutex g_pipe_mu;
+
+Pipe *get_pipe(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    Pipe &p = g_pipe[dev];
+    if (!p.init) {
+        if (cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        cudaEvent_t *evs[5] = {&p.fork, &p.split_done[0], &p.split_done[1], &p.gemm_done[0], &p.gemm_done[1]};
+        for (cudaEvent_t *e : evs)
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        p.init = true;
+    }
+    return &p;
 }
 
 }  // namespace
 
 int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
-                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *Zhi, uint16_t *Zlo, long z_rows_cap) {
+                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],
+                 long z_rows_cap) {
     const int F = g.Fv * g.Fa;
     const int Fpad = (F + 127) / 128 * 128;
     TcBatch b;
@@ -690,11 +730,12 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         b.total_tiles = 0;
     };
     reset();
-    long rows_used = 0;
     int rmax = 1;
+    long total_rows = 0;
     for (int i = 0; i < n_items; ++i) {
         const int tm = (items[i].r0_count + TC_BM - 1) / TC_BM;
         while (rmax < tm) rmax <<= 1;
+        if (items[i].cell_count > 0) total_rows += (long)items[i].cell_count * tm * TC_BM;
     }
     const TuneKey key(Mpad, Fpad, rmax, fp16 ? 1 : 0);
     int variant = tune_lookup(key);
@@ -703,6 +744,24 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         const int v = atoi(fv);
         if (v >= 0 && v < TC_VARIANTS) variant = v;
     }
+    // Rounds of about 1/TC_ROUNDS of the work (whole cells, at least TC_MIN_ROUND_ROWS rows,
+    // within the buffer), so that the split of round r+1 runs beside the contraction of
+    // round r.  DSGRFT_ROUNDS overrides the target count (1: split, then contract).
+    int n_rounds = TC_ROUNDS;
+    if (const char *nr = getenv("DSGRFT_ROUNDS")) {
+        const int v = atoi(nr);
+        if (v >= 1 && v <= 1024) n_rounds = v;
+    }
+    long round_rows = (total_rows + n_rounds - 1) / n_rounds;
+    if (n_rounds > 1 && round_rows < TC_MIN_ROUND_ROWS) round_rows = TC_MIN_ROUND_ROWS;
+    if (round_rows > z_rows_cap) round_rows = z_rows_cap;
+    std::vector<Round> rounds;
+    long rows_used = 0;
+    auto flush = [&]() {
+        if (b.n_items > 0) rounds.push_back(Round{b, rows_used});
+        reset();
+        rows_used = 0;
+    };
     for (int i = 0; i < n_items; ++i) {
         const DsTcItem &d = items[i];
         if (d.cell_count <= 0 || d.r0_count <= 0) continue;
@@ -712,12 +771,10 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         int cell = d.cell_begin;
         const int cell_end = d.cell_begin + d.cell_count;
         while (cell < cell_end) {
-            long fit = (z_rows_cap - rows_used) / r0_pad;
+            const long lim = round_rows < r0_pad ? r0_pad : round_rows;
+            long fit = (lim - rows_used) / r0_pad;
             if (fit <= 0 || b.n_items == TC_MAX_ITEMS) {
-                int e = launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo, variant, key);
-                if (e) return e;
-                reset();
-                rows_used = 0;
+                flush();
                 continue;
             }
             const int take = (int)(fit < cell_end - cell ? fit : cell_end - cell);
@@ -749,7 +806,34 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
             cell += take;
         }
     }
-    return launch_round(c, b, rows_used, Mpad, Fpad, Bhi, Blo, Zhi, Zlo, variant, key);
+    flush();
+    if (rounds.empty()) return GRFT_OK;
+    int e;
+    if (rounds.size() == 1) {            // one round: split and contract on the caller's stream
+        if ((e = launch_split(c, rounds[0].b, Zhi[0], Zlo[0]))) return e;
+        return launch_round_gemm(c, rounds[0], Mpad, Fpad, Bhi, Blo, Zhi[0], Zlo[0], variant, key);
+    }
+    // Pipeline: splits on the side stream into alternating buffers, contractions on the
+    // caller's stream; events order each buffer's reuse.
+    Pipe *pp = get_pipe(c.device);
+    if (!pp) return GRFT_ECUDA;
+    Ctx cs = c;
+    cs.stream = pp->side;
+    if (cudaEventRecord(pp->fork, c.stream) != cudaSuccess ||
+        cudaStreamWaitEvent(pp->side, pp->fork, 0) != cudaSuccess)
+        return GRFT_ECUDA;
+    for (size_t r = 0; r < rounds.size(); ++r) {
+        const int buf = (int)(r & 1);
+        if (r >= 2 && cudaStreamWaitEvent(pp->side, pp->gemm_done[buf], 0) != cudaSuccess) return GRFT_ECUDA;
+        if ((e = launch_split(cs, rounds[r].b, Zhi[buf], Zlo[buf]))) return e;
+        if (cudaEventRecord(pp->split_done[buf], pp->side) != cudaSuccess ||
+            cudaStreamWaitEvent(c.stream, pp->split_done[buf], 0) != cudaSuccess)
+            return GRFT_ECUDA;
+        if ((e = launch_round_gemm(c, rounds[r], Mpad, Fpad, Bhi, Blo, Zhi[buf], Zlo[buf], variant, key)))
+            return e;
+        if (cudaEventRecord(pp->gemm_done[buf], c.stream) != cudaSuccess) return GRFT_ECUDA;
+    }
+    return GRFT_OK;
 }
 
 }  // namespace grft

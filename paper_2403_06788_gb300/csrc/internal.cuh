@@ -126,11 +126,14 @@ struct DsTcItem {
 };
 int ds_tc_r0_pad(int r0_count);
 // Split coarse-RM pre-pass + tensor-core contraction for a list of items, in rounds whose
-// split operand (z_rows_cap rows of 2*Mpad 16-bit values per plane) fits Zhi/Zlo.  Tables
-// rho/w are indexed [cell - tab_cell0][Mtab]; B planes are [2 Fpad][2 Mpad].
+// split operand (at most z_rows_cap rows of 2*Mpad 16-bit values per plane) fits one
+// buffer.  Tables rho/w are indexed [cell - tab_cell0][Mtab]; B planes are [2 Fpad][2 Mpad].
+// Two buffers (Zhi[i], Zlo[i]) of z_rows_cap rows each: the split of one round is written
+// into one while the contraction of the previous round reads the other.
 int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
-                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *Zhi, uint16_t *Zlo, long z_rows_cap);
+                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],
+                 long z_rows_cap);
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);
@@ -142,5 +145,20 @@ int launch_refine(const Ctx &, const RadarD &, const float2 *echo, int K, double
                   const double cell[3], int steps, int gather, float *P);
 
 int check_launch();   // GRFT_OK or GRFT_ECUDA from cudaGetLastError
+
+// Records a CUDA-event pair around the launches in its scope when timing is enabled
+// (grft_timing) and the stream is not being captured.
+class KernelTimer {
+  public:
+    KernelTimer(const Ctx &c, int kernel);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    cudaStream_t stream_;
+    int kernel_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 
 }  // namespace grft

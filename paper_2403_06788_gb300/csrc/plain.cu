@@ -122,6 +122,7 @@ int launch_plain(const Ctx &c, const RadarD &R, const float2 *echo, const grft_g
     dim3 grid((g.r0_count + PL_TILE - 1) / PL_TILE, (nh + PL_H - 1) / PL_H);
     float2 *Yc = Y ? Y + h0 * g.r0_count : nullptr;
     float *Pc = P ? P + h0 * g.r0_count : nullptr;
+    KernelTimer kt(c, GRFT_KERNEL_PLAIN);
     k_plain<<<grid, PL_THREADS, 0, c.stream>>>(echo, R.M, R.N, rho, w, nh, g.r0_begin, g.r0_count,
                                                e0, Yc, Pc);
     return check_launch();

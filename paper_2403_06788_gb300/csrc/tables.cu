@@ -119,6 +119,7 @@ int launch_bins_phases(const Ctx &c, const RadarD &R, const double *v, const dou
                        int32_t *rho, grft_c32 *w) {
     long n = (long)nh * R.M;
     if (n == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_bins_phases<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, v, a, nh, rho, (float2 *)w);
     return check_launch();
 }
@@ -127,6 +128,7 @@ int launch_plain_tables(const Ctx &c, const RadarD &R, const grft_grid &g, long 
                         int32_t *rho, float2 *w) {
     long n = (long)nh * R.M;
     if (n == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_plain_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g.v.start, g.v.step, g.a.start,
                                                               g.a.step, g.a.count, h0, nh, rho, w);
     return check_launch();
@@ -136,18 +138,21 @@ int launch_coarse_tables(const Ctx &c, const RadarD &R, const grft_dsgrid &g, in
                          int cell_count, int32_t *rho, float2 *w) {
     long n = (long)cell_count * R.M;
     if (n == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_coarse_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, cell_begin, cell_count, rho, w);
     return check_launch();
 }
 
 int launch_range_phase(const Ctx &c, const RadarD &R, int r0_begin, int r0_count, float2 *e0) {
     if (r0_count == 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_range_phase<<<blocks_for(r0_count, 256), 256, 0, c.stream>>>(R, r0_begin, r0_count, e0);
     return check_launch();
 }
 
 int launch_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, float2 *D) {
     long n = (long)R.M * g.Fv * g.Fa;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_dechirp<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, D);
     return check_launch();
 }
@@ -155,6 +160,7 @@ int launch_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, float2 *
 int launch_dechirp_split(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int Mpad, int Fpad,
                          bool fp16, uint16_t *Bhi, uint16_t *Blo) {
     long n = (long)Fpad * Mpad;
+    KernelTimer kt(c, GRFT_KERNEL_TABLES);
     k_dechirp_split<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, Mpad, Fpad, fp16 ? 1 : 0, Bhi, Blo);
     return check_launch();
 }

@@ -76,3 +76,15 @@ int main(void){
     assert vals == [ctypes.sizeof(_abi.grft_det), _abi.grft_det.p.offset, _abi.grft_det.r0_m.offset,
                     ctypes.sizeof(_abi.grft_dsgrid), _abi.grft_dsgrid.Fv.offset,
                     ctypes.sizeof(_abi.grft_batch_item), _abi.grft_cfar.fixed_thresh.offset]
+
+
+def test_kernel_class_ids_match_header():
+    """The binding's kernel-class names carry the values of the header's GRFT_KERNEL_* enum."""
+    import re
+    from paper_2403_06788_gb300 import _abi
+    text = open(HEADER).read()
+    enum = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"GRFT_KERNEL_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    count = enum.pop("count")
+    assert enum == _abi.KERNELS
+    assert count == len(enum) == max(enum.values()) + 1

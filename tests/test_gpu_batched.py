@@ -117,9 +117,11 @@ def test_batched_graph_capture_and_replay(cuda_lib):
             assert torch.equal(P, r)
 
 
-def test_split_operand_in_several_rounds_matches_one_round(cuda_lib):
+def test_split_operand_in_several_rounds_matches_one_round(cuda_lib, tmp_path):
     """A small split-operand budget (environment override, read once per process) makes the
-    DS call run cell chunks in several rounds; the output is unchanged."""
+    DS call run one cell per round, split and contraction pipelined over two buffers on two
+    streams; the output matches the oracle, equals the single-round run bit for bit, and a
+    captured graph of the pipelined call replays to the same values."""
     code = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, %r)
@@ -128,17 +130,40 @@ from synth import Axis, DSGrid, Radar, Target
 R = Radar(M=200, N=900, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
 ds = DSGrid(3, 700, Axis(-40.0, 18.75, 3), Axis(-2.5, 5.0, 3), 16, 8)
 s = synth.make_echo(R, [Target(300.0, -20.0, 1.0, complex(3.0, 0.0))], 9)
-Y = g.dsgrft(R, torch.from_numpy(s).cuda(), ds, precision="bf16x3", want_Y=True, want_P=False).cpu().numpy()
+echo = torch.from_numpy(s).cuda()
+Yt = g.dsgrft(R, echo, ds, precision="bf16x3", want_Y=True, want_P=False)
+Y = Yt.cpu().numpy()
 Yo = oracle.dsgrft_full(R, s, ds)
 err = np.abs(Y - Yo).max() / np.abs(Yo).max()
 assert g.grft_sync_status() == 0
+np.save(sys.argv[1], Y)
+nv, na = ds.vc.count * ds.Fv, ds.ac.count * ds.Fa
+Yc = torch.zeros((nv, na, ds.r0_count), dtype=torch.complex64, device="cuda")
+st = torch.cuda.Stream()
+torch.cuda.synchronize()
+graph = torch.cuda.CUDAGraph()
+with torch.cuda.graph(graph, stream=st):
+    g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.vc.count * ds.ac.count, "bf16x3", Yc, None)
+for _ in range(2):
+    Yc.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Yc, Yt)
+assert g.grft_sync_status() == 0
 print("ERR", err)
 """ % ROOT
-    env = dict(os.environ, DSGRFT_SPLIT_BUDGET_BYTES=str(2 * 768 * 448 * 2 * 2))   # two cells per round
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, r.stderr[-2000:]
-    err = float(r.stdout.split("ERR")[1])
-    assert err <= 1e-4
+    outs = []
+    for rounds_env in ({"DSGRFT_SPLIT_BUDGET_BYTES": str(4 * 768 * 448 * 2)},   # one cell per round
+                       {"DSGRFT_ROUNDS": "1"}):
+        env = dict(os.environ, **rounds_env)
+        path = os.path.join(str(tmp_path), "Y%d.npy" % len(outs))
+        r = subprocess.run([sys.executable, "-c", code, path], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        err = float(r.stdout.split("ERR")[1])
+        assert err <= 1e-4
+        outs.append(np.load(path))
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_cfg4_shaped_batch_sampled(cuda_lib):
