@@ -29,9 +29,12 @@ import numpy as np  # noqa: E402
 
 METRIC = "DS-GRFT vs plain GRFT hypothesis·pulse MACs/s, 1 GB300, ≤2e-3 rel peak err"
 UNIT = "hyp*pulse/s"
-WORKLOAD = "DS-GRFT cfg2: M=512 x N=4096 complex64, 4096 r0 x (32x64) v x (8x16) a = 2^30 hypotheses"
+WORKLOAD = "DS-GRFT, M=512 x N=4096 complex64, 4096 r0 x (32x64) v x (8x16) a = 2^30 hypotheses"
 FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
-DRAM_TRAFFIC_PER_LAUNCH = None  # from profiles/ (ncu dram bytes of the tensor-core kernel)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_ds_tc<256,2> on the first 16 coarse
+# cells (276.9 MB + 223.7 MB), scaled by 8 to one launch of this workload (128 cells per
+# launch, two launches per step).  Reset to None whenever that kernel changes.
+DRAM_TRAFFIC_PER_LAUNCH = 8 * (276.885760e6 + 223.732992e6)
 
 
 def _peaks():
@@ -146,7 +149,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    sc = synth.cfg2()
+    sc = synth.ds_m512()
     s = synth.make_echo(sc.radar, sc.targets, sc.seed)
     for _ in range(args.warmup):
         _cpu_oracle_sample(sc, s, target_s=1.0)
@@ -204,7 +207,7 @@ def main():
     dev = torch.device("cuda", local)
     g.load()
 
-    sc = synth.cfg2(run=rank)               # weak scaling: every rank owns its own CPI
+    sc = synth.ds_m512(run=rank)               # weak scaling: every rank owns its own CPI
     R, ds = sc.radar, sc.ds
     pg = ds.plain_equivalent()
     s = synth.make_echo(R, sc.targets, sc.seed)
@@ -367,7 +370,9 @@ def main():
                      "peak_source": f"{src} {'bf16_tflops_sustained' if args.precision != 'fp32' else 'FP32 FFMA from SM count and max clock'}",
                      "algorithmic_flop_per_launch": alg_flops, "executed_flop_per_launch": alg_flops * exec_factor,
                      "tensor_pipe_frac": alg_flops * exec_factor / gemm_avg_s / 1e12 / peak,
-                     "traffic": DRAM_TRAFFIC_PER_LAUNCH, "ms": 1e3 * gemm_avg_s,
+                     "traffic": (DRAM_TRAFFIC_PER_LAUNCH if (launches_per_step == 2 and args.cells == 0
+                                                             and args.precision != "fp32") else None),
+                     "ms": 1e3 * gemm_avg_s,
                      "launches_per_step": launches_per_step},
         "stages_ms": dict({"dsgrft_fine_dfm call": sum(gemm_ms) / len(gemm_ms),
                            "detect_peaks call": sum(det_ms) / len(det_ms)},

@@ -138,7 +138,7 @@ def walk_margin_bins(radar: Radar, vmax: float, amax: float) -> int:
     return int(math.ceil((vmax * T + 0.5 * amax * T * T) / radar.dr_m)) + 2
 
 
-def cfg1(run: int = 0) -> Scenario:
+def plain_m64(run: int = 0) -> Scenario:
     """Plain GRFT parity case: M=64, N=256, f_c=1 GHz, B=10 MHz (dr=15 m), PRF=500 Hz.
 
     One sinc-shaped target at r0 = bin 100.3, v = 180 m/s, a = 12 m/s^2, SNR 3 dB.
@@ -153,10 +153,10 @@ def cfg1(run: int = 0) -> Scenario:
     seed = 1000 * 1 + run
     rng = np.random.Generator(np.random.PCG64(seed))
     tgt = [Target(100.3, 180.0, 12.0, _snr_amp(rng, 3.0))]
-    return Scenario("cfg1", radar, tgt, seed, plain=grid, snr_db=[3.0])
+    return Scenario("plain_m64", radar, tgt, seed, plain=grid, snr_db=[3.0])
 
 
-def _ds_grid_cfg2(radar: Radar, Fv: int, Fa: int, r0_count: int | None = None) -> DSGrid:
+def _ds_grid_32x8(radar: Radar, Fv: int, Fa: int, r0_count: int | None = None) -> DSGrid:
     # coarse 32 v x 8 a cells tiling v in [-300, 300] m/s, a in [-20, 20] m/s^2 (cell centres)
     vstep = 600.0 / 32
     astep = 40.0 / 8
@@ -178,7 +178,7 @@ def _random_targets(rng: np.random.Generator, radar: Radar, n: int, snr_lo: floa
     return tg, snrs
 
 
-def cfg2(run: int = 0) -> Scenario:
+def ds_m512(run: int = 0) -> Scenario:
     """DS-GRFT vs plain GRFT: M=512, N=4096, f_c=1.5 GHz, PRF=1 kHz, dr=15 m, 8 targets,
     v in [-300,300] m/s, a in [-20,20] m/s^2, SNR in [-15,0] dB.
     Coarse grid 4096 r0 x 32 v x 8 a; fine 64 dv x 16 da per coarse cell (2^30 hypotheses)."""
@@ -186,24 +186,24 @@ def cfg2(run: int = 0) -> Scenario:
     seed = 1000 * 2 + run
     rng = np.random.Generator(np.random.PCG64(seed))
     tg, snrs = _random_targets(rng, radar, 8, -15.0, 0.0)
-    ds = _ds_grid_cfg2(radar, 64, 16)
-    return Scenario("cfg2", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
+    ds = _ds_grid_32x8(radar, 64, 16)
+    return Scenario("ds_m512", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
 
 
-def cfg3(run: int = 0) -> Scenario:
+def ds_precision_m2048(run: int = 0) -> Scenario:
     """Precision case: M=2048, N=8192, 32 targets, SNR in [-20,0] dB, f_c=1.5 GHz, PRF=1 kHz,
-    coarse 32 v x 8 a as in cfg2, fine 256 dv x 64 da (3.4e10 hypotheses)."""
+    coarse 32 v x 8 a as in ds_m512, fine 256 dv x 64 da (3.4e10 hypotheses)."""
     radar = Radar(M=2048, N=8192, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
     seed = 1000 * 3 + run
     rng = np.random.Generator(np.random.PCG64(seed))
     tg, snrs = _random_targets(rng, radar, 32, -20.0, 0.0)
-    ds = _ds_grid_cfg2(radar, 256, 64)
-    return Scenario("cfg3", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
+    ds = _ds_grid_32x8(radar, 256, 64)
+    return Scenario("ds_precision_m2048", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
 
 
-def cfg4(run: int = 0, n_cpi: int = 64) -> List[Scenario]:
+def ds_batch(run: int = 0, n_cpi: int = 64) -> List[Scenario]:
     """Batching case: n_cpi independent CPIs with M ~ U{256..2048}, N ~ U{1024..8192},
-    1-16 targets each at SNR in [-15,5] dB; grids as in cfg2 (fine 64 x 16)."""
+    1-16 targets each at SNR in [-15,5] dB; grids as in ds_m512 (fine 64 x 16)."""
     seed = 1000 * 4 + run
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -213,19 +213,19 @@ def cfg4(run: int = 0, n_cpi: int = 64) -> List[Scenario]:
         radar = Radar(M=M, N=N, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
         nt = int(rng.integers(1, 17))
         tg, snrs = _random_targets(rng, radar, nt, -15.0, 5.0)
-        ds = _ds_grid_cfg2(radar, 64, 16)
-        out.append(Scenario(f"cfg4[{i}]", radar, tg, seed * 100 + i, plain=ds.plain_equivalent(), ds=ds,
+        ds = _ds_grid_32x8(radar, 64, 16)
+        out.append(Scenario(f"ds_batch[{i}]", radar, tg, seed * 100 + i, plain=ds.plain_equivalent(), ds=ds,
                             snr_db=snrs))
     return out
 
 
-def cfg5(run: int = 0) -> Scenario:
+def ds_adjoint_m1024(run: int = 0) -> Scenario:
     """Differentiation case: M=1024, N=4096, 16 targets whose motion lies off-grid
-    (uniform sub-cell offsets); grids as in cfg2; top-1000 detections, 20 ascent steps."""
+    (uniform sub-cell offsets); grids as in ds_m512; top-1000 detections, 20 ascent steps."""
     radar = Radar(M=1024, N=4096, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
     seed = 1000 * 5 + run
     rng = np.random.Generator(np.random.PCG64(seed))
-    ds = _ds_grid_cfg2(radar, 64, 16)
+    ds = _ds_grid_32x8(radar, 64, 16)
     pg = ds.plain_equivalent()
     margin = walk_margin_bins(radar, 300.0, 20.0)
     tg, snrs = [], []
@@ -238,7 +238,7 @@ def cfg5(run: int = 0) -> Scenario:
         tg.append(Target(n0 + float(orr), float(pg.v.start + (j + ov) * pg.v.step),
                          float(pg.a.start + (k + oa) * pg.a.step), _snr_amp(rng, snr)))
         snrs.append(snr)
-    return Scenario("cfg5", radar, tg, seed, plain=pg, ds=ds, snr_db=snrs)
+    return Scenario("ds_adjoint_m1024", radar, tg, seed, plain=pg, ds=ds, snr_db=snrs)
 
 
 def scaled(s: Scenario, **radar_overrides) -> Scenario:

@@ -166,11 +166,11 @@ print("ERR", err)
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_cfg4_shaped_batch_sampled(cuda_lib):
+def test_ds_batch_shaped_batch_sampled(cuda_lib):
     """Eight CPIs drawn as in the batching configuration (M in [256, 2048], N in [1024, 8192],
     1-16 targets, coarse 32 x 8 cells, fine 64 x 16), full grids, sampled rows vs the oracle."""
     g = cuda_lib
-    cpis = synth.cfg4(n_cpi=8)
+    cpis = synth.ds_batch(n_cpi=8)
     grid = cpis[0].ds
     nv, na = grid.vc.count * grid.Fv, grid.ac.count * grid.Fa
     batch, data = [], []

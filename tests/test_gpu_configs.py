@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 def test_precision_config_slab_bf16x3_and_fp16x3(cuda_lib):
     g = cuda_lib
-    sc = synth.cfg3()
+    sc = synth.ds_precision_m2048()
     R, ds = sc.radar, sc.ds
     s = synth.make_echo(R, sc.targets, sc.seed)
     echo = torch.from_numpy(s).cuda()
@@ -56,7 +56,7 @@ def test_differentiation_config_pipeline(cuda_lib):
     gather).  Refined powers and points of 32 detections agree with the FP64 oracle's
     refinement; gradients at the refined points agree with the oracle's to 1e-4 of scale."""
     g = cuda_lib
-    sc = synth.cfg5()
+    sc = synth.ds_adjoint_m1024()
     R, ds = sc.radar, sc.ds
     pg = ds.plain_equivalent()
     s = synth.make_echo(R, sc.targets, sc.seed)

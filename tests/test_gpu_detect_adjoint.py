@@ -72,7 +72,7 @@ def test_topk_radix_select_path_and_ties(cuda_lib):
 
 def test_detection_estimates_map_to_grid_values(cuda_lib):
     g = cuda_lib
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     s = synth.make_echo(sc.radar, sc.targets, sc.seed)
     P = g.grft(sc.radar, torch.from_numpy(s).cuda(), sc.plain)
     out, n_out = g.detect_peaks(P, CFAR(2, 16, 1e-6), 4, axes=sc.plain, dr_m=sc.radar.dr_m)
@@ -85,7 +85,7 @@ def test_detection_estimates_map_to_grid_values(cuda_lib):
 
 
 def _adj_case():
-    sc = synth.cfg5()
+    sc = synth.ds_adjoint_m1024()
     R = sc.radar
     s = synth.make_echo(R, sc.targets, sc.seed)
     pg = sc.plain
@@ -179,7 +179,7 @@ def test_grad_s_matches_oracle_and_autograd(cuda_lib):
 
 def test_refine_matches_oracle(cuda_lib):
     g = cuda_lib
-    sc = synth.cfg5()
+    sc = synth.ds_adjoint_m1024()
     R, pg = sc.radar, sc.plain
     s = synth.make_echo(R, sc.targets, sc.seed, noise=False)
     th0 = []

@@ -112,11 +112,11 @@ def test_ds_fine_grid_padding_and_single_cell(cuda_lib):
         assert rel_peak_err(Y.cpu().numpy(), oracle.dsgrft_full(R, s, ds)) <= TOL[prec]
 
 
-def test_ds_full_cfg2_sampled(cuda_lib):
-    """cfg2 at full size (2^30 hypotheses) in the launch configuration the benchmark times,
+def test_ds_full_ds_m512_sampled(cuda_lib):
+    """ds_m512 at full size (2^30 hypotheses) in the launch configuration the benchmark times,
     compared with the oracle on sampled rows (every r0 of 24 (v, a) rows, incl. targets)."""
     g = cuda_lib
-    sc = synth.cfg2()
+    sc = synth.ds_m512()
     R, ds = sc.radar, sc.ds
     s = synth.make_echo(R, sc.targets, sc.seed)
     es = torch.from_numpy(s).cuda()

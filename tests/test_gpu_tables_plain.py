@@ -48,9 +48,9 @@ def _plain_case(R, grid, s):
     return P.cpu().numpy(), Y.cpu().numpy(), Yo
 
 
-def test_plain_cfg1_full_grid(cuda_lib):
-    """cfg1: M=64, N=256, one target, 256 x 64 x 16 hypotheses, every output compared."""
-    sc = synth.cfg1()
+def test_plain_plain_m64_full_grid(cuda_lib):
+    """plain_m64: M=64, N=256, one target, 256 x 64 x 16 hypotheses, every output compared."""
+    sc = synth.plain_m64()
     s = synth.make_echo(sc.radar, sc.targets, sc.seed)
     P, Y, Yo = _plain_case(sc.radar, sc.plain, s)
     assert rel_peak_err(Y, Yo) <= TOL_FP32
@@ -76,7 +76,7 @@ def test_plain_ragged_and_edges(cuda_lib, M, N, r0b, r0c, nv, na):
 
 def test_plain_rejects_bad_arguments(cuda_lib):
     g = cuda_lib
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     es = torch.zeros((sc.radar.M, sc.radar.N), dtype=torch.complex64, device="cuda")
     P = torch.empty(10, device="cuda")
     bad = dataclasses.replace(sc.plain, r0_begin=200, r0_count=100)    # beyond N

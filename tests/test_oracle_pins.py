@@ -19,7 +19,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _tiny_radar(M=8, N=16):
-    return dataclasses.replace(synth.cfg1().radar, M=M, N=N)
+    return dataclasses.replace(synth.plain_m64().radar, M=M, N=N)
 
 
 # ---------------------------------------------------------------- bins: exact arithmetic
@@ -64,7 +64,7 @@ def test_bins_exact_ties_round_up():
 def test_delta_target_peak_equals_M_times_A():
     """Noiseless unit-sample target on a grid hypothesis: the matched phase cancels the
     echo phase exp(-j4piR/lambda) exactly, so Y(truth) = M A, and |Y| <= M |A| elsewhere."""
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R = sc.radar
     g = sc.plain
     j, k, n0 = 30, 9, 100
@@ -82,8 +82,8 @@ def test_delta_target_peak_equals_M_times_A():
 # ---------------------------------------------------------------- P2/P10: zero motion = pulse sum
 def test_zero_motion_is_plain_pulse_sum_with_unit_range_phase():
     """v = a = 0: Y(n0) = exp(j4pi n0 dr/lambda) sum_m s[m][n0]; with integer f_c/f_s = 100
-    the range phase is exactly one (cfg1 radar)."""
-    sc = synth.cfg1()
+    the range phase is exactly one (plain_m64 radar)."""
+    sc = synth.plain_m64()
     R = sc.radar
     s = synth.make_echo(R, sc.targets, sc.seed)
     g = PlainGrid(0, R.N, Axis(0.0, 1.0, 1), Axis(0.0, 1.0, 1))
@@ -96,7 +96,7 @@ def test_zero_motion_is_plain_pulse_sum_with_unit_range_phase():
 def test_no_range_migration_doppler_is_ifft_and_parseval():
     """With v_k = k lambda PRF/(2M), a = 0 and |v_k| T < dr/2 no bin moves, and the GFT is
     the DFT over slow time (Def. 1): Y(n0, v_k) = e0 M ifft(s[:, n0])[k]."""
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R = sc.radar
     s = synth.make_echo(R, sc.targets, sc.seed + 1)
     vstep = R.wavelength * R.prf_hz / (2 * R.M)
@@ -158,7 +158,7 @@ def test_coarse_rm_then_dechirp_sum_equals_dsgrft():
 # ---------------------------------------------------------------- P6: DS == GRFT where bins agree
 def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
     """Prop. 1/2: with the same bins the two sums have identical terms up to rounding."""
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R = dataclasses.replace(sc.radar, M=32, N=128)
     s = synth.make_echo(R, [Target(50.0, 100.0, 10.0, complex(3.0, 0.0))], 21)
     ds = DSGrid(0, 128, Axis(60.0, 24.0, 3), Axis(0.0, 20.0, 2), 8, 4)
@@ -181,7 +181,7 @@ def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
 def test_sinc_target_closed_form_at_truth():
     """Noiseless sinc target: at its true (n0, v, a) the gathered samples are
     A sinc(rho_m - d_m/dr) with the carrier cancelled, so Y = A sum_m sinc(rho_m - d_m/dr)."""
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R = sc.radar
     g = sc.plain
     j, k, n0 = 35, 6, 120
@@ -199,11 +199,11 @@ def test_sinc_target_closed_form_at_truth():
 # ---------------------------------------------------------------- P11: DS vs GRFT peak location
 def test_ds_and_grft_peaks_coincide_on_grid_targets():
     """Prop. 2 / Exp. 2 ('almost the same performance'): noiseless on-grid sinc targets peak
-    at the same (n0, v, a) under plain GRFT and DS-GRFT (cfg2 radar, reduced grid)."""
-    sc = synth.cfg2()
+    at the same (n0, v, a) under plain GRFT and DS-GRFT (ds_m512 radar, reduced grid)."""
+    sc = synth.ds_m512()
     R = sc.radar
     full = sc.ds
-    # a 2x2-cell window of the cfg2 grid around one target, r0 window of 24 bins
+    # a 2x2-cell window of the ds_m512 grid around one target, r0 window of 24 bins
     i0, l0 = 20, 5
     ds = DSGrid(1500, 24, Axis(full.vc.start + i0 * full.vc.step, full.vc.step, 2),
                 Axis(full.ac.start + l0 * full.ac.step, full.ac.step, 2), full.Fv, full.Fa)
@@ -296,7 +296,7 @@ def test_cfar_false_alarm_rate_of_alpha_rule():
 
 # ---------------------------------------------------------------- adjoint pins
 def _grad_setup(mode):
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R = sc.radar
     s = synth.make_echo(R, sc.targets, sc.seed)
     tg = sc.targets[0]
@@ -371,7 +371,7 @@ def test_theta_gradient_matches_central_difference():
 
 def test_trajectory_sum_on_grid_equals_plain_grft():
     """The adjoint's forward at a grid hypothesis (nearest gather) reproduces plain GRFT."""
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R, g = sc.radar, sc.plain
     s = synth.make_echo(R, sc.targets, sc.seed)
     Y = oracle.grft_plain_rows(R, s, g, [20, 40], [3, 11])
@@ -382,7 +382,7 @@ def test_trajectory_sum_on_grid_equals_plain_grft():
 
 
 def test_refinement_increases_power_and_approaches_offgrid_truth():
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     R, g = sc.radar, sc.plain
     tg = Target(100.37, g.v.start + 30.4 * g.v.step, g.a.start + 7.7 * g.a.step, complex(2.0, 0.0))
     s = synth.make_echo(R, [tg], 0, noise=False)

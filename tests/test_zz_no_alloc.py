@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _cases():
-    sc = synth.cfg1()
+    sc = synth.plain_m64()
     yield sc.radar, sc.plain, synth.make_echo(sc.radar, sc.targets, sc.seed)
     # M = 512 and 8192 hypotheses: several chunks of the fixed scratch, ragged r0 tail
     R = Radar(M=512, N=1200, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
