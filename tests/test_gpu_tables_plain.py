@@ -48,7 +48,7 @@ def _plain_case(R, grid, s):
     return P.cpu().numpy(), Y.cpu().numpy(), Yo
 
 
-def test_plain_plain_m64_full_grid(cuda_lib):
+def test_plain_m64_full_grid(cuda_lib):
     """plain_m64: M=64, N=256, one target, 256 x 64 x 16 hypotheses, every output compared."""
     sc = synth.plain_m64()
     s = synth.make_echo(sc.radar, sc.targets, sc.seed)
