@@ -36,6 +36,23 @@ size_t split_budget() {
     return v;
 }
 
+// Rows per split-operand buffer.  If the whole operand (total_rows) fits the budget in one
+// buffer of two planes, one buffer holding all of it (one round); otherwise two buffers of
+// a quarter of the budget each, so that the split of one round can be written while the
+// contraction of the previous one reads the other.  At least min_rows (one cell or item).
+long split_rows(long total_rows, long min_rows, long row_bytes, int &nbuf, bool force_two = false) {
+    const long budget_rows = (long)(split_budget() / (2 * (size_t)row_bytes));
+    if (!force_two && total_rows <= budget_rows) {
+        nbuf = 1;
+        return total_rows > min_rows ? total_rows : min_rows;
+    }
+    nbuf = 2;
+    long rows = budget_rows / 2;
+    if (min_rows > 0 && rows > min_rows) rows = rows / min_rows * min_rows;   // whole cells
+    if (rows > total_rows) rows = total_rows;
+    return rows > min_rows ? rows : min_rows;
+}
+
 struct DevState {
     bool init = false;
     int *status = nullptr;
@@ -374,16 +391,12 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     // split operand: as many whole cells as fit the budget (at least one)
     const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
     const long r0_pad = tc ? ds_tc_r0_pad(grid->r0_count) : 0;
-    long z_rows = 0;                 // rows per buffer (two buffers of two planes)
-    if (tc) {
-        long cells_fit = (long)(split_budget() / (4 * r0_pad * row_bytes));
-        if (cells_fit < 1) cells_fit = 1;
-        if (cells_fit > cell_count) cells_fit = cell_count;
-        z_rows = cells_fit * r0_pad;
-    }
+    long z_rows = 0;                 // rows per operand buffer (two 16-bit planes each)
+    int nbuf = 1;
+    if (tc) z_rows = split_rows(r0_pad * cell_count, r0_pad, row_bytes, nbuf);
     const size_t z_plane = align_up((size_t)z_rows * row_bytes);
     unsigned char *ws = (unsigned char *)workspace(
-        c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 4 * z_plane : d_bytes));
+        c, rho_bytes + w_bytes + e0_bytes + (tc ? 2 * d_bytes + 2 * nbuf * z_plane : d_bytes));
     if (!ws) return GRFT_ENOMEM;
     int32_t *rho = (int32_t *)ws;
     float2 *w = (float2 *)(ws + rho_bytes);
@@ -407,8 +420,8 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     }
     uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
     unsigned char *zp = dptr + 2 * d_bytes;
-    uint16_t *const Zhi[2] = {(uint16_t *)zp, (uint16_t *)(zp + 2 * z_plane)};
-    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), (uint16_t *)(zp + 3 * z_plane)};
+    uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
+    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
     DsTcItem it;
@@ -463,11 +476,14 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     const size_t e0_bytes = align_up((size_t)Nmax * sizeof(float2));
     const size_t d_bytes = align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t));
     const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
-    long z_rows = (long)(split_budget() / (4 * row_bytes));      // rows per buffer
-    if (z_rows < rpad_max) z_rows = rpad_max;
+    long total_rows = 0;
+    for (int i = 0; i < n_items; ++i) total_rows += (long)ncell * ds_tc_r0_pad(items[i].r0_count);
+    int nbuf = 1;
+    // more items than one launch holds: rounds are forced, so keep two buffers
+    long z_rows = split_rows(total_rows, rpad_max, row_bytes, nbuf, n_items > DS_TC_MAX_ITEMS);
     const size_t z_plane = align_up((size_t)z_rows * row_bytes);
     unsigned char *ws =
-        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + 2 * d_bytes + 4 * z_plane);
+        (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + 2 * d_bytes + 2 * nbuf * z_plane);
     if (!ws) return GRFT_ENOMEM;
     int32_t *rho = (int32_t *)ws;
     float2 *w = (float2 *)(ws + rho_bytes);
@@ -475,8 +491,8 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
     uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
     unsigned char *zp = dptr + 2 * d_bytes;
-    uint16_t *const Zhi[2] = {(uint16_t *)zp, (uint16_t *)(zp + 2 * z_plane)};
-    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), (uint16_t *)(zp + 3 * z_plane)};
+    uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
+    uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
     const bool fp16 = precision == GRFT_FP16X3;
     if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
     if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;

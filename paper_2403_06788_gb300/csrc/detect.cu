@@ -163,123 +163,280 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
 #undef SV
 }
 
-// Specialisation for compile-time guard/train counts (the default 2/16): the positions
-// read around the thread's 16 bins are known at compile time, so reads inside the thread's
-// own bins come from registers and the others use immediate shared-memory offsets.
-template <int G, int T>
-__global__ __launch_bounds__(CF_THREADS, 4) void k_cfar_fixed(const float *__restrict__ P, CfarParams cp,
-                                                           int nseg, int *__restrict__ count,
-                                                           float *__restrict__ cand_p,
-                                                           int64_t *__restrict__ cand_i, int *status) {
-    static_assert(G + T + 1 <= CF_MAXHALO && CF_MAXHALO % 16 == 0, "halo");
-    constexpr int HALO = G + T + 1;
-    __shared__ float sv[CF_STAGE + CF_STAGE / 16 + 1];
-    const long row = blockIdx.x / nseg;
-    const int seg0 = (int)(blockIdx.x % nseg) * CF_SEG;
+// Local-maximum test over the 26 (v, a, r0) neighbours (ties: the lower linear index
+// wins) and warp-aggregated append of the survivors.  Called by all 32 lanes; `pass` is the
+// lane's threshold result for cell (row, n) of power p.
+__device__ __forceinline__ void cfar_append(bool pass, const float *__restrict__ P, const CfarParams &cp,
+                                            long row, int n, float p, int *__restrict__ count,
+                                            float *__restrict__ cand_p, int64_t *__restrict__ cand_i,
+                                            int *status) {
     const int nr0 = cp.nr0;
-    const float *prow = P + row * nr0;
-    const int nb = seg0 + threadIdx.x * CF_PER;
-    const int sb = CF_MAXHALO - seg0;
-    float x[CF_PER];
-    const bool vec = ((((uintptr_t)(prow + nb)) & 15) == 0) && nb + CF_PER <= nr0;
-    if (vec) {
-        const float4 *src = reinterpret_cast<const float4 *>(prow + nb);
-#pragma unroll
-        for (int q = 0; q < CF_PER / 4; ++q) {
-            const float4 t = __ldcs(src + q);
-            x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < CF_PER; ++q) x[q] = (nb + q < nr0) ? __ldcs(prow + nb + q) : 0.f;
-    }
-    float hl = 0.f, hr = 0.f;
-    if (threadIdx.x < HALO) {
-        const int nl = seg0 - HALO + threadIdx.x, nrr = seg0 + CF_SEG + threadIdx.x;
-        hl = (nl >= 0 && nl < nr0) ? __ldg(prow + nl) : 0.f;
-        hr = (nrr < nr0) ? __ldg(prow + nrr) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < CF_PER; ++q) sv[cf_slot(nb + q + sb)] = x[q];
-    if (threadIdx.x < HALO) {
-        sv[cf_slot(CF_MAXHALO - HALO + threadIdx.x)] = hl;
-        sv[cf_slot(CF_MAXHALO + CF_SEG + threadIdx.x)] = hr;
-    }
-    __syncthreads();
-    // staged position of bin nb + c is 16 (threadIdx.x + CF_MAXHALO/16) + c
-    const float *base = sv + 17 * (threadIdx.x + CF_MAXHALO / 16);
-    auto at = [&](int c) -> float {   // value of bin nb + c (c compile-time after unrolling)
-        return (c >= 0 && c < CF_PER) ? x[c < 0 ? 0 : (c >= CF_PER ? CF_PER - 1 : c)]
-                                      : base[c + (c >> 4)];
-    };
-
-    const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
-    const bool interior = nb - G - T >= 0 && nb + CF_PER - 1 + G + T < nr0;
-    const float alpha_in = cp.alpha[2 * T];
-    float L = 0.f, Rr = 0.f;
-#pragma unroll
-    for (int c = -G - T; c <= -G - 1; ++c) L += at(c);
-#pragma unroll
-    for (int c = G + 1; c <= G + T; ++c) Rr += at(c);
-    unsigned pmask = 0;
-#pragma unroll
-    for (int q = 0; q < CF_PER; ++q) {
-        const int n = nb + q;
-        if (q > 0) {
-            L += at(q - G - 1) - at(q - G - T - 1);
-            Rr += at(q + G + T) - at(q + G);
-        }
-        const float p = x[q];
-        bool pass;
-        if (interior) {
-            pass = p > alpha_in * (L + Rr);
-        } else {
-            const int nt = window_count(n - G - T, n - G - 1, nr0) + window_count(n + G + 1, n + G + T, nr0);
-            pass = nt > 0 && p > cp.alpha[nt] * (L + Rr);
-        }
-        if (pass && n < nr0) pmask |= 1u << q;
-    }
-    if (__any_sync(0xffffffffu, pmask != 0)) {
-#pragma unroll 1
-        for (int q = 0; q < CF_PER; ++q) {
-            const int n = nb + q;
-            bool pass = (pmask >> q) & 1u;
-            float p = 0.f;
-            if (pass) {
-                p = sv[cf_slot(n + sb)];
-                const long me = row * nr0 + n;
-                for (int dv = -1; dv <= 1 && pass; ++dv)
-                    for (int da = -1; da <= 1 && pass; ++da)
-                        for (int dn = -1; dn <= 1 && pass; ++dn) {
-                            if (!dv && !da && !dn) continue;
-                            const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
-                            if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
-                            const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
-                            const float po = (dv == 0 && da == 0) ? sv[cf_slot(n2 + sb)] : __ldg(P + o);
-                            if (po > p || (po == p && o < me)) pass = false;
-                        }
-            }
-            const unsigned ballot = __ballot_sync(0xffffffffu, pass);
-            if (ballot) {
-                const int lane = threadIdx.x & 31;
-                int b0 = 0;
-                if (lane == __ffs(ballot) - 1) b0 = atomicAdd(count, __popc(ballot));
-                b0 = __shfl_sync(0xffffffffu, b0, __ffs(ballot) - 1);
-                if (pass) {
-                    const long pos = (long)b0 + __popc(ballot & ((1u << lane) - 1));
-                    if (pos < CAND_CAP) {
-                        cand_p[pos] = p;
-                        cand_i[pos] = row * nr0 + n;
-                    } else {
-                        latch_error(status, GRFT_EOVERFLOW);
-                    }
+    if (pass) {
+        const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
+        const long me = row * nr0 + n;
+        for (int dv = -1; dv <= 1 && pass; ++dv)
+            for (int da = -1; da <= 1 && pass; ++da)
+                for (int dn = -1; dn <= 1 && pass; ++dn) {
+                    if (!dv && !da && !dn) continue;
+                    const int v2 = vi + dv, a2 = ai + da, n2 = n + dn;
+                    if (v2 < 0 || v2 >= cp.nv || a2 < 0 || a2 >= cp.na || n2 < 0 || n2 >= nr0) continue;
+                    const long o = ((long)v2 * cp.na + a2) * nr0 + n2;
+                    const float po = __ldg(P + o);
+                    if (po > p || (po == p && o < me)) pass = false;
                 }
-            }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, pass);
+    if (!ballot) return;
+    const int lane = threadIdx.x & 31;
+    int b0 = 0;
+    if (lane == __ffs(ballot) - 1) b0 = atomicAdd(count, __popc(ballot));
+    b0 = __shfl_sync(0xffffffffu, b0, __ffs(ballot) - 1);
+    if (pass) {
+        const long pos = (long)b0 + __popc(ballot & ((1u << lane) - 1));
+        if (pos < CAND_CAP) {
+            cand_p[pos] = p;
+            cand_i[pos] = row * nr0 + n;
+        } else {
+            latch_error(status, GRFT_EOVERFLOW);
         }
     }
 }
 
-// (p, idx) ordering: larger p first, then smaller idx.
+// Specialisation for compile-time guard/train counts (the default 2/16), one warp per
+// 1024-bin chunk of a row: lane l holds bins [32 l, 32 l + 32) of the chunk in registers
+// and the G+T bins on either side of them (zeros outside the row), and slides one sum over
+// both training windows across its 32 bins: four adds, a multiply and a compare per cell.
+// Bins outside the row are zero, so that sum is the sum over the available training cells
+// at the row ends too, and since alpha(Nt) = pfa^(-1/Nt) - 1 falls as Nt grows, a cell
+// with a clipped window can only pass if it passes with the full-window alpha: the scan
+// uses that one alpha, and only cells that pass are re-tested (clipped windows summed
+// again with their own alpha) and compared with their 26 neighbours; they are rare.
+constexpr int CW_LANE = 32;                     // bins per lane
+constexpr int CW_CHUNK = 32 * CW_LANE;          // bins per warp
+constexpr int CW_THREADS = 256;
+
+// The CFAR test of chunk [c0, c0 + 1024) of row `row`: x = the lane's bins c0 + 32 l + q,
+// hl / hr = bins c0 + 32 l - H + k and c0 + 32 l + 32 + k.  Called by all 32 lanes.
+template <int G, int T>
+__device__ __forceinline__ void cfar_chunk(const float (&x)[CW_LANE], const float (&hl)[G + T],
+                                           const float (&hr)[G + T], const float *__restrict__ P,
+                                           const CfarParams &cp, long row, int c0, int *__restrict__ count,
+                                           float *__restrict__ cand_p, int64_t *__restrict__ cand_i,
+                                           int *status) {
+    constexpr int H = G + T;                    // reach of the window on either side
+    static_assert(H >= 1 && H <= CW_LANE, "window reach within one neighbour lane");
+    constexpr unsigned FULL = 0xffffffffu;
+    auto at = [&](int c) -> float {             // bin nb + c; c is a constant after unrolling
+        return c < 0 ? hl[c < 0 ? H + c : 0]
+                     : (c < CW_LANE ? x[c < CW_LANE ? c : 0] : hr[c - CW_LANE < H ? c - CW_LANE : 0]);
+    };
+    const float alpha_in = cp.alpha[2 * T];
+    float S0 = 0.f;
+#pragma unroll
+    for (int c = -H; c <= -G - 1; ++c) S0 += at(c);
+#pragma unroll
+    for (int c = G + 1; c <= H; ++c) S0 += at(c);
+    bool hit = false;
+    {
+        float S = S0;
+#pragma unroll
+        for (int q = 0; q < CW_LANE; ++q) {
+            if (q > 0) S += (at(q - G - 1) - at(q - H - 1)) + (at(q + H) - at(q + G));
+            hit |= x[q] > alpha_in * S;
+        }
+    }
+    if (!__any_sync(FULL, hit)) return;
+
+    // rare: the same scan again, keeping which cells passed
+    const int lane = threadIdx.x & 31;
+    const int nr0 = cp.nr0;
+    const float *prow = P + row * nr0;
+    const int nb = c0 + lane * CW_LANE;
+    unsigned pmask = 0;
+    {
+        float S = S0;
+#pragma unroll
+        for (int q = 0; q < CW_LANE; ++q) {
+            if (q > 0) S += (at(q - G - 1) - at(q - H - 1)) + (at(q + H) - at(q + G));
+            pmask |= (x[q] > alpha_in * S ? 1u : 0u) << q;
+        }
+    }
+    unsigned any = __reduce_or_sync(FULL, pmask);
+    while (any) {                               // warp-uniform loop over the passing offsets
+        const int q = __ffs(any) - 1;
+        any &= any - 1;
+        const int n = nb + q;
+        bool pass = ((pmask >> q) & 1u) && n < nr0;
+        float p = 0.f;
+        if (pass) {
+            p = __ldg(prow + n);
+            if (n < H || n >= nr0 - H) {        // clipped window: its own count and alpha
+                float Ls = 0.f, Rs = 0.f;
+                for (int j = max(n - H, 0); j <= n - G - 1; ++j) Ls += __ldg(prow + j);
+                for (int j = n + G + 1; j <= min(n + H, nr0 - 1); ++j) Rs += __ldg(prow + j);
+                const int nt = window_count(n - H, n - G - 1, nr0) + window_count(n + G + 1, n + H, nr0);
+                pass = nt > 0 && p > cp.alpha[nt] * (Ls + Rs);
+            }
+        }
+        cfar_append(pass, P, cp, row, n, p, count, cand_p, cand_i, status);
+    }
+}
+
+// Any row length and alignment: each warp loads its chunk with plain loads and takes the
+// neighbouring bins from the adjacent lanes by shuffles (lanes 0 and 31 load theirs).
+template <int G, int T>
+__global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_warp(const float *__restrict__ P, CfarParams cp,
+                                                           int nch, long rows, int *__restrict__ count,
+                                                           float *__restrict__ cand_p,
+                                                           int64_t *__restrict__ cand_i, int *status) {
+    constexpr int H = G + T;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long gw = (long)blockIdx.x * (CW_THREADS / 32) + (threadIdx.x >> 5);
+    if (gw >= rows * nch) return;               // whole warp
+    const long row = gw / nch;
+    const int nr0 = cp.nr0;
+    const float *prow = P + row * nr0;
+    const int c0 = (int)(gw % nch) * CW_CHUNK;
+    const int nb = c0 + lane * CW_LANE;
+    float x[CW_LANE];
+    if (nb + CW_LANE <= nr0 && ((((uintptr_t)(prow + nb)) & 15) == 0)) {
+        const float4 *src = reinterpret_cast<const float4 *>(prow + nb);
+#pragma unroll
+        for (int q = 0; q < CW_LANE / 4; ++q) {
+            const float4 t = __ldg(src + q);
+            x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CW_LANE; ++q) x[q] = (nb + q < nr0) ? __ldg(prow + nb + q) : 0.f;
+    }
+    float hl[H], hr[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        const int nl = nb - H + k, nr = nb + CW_LANE + k;
+        const float vl = __shfl_up_sync(FULL, x[CW_LANE - H + k], 1);
+        const float vr = __shfl_down_sync(FULL, x[k], 1);
+        hl[k] = lane != 0 ? vl : ((nl >= 0 && nl < nr0) ? __ldg(prow + nl) : 0.f);
+        hr[k] = lane != 31 ? vr : (nr < nr0 ? __ldg(prow + nr) : 0.f);
+    }
+    cfar_chunk<G, T>(x, hl, hr, P, cp, row, c0, count, cand_p, cand_i, status);
+}
+
+// 16-byte aligned rows (nr0 % 4 == 0) and fewer than 2^31 chunks: persistent warps walk
+// the chunks gw, gw + W, ... (W warps in the grid) with a CP_STAGES-deep pipeline of
+// asynchronous copies into shared memory, so that two chunks per warp are in flight while
+// one is tested.  Each lane copies its own 128 bytes (eight 16-byte cp.async whose
+// positions are XOR-swizzled by lane, so reads are free of bank conflicts); lanes 0 and 31
+// also copy the 20 bins before and after the chunk (zero-filled outside the row).  After
+// the wait and a warp barrier every lane reads its bins and, from its neighbours' slots,
+// the G+T bins on either side.
+constexpr int CP_STAGES = 3;
+constexpr int CP_HALO = 20;                               // >= G + T, multiple of 4
+constexpr int CP_SEG = 32 * CW_LANE;                      // floats of the 32 lanes' slots
+constexpr int CP_STAGE_FLOATS = CP_SEG + 2 * CP_HALO;     // + left and right halo slots
+constexpr size_t CP_SMEM = (size_t)(CW_THREADS / 32) * CP_STAGES * CP_STAGE_FLOATS * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 16-byte chunk c (0..7) of lane l's slot inside a stage
+__device__ __forceinline__ int cp_pos(int l, int c) { return l * CW_LANE + 4 * (c ^ (l & 7)); }
+
+template <int G, int T>
+__global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_pipe(const float *__restrict__ P, CfarParams cp,
+                                                           int nch, int items, int *__restrict__ count,
+                                                           float *__restrict__ cand_p,
+                                                           int64_t *__restrict__ cand_i, int *status) {
+    constexpr int H = G + T;
+    static_assert(H <= CP_HALO && CP_HALO % 4 == 0 && CP_HALO <= 4 * 5, "halo copy");
+    extern __shared__ float4 cf_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wbase = reinterpret_cast<float *>(cf_smem) + (size_t)warp * CP_STAGES * CP_STAGE_FLOATS;
+    const int gw = blockIdx.x * (CW_THREADS / 32) + warp;
+    const int W = gridDim.x * (CW_THREADS / 32);
+    const int nr0 = cp.nr0;
+    // halo copies: lane 0 the CP_HALO bins before the chunk, lane 31 those after it
+    const bool hlane = lane == 0 || lane == 31;
+    const int hoff = lane == 0 ? -CP_HALO : CW_CHUNK;
+    const int hslot = CP_SEG + (lane == 0 ? 0 : CP_HALO);
+
+    auto prefetch = [&](int i, int stage) {
+        float *st = wbase + stage * CP_STAGE_FLOATS;
+        if (i < items) {
+            const unsigned row = (unsigned)i / (unsigned)nch;
+            const int c0 = (int)((unsigned)i - row * (unsigned)nch) * CW_CHUNK;
+            const float *prow = P + (size_t)row * nr0;
+            const int nb = c0 + lane * CW_LANE;
+            if (c0 + CW_CHUNK <= nr0) {
+#pragma unroll
+                for (int c = 0; c < CW_LANE / 4; ++c) cp_async16(st + cp_pos(lane, c), prow + nb + 4 * c, 16);
+            } else {
+#pragma unroll
+                for (int c = 0; c < CW_LANE / 4; ++c) {
+                    const int b = nb + 4 * c;
+                    const bool in = b < nr0;             // nr0 % 4 == 0: whole 16-byte runs
+                    cp_async16(st + cp_pos(lane, c), in ? prow + b : prow, in ? 16 : 0);
+                }
+            }
+            if (hlane) {
+#pragma unroll
+                for (int c = 0; c < CP_HALO / 4; ++c) {
+                    const int b = c0 + hoff + 4 * c;
+                    const bool in = b >= 0 && b < nr0;
+                    cp_async16(st + hslot + 4 * c, in ? prow + b : prow, in ? 16 : 0);
+                }
+            }
+        }
+        cp_async_commit();                      // one group per item, empty past the end
+    };
+
+#pragma unroll
+    for (int t = 0; t < CP_STAGES - 1; ++t) prefetch(gw + t * W, t);
+    for (int t = 0;; ++t) {
+        const int i = gw + t * W;               // items + W < 2^31 (host check)
+        if (i >= items) break;                  // warp-uniform
+        const float *st = wbase + (t % CP_STAGES) * CP_STAGE_FLOATS;
+        cp_async_wait<CP_STAGES - 2>();         // this lane's copies of item t have landed
+        __syncwarp();                           // ... and every lane's
+        float x[CW_LANE];
+#pragma unroll
+        for (int c = 0; c < CW_LANE / 4; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(st + cp_pos(lane, c));
+            x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+        }
+        // bins before the lane's: chunks 3..7 of lane l-1 (its bins 12..31), or the left
+        // halo slot for lane 0; bins after: chunks 0..4 of lane l+1, or the right slot
+        float lv[CP_HALO], rv[CP_HALO];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float4 a = *reinterpret_cast<const float4 *>(
+                st + (lane == 0 ? CP_SEG + 4 * c : cp_pos(lane - 1, 3 + c)));
+            const float4 b = *reinterpret_cast<const float4 *>(
+                st + (lane == 31 ? CP_SEG + CP_HALO + 4 * c : cp_pos(lane + 1, c)));
+            lv[4 * c] = a.x; lv[4 * c + 1] = a.y; lv[4 * c + 2] = a.z; lv[4 * c + 3] = a.w;
+            rv[4 * c] = b.x; rv[4 * c + 1] = b.y; rv[4 * c + 2] = b.z; rv[4 * c + 3] = b.w;
+        }
+        float hl[H], hr[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            hl[k] = lv[CP_HALO - H + k];
+            hr[k] = rv[k];
+        }
+        __syncwarp();                           // all reads of this stage done before it is refilled
+        prefetch(gw + (t + CP_STAGES - 1) * W, (t + CP_STAGES - 1) % CP_STAGES);
+        const unsigned row = (unsigned)i / (unsigned)nch;
+        cfar_chunk<G, T>(x, hl, hr, P, cp, (long)row, (int)((unsigned)i - row * (unsigned)nch) * CW_CHUNK,
+                         count, cand_p, cand_i, status);
+    }
+    cp_async_wait<0>();
+}
+
 __device__ __forceinline__ bool before(float pa, int64_t ia, float pb, int64_t ib) {
     return pa > pb || (pa == pb && ia < ib);
 }
@@ -434,10 +591,30 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
     const int nseg = (nr0 + CF_SEG - 1) / CF_SEG;
     if (rows > 0 && nr0 > 0) {
         KernelTimer kt(c, GRFT_KERNEL_CFAR);
-        if (cfar.mode == 0 && cfar.guard == 2 && cfar.train == 16)
-            k_cfar_fixed<2, 16><<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p,
-                                                                                    cand_i, c.status);
-        else
+        if (cfar.mode == 0 && cfar.guard == 2 && cfar.train == 16) {
+            const int nch = (nr0 + CW_CHUNK - 1) / CW_CHUNK;
+            const long warps = rows * nch;
+            const long blocks = (warps + CW_THREADS / 32 - 1) / (CW_THREADS / 32);
+            if (blocks > 0x7fffffffL) return GRFT_EINVAL;
+            static bool pipe_attr[64] = {false};
+            const bool aligned = (nr0 % 4) == 0 && (((uintptr_t)P) & 15) == 0 && c.device < 64 &&
+                                 warps + 2L * c.num_sms * (CW_THREADS / 32) * CP_STAGES < 0x7fffffffL;
+            if (aligned && !pipe_attr[c.device]) {
+                if (cudaFuncSetAttribute(k_cfar_pipe<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CP_SMEM) != cudaSuccess)
+                    return GRFT_ECUDA;
+                pipe_attr[c.device] = true;
+            }
+            if (aligned) {
+                const long pblocks = blocks < 2L * c.num_sms ? blocks : 2L * c.num_sms;
+                k_cfar_pipe<2, 16><<<(unsigned)pblocks, CW_THREADS, CP_SMEM, c.stream>>>(P, cp, nch, (int)warps,
+                                                                                      count, cand_p, cand_i,
+                                                                                      c.status);
+            } else {
+                k_cfar_warp<2, 16><<<(unsigned)blocks, CW_THREADS, 0, c.stream>>>(P, cp, nch, rows, count, cand_p,
+                                                                                  cand_i, c.status);
+            }
+        } else
             k_cfar<<<(unsigned)(rows * nseg), CF_THREADS, 0, c.stream>>>(P, cp, nseg, count, cand_p, cand_i,
                                                                         c.status);
         int e = check_launch();

@@ -59,7 +59,7 @@ constexpr size_t tc_smem_bytes(int BN, int ST) {
 constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
 constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
 
-constexpr int TC_MAX_ITEMS = 64;                     // CPIs per launch (kernel-parameter table)
+constexpr int TC_MAX_ITEMS = DS_TC_MAX_ITEMS;        // CPIs per launch (kernel-parameter table)
 constexpr int TC_ROUNDS = 1;                         // rounds beyond what the buffer forces (1: none)
 constexpr long TC_MIN_ROUND_ROWS = 65536;            // 512 bin tiles: several GEMM waves per round
 
@@ -809,9 +809,12 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     flush();
     if (rounds.empty()) return GRFT_OK;
     int e;
-    if (rounds.size() == 1) {            // one round: split and contract on the caller's stream
-        if ((e = launch_split(c, rounds[0].b, Zhi[0], Zlo[0]))) return e;
-        return launch_round_gemm(c, rounds[0], Mpad, Fpad, Bhi, Blo, Zhi[0], Zlo[0], variant, key);
+    if (rounds.size() == 1 || !Zhi[1] || !Zlo[1]) {   // one buffer: rounds on the caller's stream
+        for (const Round &rd : rounds) {
+            if ((e = launch_split(c, rd.b, Zhi[0], Zlo[0]))) return e;
+            if ((e = launch_round_gemm(c, rd, Mpad, Fpad, Bhi, Blo, Zhi[0], Zlo[0], variant, key))) return e;
+        }
+        return GRFT_OK;
     }
     // Pipeline: splits on the side stream into alternating buffers, contractions on the
     // caller's stream; events order each buffer's reuse.

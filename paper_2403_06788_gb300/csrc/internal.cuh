@@ -128,8 +128,10 @@ int ds_tc_r0_pad(int r0_count);
 // Split coarse-RM pre-pass + tensor-core contraction for a list of items, in rounds whose
 // split operand (at most z_rows_cap rows of 2*Mpad 16-bit values per plane) fits one
 // buffer.  Tables rho/w are indexed [cell - tab_cell0][Mtab]; B planes are [2 Fpad][2 Mpad].
-// Two buffers (Zhi[i], Zlo[i]) of z_rows_cap rows each: the split of one round is written
-// into one while the contraction of the previous round reads the other.
+// Buffers (Zhi[i], Zlo[i]) of z_rows_cap rows each: with two, the split of one round is
+// written into one while the contraction of the previous round reads the other; with one
+// (Zhi[1] == nullptr) rounds run one after the other on the caller's stream.
+constexpr int DS_TC_MAX_ITEMS = 64;    // CPIs per tensor-core launch (kernel-parameter table)
 int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],

@@ -31,14 +31,22 @@ def _ambiguous(P, cfar, idx_set_diff):
     return all(out)
 
 
-@pytest.mark.parametrize("nr0", [4096, 3001])
+@pytest.mark.parametrize("nr0", [4096, 3001, 2052, 1043, 50])
 def test_cfar_topk_matches_oracle_on_same_power(cuda_lib, nr0):
+    """Row lengths: whole 1024-bin warp chunks, ragged and unaligned rows, a second chunk
+    holding a few bins, a row shorter than the training window.  Targets also sit on
+    lane and chunk boundaries, and two equal adjacent peaks test the index tie-break."""
     g = cuda_lib
     rng = np.random.default_rng(nr0)
     nv, na = 24, 7
     P = rng.exponential(1.0, size=(nv, na, nr0)).astype(np.float32)
     for k in range(40):       # strong and weak targets
         P[rng.integers(nv), rng.integers(na), rng.integers(nr0)] = np.float32(rng.uniform(20, 200))
+    for n in (0, 31, 32, 1023, 1024, 1025, nr0 - 1):
+        if 0 <= n < nr0:
+            P[rng.integers(nv), rng.integers(na), n] = np.float32(rng.uniform(50, 300))
+    if nr0 > 8:
+        P[5, 3, nr0 // 2] = P[5, 3, nr0 // 2 + 1] = np.float32(400.0)
     cfar = CFAR(2, 16, 1e-4)
     K = 64
     out, n_out = g.detect_peaks(torch.from_numpy(P).cuda(), cfar, K)
