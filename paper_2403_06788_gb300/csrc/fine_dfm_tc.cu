@@ -48,12 +48,13 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                      // real k per stage (32 pulses x re/im)
 constexpr int TC_THREADS = 192;
-constexpr uint32_t TC_A_BYTES = TC_BM * 128;   // 16 KB per plane
 constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unwind path
 // Tile-shape variants of kernel b (chosen per problem shape by the autotuner):
 // BN real columns per tile (BN/2 fine hypotheses) and ST pipeline stages.
-constexpr size_t tc_smem_bytes(int BN, int ST) {
-    return (size_t)ST * (2 * TC_A_BYTES + 2 * (size_t)BN * 128) + 1024;
+// ... and BK real k per stage: 64 (128-byte swizzle rows) or 32 (64-byte swizzle rows, so
+// twice the stages fit the same shared memory).
+constexpr size_t tc_smem_bytes(int BN, int ST, int BK) {
+    return (size_t)ST * (2 * (size_t)TC_BM * BK * 2 + 2 * (size_t)BN * BK * 2) + 1024;
 }
 
 constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
@@ -105,14 +106,36 @@ __device__ __forceinline__ int find_item_tile(const TcBatch &b, int idx) {
     return i;
 }
 
+// Coordinates of a work unit: with CL = 1 one tile (item, cell, bin tile mt, hypothesis
+// tile nt); with CL = 2 a pair of bin tiles (2 mg, 2 mg + 1) sharing hypothesis tile nt,
+// CTA `rank` of the cluster taking bin tile 2 mg + rank (a tile past the item's last bin
+// tile computes on whatever rows it loads and stores nothing).
+template <int CL>
+__device__ __forceinline__ const TcItem &decode_unit(const TcBatch &b, int unit, int rank, int &nt, int &mt,
+                                                     int &cl) {
+    const TcItem &p = b.it[find_item_tile(b, unit)];
+    const int local = unit - p.tile0;
+    nt = local % b.tiles_n;
+    const int rest = local / b.tiles_n;
+    const int groups = (p.tiles_m + CL - 1) / CL;
+    mt = (rest % groups) * CL + rank;
+    cl = rest / groups;
+    return p;
+}
+
 // ----------------------------------------------------------------------- tcgen05 wrappers
+// Shared-memory matrix descriptor of a K-major tile whose rows are BK 16-bit values (BK = 64:
+// 128-byte rows, 128-byte swizzle; BK = 32: 64-byte rows, 64-byte swizzle), 8-row groups
+// packed back to back.
+template <int BK>
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    static_assert(BK == 64 || BK == 32, "row of 128 or 64 bytes");
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
     d |= (uint64_t)1 << 16;                     // leading byte offset (unused, K-major swizzled)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)((8 * BK * 2) >> 4) << 32;   // stride byte offset: 8 rows
     d |= (uint64_t)1 << 46;                     // descriptor version
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;    // 128-byte or 64-byte swizzle
     return d;
 }
 
@@ -130,6 +153,38 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+// Commit to the same mbarrier in every CTA of cta_mask (cluster of two: both consumers of
+// a multicast stage signal both producers).
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(cta_mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 2-D tiled TMA load delivered to the same shared-memory offset (and completing the same
+// mbarrier offset) in every CTA of cta_mask.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                               uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() {
@@ -287,17 +342,22 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
 }
 
 // =========================================================================== kernel b
-template <int BN, int ST>
+template <int BN, int ST, int CL, int BK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
             const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
             const __grid_constant__ TcBatch B) {
     constexpr int TC_BN = BN;                          // real columns per tile
     constexpr int TC_STAGES = ST;
-    constexpr uint32_t TC_B_BYTES = BN * 128;          // per plane
+    constexpr uint32_t TC_A_BYTES = TC_BM * BK * 2;    // per plane
+    constexpr uint32_t TC_B_BYTES = BN * BK * 2;       // per plane
     constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+    constexpr int KSUB = 64 / BK;                      // stages per 32-pulse group
     constexpr uint32_t TC_TMEM_COLS = 2 * BN;          // two accumulators
     static_assert(BN % 32 == 0 && BN <= 256 && TC_TMEM_COLS >= 32, "tile");
+    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
+    constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
+    constexpr uint32_t TC_B_PART = TC_B_BYTES / CL;    // rows of B this CTA fetches (per plane)
     extern __shared__ unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
@@ -308,6 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int cid = (int)blockIdx.x / CL, ncl = (int)gridDim.x / CL;   // cluster index, count
 
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&mapAhi);
@@ -316,7 +378,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tma_prefetch_desc(&mapBlo);
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CL);             // every CTA of the cluster reads each stage's B
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tmem_full[b], 1);
@@ -335,6 +397,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
     }
     __syncthreads();
+    if (CL > 1) cluster_sync_all();              // peers' barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem_base = tmem_holder;
     const uint64_t lim = B.wait_limit;
@@ -344,15 +407,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             int it = 0;
             int last_it = -1;
-            for (int tile = blockIdx.x; tile < B.total_tiles && !abort_flag; tile += gridDim.x) {
-                const TcItem &p = B.it[find_item_tile(B, tile)];
-                const int local = tile - p.tile0;
-                const int nt = local % B.tiles_n;
-                const int nt_m = local / B.tiles_n;
-                const int mt = nt_m % p.tiles_m;
-                const int cl = nt_m / p.tiles_m;
+            for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl) {
+                int nt, mt, cl;
+                const TcItem &p = decode_unit<CL>(B, tile, rank, nt, mt, cl);
                 const int arow = (int)(p.zrow0 + (long)cl * p.r0_pad + mt * TC_BM);
-                for (int kt = 0; kt < p.KT; ++kt, ++it) {
+                for (int kt = 0; kt < p.KT * KSUB; ++kt, ++it) {
                     const int s = it % TC_STAGES;
                     if (!mbar_wait_backoff(&empty[s], ((it / TC_STAGES) & 1) ^ 1, lim, 32)) {
                         latch_error(B.status, GRFT_ETIMEOUT);
@@ -361,11 +420,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     unsigned char *st = smem + s * TC_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
-                    tma_load_2d(st, &mapAhi, kt * TC_BK, arow, &full[s]);
-                    tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * TC_BK, arow, &full[s]);
-                    tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * TC_BK, nt * TC_BN, &full[s]);
-                    tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &mapBlo, kt * TC_BK, nt * TC_BN,
-                                &full[s]);
+                    tma_load_2d(st, &mapAhi, kt * BK, arow, &full[s]);
+                    tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * BK, arow, &full[s]);
+                    if (CL == 1) {
+                        tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * BK, nt * TC_BN, &full[s]);
+                        tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &mapBlo, kt * BK, nt * TC_BN,
+                                    &full[s]);
+                    } else {   // this CTA's share of the B rows, delivered to every CTA of the cluster
+                        const int brow = nt * TC_BN + rank * (TC_BN / CL);
+                        tma_load_2d_mc(st + 2 * TC_A_BYTES + rank * TC_B_PART, &mapBhi, kt * BK, brow,
+                                       &full[s], CL_MASK);
+                        tma_load_2d_mc(st + 2 * TC_A_BYTES + TC_B_BYTES + rank * TC_B_PART, &mapBlo, kt * BK,
+                                       brow, &full[s], CL_MASK);
+                    }
                     last_it = it;
                 }
             }
@@ -379,9 +446,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             int it = 0, tcount = 0;
             bool issued_any = false;
-            for (int tile = blockIdx.x; tile < B.total_tiles && !abort_flag; tile += gridDim.x, ++tcount) {
+            for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl, ++tcount) {
                 const int b = tcount & 1;
-                const int KT = B.it[find_item_tile(B, tile)].KT;
+                const int KT = B.it[find_item_tile(B, tile)].KT * KSUB;
                 if (!mbar_wait(&tmem_empty[b], ((tcount >> 1) & 1) ^ 1, lim)) {
                     latch_error(B.status, GRFT_ETIMEOUT);
                     abort_flag = 1;
@@ -403,15 +470,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t a_hi = st, a_lo = st + TC_A_BYTES;
                     const uint32_t b_hi = st + 2 * TC_A_BYTES, b_lo = b_hi + TC_B_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t off = kk * 32;   // 16 elements x 2 bytes inside the swizzle row
-                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_hi + off), B.idesc,
+                        umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_hi + off), B.idesc,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        umma_f16(d_tmem, umma_desc(a_hi + off), umma_desc(b_lo + off), B.idesc, 1u);
-                        umma_f16(d_tmem, umma_desc(a_lo + off), umma_desc(b_hi + off), B.idesc, 1u);
+                        umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_lo + off), B.idesc, 1u);
+                        umma_f16(d_tmem, umma_desc<BK>(a_lo + off), umma_desc<BK>(b_hi + off), B.idesc, 1u);
                     }
                     issued_any = true;
-                    umma_commit(&empty[s]);
+                    if (CL == 1)
+                        umma_commit(&empty[s]);
+                    else
+                        umma_commit_mc(&empty[s], CL_MASK);   // the stage's B is shared
                 }
                 if (!ok) break;
                 umma_commit(&tmem_full[b]);
@@ -434,14 +504,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int na_full = B.na_c * B.Fa;
         bool aborted = false;
         int tcount = 0;
-        for (int tile = blockIdx.x; tile < B.total_tiles; tile += gridDim.x, ++tcount) {
+        for (int tile = cid; tile < B.total_tiles; tile += ncl, ++tcount) {
             const int b = tcount & 1;
-            const TcItem &p = B.it[find_item_tile(B, tile)];
-            const int local = tile - p.tile0;
-            const int nt = local % B.tiles_n;
-            const int nt_m = local / B.tiles_n;
-            const int mt = nt_m % p.tiles_m;
-            const int cl = nt_m / p.tiles_m;
+            int nt, mt, cl;
+            const TcItem &p = decode_unit<CL>(B, tile, rank, nt, mt, cl);
             const int c = p.cell0 + cl;
             const int iv = c / B.na_c - p.i0, il = c % B.na_c;
             named_bar_sync(1, 128);                  // previous tile's offsets no longer read
@@ -498,6 +564,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      "r"(TC_TMEM_COLS)
                      : "memory");
     }
+    if (CL > 1) cluster_sync_all();              // no peer still signals or writes into this CTA
 }
 
 bool set_smem_attr(const void *fn, size_t bytes, int device, bool *done) {
@@ -524,7 +591,7 @@ namespace {
 // DSGRFT_AUTOTUNE=0 disables timing (the default variant is used); DSGRFT_TILE_VARIANT=v
 // forces variant v.  Variants give
 // bit-identical results: only the N tiling changes, not the order of the K accumulation.
-constexpr int TC_VARIANTS = 2;     // 0: BN 256, 2 stages; 1: BN 128, 3 stages
+constexpr int TC_VARIANTS = 5;     // (BN, stages, CTAs per cluster, BK): see launch_gemm_variant
 using TuneKey = std::tuple<int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
@@ -606,41 +673,77 @@ int tune_variant(const Ctx &c, const TcBatch &, Run run) {
     return best;
 }
 
-template <int BN, int ST>
-int launch_gemm(const Ctx &c, const TcBatch &b, const CUtensorMap &mzh, const CUtensorMap &mzl,
+template <int BN, int ST, int CL, int BK>
+int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
     static bool attr[64] = {false};
-    if (!set_smem_attr((const void *)k_ds_tc<BN, ST>, tc_smem_bytes(BN, ST), c.device, attr))
-        return GRFT_ECUDA;
+    static int max_clusters[64] = {0};
+    const size_t smem = tc_smem_bytes(BN, ST, BK);
+    if (!set_smem_attr((const void *)k_ds_tc<BN, ST, CL, BK>, smem, c.device, attr)) return GRFT_ECUDA;
     const uint64_t kdim = 2ull * Mpad;
-    CUtensorMap mbh, mbl;
-    if (!encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2,
-                       TC_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2,
-                       TC_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    const CUtensorMapSwizzle sw = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUtensorMap mzh, mzl, mbh, mbl;
+    if (!encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)zrows, kdim * 2, BK,
+                       TC_BM, sw) ||
+        !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)zrows, kdim * 2, BK,
+                       TC_BM, sw) ||
+        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2, BK,
+                       BN / CL, sw) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2, BK,
+                       BN / CL, sw))
         return GRFT_ECUDA;
     TcBatch bb = b;
     bb.tiles_n = 2 * Fpad / BN;
-    long tiles = 0;
+    long units = 0;
     for (int i = 0; i < bb.n_items; ++i) {
-        bb.it[i].tile0 = (int)tiles;
-        tiles += (long)bb.it[i].ncell * bb.it[i].tiles_m * bb.tiles_n;
+        bb.it[i].tile0 = (int)units;
+        units += (long)bb.it[i].ncell * ((bb.it[i].tiles_m + CL - 1) / CL) * bb.tiles_n;
     }
-    if (tiles > 0x7fffffffL) return GRFT_EINVAL;
-    bb.total_tiles = (int)tiles;
+    if (units > 0x7fffffffL) return GRFT_EINVAL;
+    bb.total_tiles = (int)units;
     const uint32_t fmt = bb.fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
     bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TC_BM >> 4) << 24);
-    const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute la[1];
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    int slots = c.num_sms;                    // persistent CTAs (CL = 1) or clusters (CL = 2)
+    if (CL > 1) {
+        la[0].id = cudaLaunchAttributeClusterDimension;
+        la[0].val.clusterDim.x = CL;
+        la[0].val.clusterDim.y = 1;
+        la[0].val.clusterDim.z = 1;
+        cfg.attrs = la;
+        cfg.numAttrs = 1;
+        if (c.device >= 64) return GRFT_EUNSUPPORTED;
+        if (max_clusters[c.device] <= 0) {
+            cfg.gridDim = dim3(CL * (c.num_sms / CL));
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_ds_tc<BN, ST, CL, BK>, &cfg) != cudaSuccess || n <= 0)
+                return GRFT_ECUDA;
+            max_clusters[c.device] = n;
+        }
+        slots = max_clusters[c.device];
+    }
+    const int groups = bb.total_tiles < slots ? bb.total_tiles : slots;
+    cfg.gridDim = dim3(CL * groups);
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
-    k_ds_tc<BN, ST><<<grid, TC_THREADS, tc_smem_bytes(BN, ST), c.stream>>>(mzh, mzl, mbh, mbl, bb);
+    if (cudaLaunchKernelEx(&cfg, k_ds_tc<BN, ST, CL, BK>, mzh, mzl, mbh, mbl, bb) != cudaSuccess)
+        return GRFT_ECUDA;
     return check_launch();
 }
 
-int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const CUtensorMap &mzh,
-                        const CUtensorMap &mzl, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
-    if (variant == 1) return launch_gemm<128, 3>(c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
-    return launch_gemm<256, 2>(c, b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo,
+                        long zrows, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    switch (variant) {
+        case 1: return launch_gemm<128, 3, 1, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 2: return launch_gemm<256, 2, 2, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 3: return launch_gemm<256, 4, 1, 32>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 4: return launch_gemm<256, 4, 2, 32>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        default: return launch_gemm<256, 2, 1, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+    }
 }
 
 // One round = the split kernel over every (item, cell, bin tile) of the batch, then the
@@ -650,14 +753,6 @@ struct Round {
     long rows;
 };
 
-bool encode_split_maps(uint16_t *Zhi, uint16_t *Zlo, long rows, int Mpad, CUtensorMap &mzh, CUtensorMap &mzl) {
-    const uint64_t kdim = 2ull * Mpad;
-    return encode_tma_2d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, kdim, (uint64_t)rows, kdim * 2,
-                         TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B) &&
-           encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)rows, kdim * 2,
-                         TC_BK, TC_BM, CU_TENSOR_MAP_SWIZZLE_128B);
-}
-
 int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
     KernelTimer kt(c, GRFT_KERNEL_SPLIT);
     k_coarse_split<<<b.total_ctas, SP_THREADS, 0, c.stream>>>(b, Zhi, Zlo);
@@ -666,16 +761,14 @@ int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
 
 int launch_round_gemm(const Ctx &c, const Round &rd, int Mpad, int Fpad, const uint16_t *Bhi,
                       const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
-    CUtensorMap mzh, mzl;
-    if (!encode_split_maps(Zhi, Zlo, rd.rows, Mpad, mzh, mzl)) return GRFT_ECUDA;
     if (variant < 0) {   // autotune: time the tile shapes on this round, keep the fastest
         variant = tune_variant(c, rd.b, [&](int v) {
-            return launch_gemm_variant(v, c, rd.b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+            return launch_gemm_variant(v, c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Fpad);
         });
         if (variant < 0) return GRFT_ECUDA;
         tune_store(key, variant);
     }
-    return launch_gemm_variant(variant, c, rd.b, mzh, mzl, Bhi, Blo, Mpad, Fpad);
+    return launch_gemm_variant(variant, c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Fpad);
 }
 
 // Side stream and events of the split/contraction pipeline, created once per device.
