@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     // current stage is converted.
     __shared__ int s_rho[SP_TAB_MAX];
     __shared__ float2 s_w[SP_TAB_MAX];
+    __shared__ int s_rng[2];                    // least and greatest bin shift of the cell
     const TcItem &p = B.it[find_item_cta(B, blockIdx.x)];
     const int local = blockIdx.x - p.cta0;
     const int mt = local % p.tiles_m;
@@ -280,9 +281,24 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     const int nbase = p.r0_begin + j;
     const bool tab_smem = !p.Z && p.M <= SP_TAB_MAX;
     if (tab_smem) {
+        if (tid == 0) {
+            s_rng[0] = 0x7fffffff;
+            s_rng[1] = -0x7fffffff - 1;
+        }
+        __syncthreads();
+        int lo = 0x7fffffff, hi = -0x7fffffff - 1;
         for (int m = tid; m < p.M; m += SP_THREADS) {
-            s_rho[m] = __ldg(B.rho + tab + m);
+            const int rr = __ldg(B.rho + tab + m);
+            s_rho[m] = rr;
             s_w[m] = __ldg(B.w + tab + m);
+            lo = min(lo, rr);
+            hi = max(hi, rr);
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) {
+            atomicMin(&s_rng[0], lo);
+            atomicMax(&s_rng[1], hi);
         }
         __syncthreads();
     }
@@ -291,6 +307,58 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     const size_t row = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j;
     uint16_t *zh = Zhi + row * (size_t)B.zld + g * 8;
     uint16_t *zl = Zlo + row * (size_t)B.zld + g * 8;
+
+    auto split_store = [&](int kt, const float (&re)[8], const float (&im)[8]) {
+        uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
+            split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
+        }
+        const int o = kt * TC_BK;
+        st_global_v4(zh + o, rh[0], rh[1], rh[2], rh[3]);
+        st_global_v4(zl + o, rl[0], rl[1], rl[2], rl[3]);
+        st_global_v4(zh + o + 32, ih[0], ih[1], ih[2], ih[3]);
+        st_global_v4(zl + o + 32, il[0], il[1], il[2], il[3]);
+    };
+
+    // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
+    // of the tile is inside the r0 range and every gathered bin is inside the echo, so the
+    // loop carries no bound checks.
+    const int j0 = mt * TC_BM;
+    if (tab_smem && (p.M % 32) == 0 && j0 + TC_BM <= p.r0_count &&
+        p.r0_begin + j0 + s_rng[0] >= 0 && p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
+        const float2 *src = p.echo + nbase;
+        const long N = p.N;
+        const int KT = p.KT;
+        auto ld = [&](int kt, float2 (&v)[8]) {
+            const int m0 = kt * 32 + g * 8;
+            const float2 *rowp = src + (long)m0 * N;
+#pragma unroll
+            for (int i = 0; i < 8; ++i, rowp += N) v[i] = __ldg(rowp + s_rho[m0 + i]);
+        };
+        auto cv = [&](int kt, const float2 (&v)[8]) {
+            const int m0 = kt * 32 + g * 8;
+            float re[8], im[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 x = cmul(v[i], s_w[m0 + i]);
+                re[i] = x.x;
+                im[i] = x.y;
+            }
+            split_store(kt, re, im);
+        };
+        float2 va[8], vb[8];
+        ld(0, va);
+        for (int kt = 0; kt < KT; kt += 2) {    // the two buffers alternate
+            if (kt + 1 < KT) ld(kt + 1, vb);
+            cv(kt, va);
+            if (kt + 1 >= KT) break;
+            if (kt + 2 < KT) ld(kt + 2, va);
+            cv(kt + 1, vb);
+        }
+        return;
+    }
 
     auto load8 = [&](int kt, float2 (&v)[8]) {
 #pragma unroll
@@ -318,26 +386,13 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
             re[i] = x.x;
             im[i] = x.y;
         }
-        uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
-            split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
-        }
-        const int o = kt * TC_BK;
-        st_global_v4(zh + o, rh[0], rh[1], rh[2], rh[3]);
-        st_global_v4(zl + o, rl[0], rl[1], rl[2], rl[3]);
-        st_global_v4(zh + o + 32, ih[0], ih[1], ih[2], ih[3]);
-        st_global_v4(zl + o + 32, il[0], il[1], il[2], il[3]);
+        split_store(kt, re, im);
     };
-    float2 va[8], vb[8];
-    load8(0, va);
-    for (int kt = 0; kt < p.KT; kt += 2) {      // the two buffers alternate
-        if (kt + 1 < p.KT) load8(kt + 1, vb);
-        store8(kt, va);
-        if (kt + 1 >= p.KT) break;
-        if (kt + 2 < p.KT) load8(kt + 2, va);
-        store8(kt + 1, vb);
+    // general path (edge tiles, materialised Z, partial pulse groups): one stage at a time
+    for (int kt = 0; kt < p.KT; ++kt) {
+        float2 v[8];
+        load8(kt, v);
+        store8(kt, v);
     }
 }
 
