@@ -2,11 +2,14 @@
 //   Y[h][n0] = e0(n0) * sum_m s[m][n0 + rho_h(m)] * w_h(m)
 // FP32 SIMT.  A CTA owns a group of PL_H hypotheses and a tile of PL_THREADS*PL_J range
 // bins; each thread accumulates PL_J bins (32 apart, so warp accesses are contiguous) for
-// all PL_H hypotheses.  Bins and
-// phases come from a per-chunk table (FP64-built).  Consecutive hypotheses of a group are
-// neighbouring accelerations, whose bin shift is nearly always the same at a given pulse:
-// the echo samples are reloaded only when the (CTA-uniform) shift changes, so the inner
-// loop is FFMA-bound rather than load-bound.
+// all PL_H hypotheses.  Bins and phases come from a per-chunk table (FP64-built).
+// Consecutive hypotheses of a group are neighbouring accelerations, whose bin shift is
+// nearly always the same at a given pulse: a per-pulse flag marks the pulses where all of
+// them share the first one's shift (one row of samples, no per-hypothesis check); at the
+// others the samples are reloaded when the (CTA-uniform) shift changes.  The complex
+// multiply-adds run as paired FP32 FMAs (fma.rn.f32x2 on (re, im) accumulator pairs, with
+// the phase and the phase times j staged in shared memory), which rounds exactly as the
+// scalar form and halves the FMA instruction count.
 #include <climits>
 
 #include "internal.cuh"
@@ -21,12 +24,29 @@ constexpr int PL_H = 8;
 constexpr int PL_MCHUNK = 128;
 constexpr int PL_TILE = PL_THREADS * PL_J;
 
+// Paired FP32 arithmetic (two independent IEEE fma.rn per instruction).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ void ffma2(uint64_t &acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     const float2 *__restrict__ echo, int M, int N, const int32_t *__restrict__ rho_tab,
     const float2 *__restrict__ w_tab, int nh, int r0_begin, int r0_count,
     const float2 *__restrict__ e0, float2 *__restrict__ Y, float *__restrict__ P) {
     __shared__ int s_rho[PL_MCHUNK][PL_H];
-    __shared__ float2 s_w[PL_MCHUNK][PL_H];
+    __shared__ alignas(16) float2 s_w[PL_MCHUNK][PL_H];     // w
+    __shared__ alignas(16) float2 s_jw[PL_MCHUNK][PL_H];    // j w = (-w.im, w.re)
+    __shared__ int s_same[PL_MCHUNK];            // every hypothesis of the group shifts like the first
 
     const int h0 = blockIdx.y * PL_H;
     const int nhl = min(PL_H, nh - h0);
@@ -35,21 +55,30 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     const int j0 = blockIdx.x * PL_TILE + (threadIdx.x >> 5) * (32 * PL_J) + (threadIdx.x & 31);
     const int n0 = r0_begin + j0;
 
-    float2 acc[PL_H][PL_J];
+    uint64_t acc[PL_H][PL_J];                  // (re, im) pairs for the paired FMA
 #pragma unroll
     for (int h = 0; h < PL_H; ++h)
 #pragma unroll
-        for (int j = 0; j < PL_J; ++j) acc[h][j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < PL_J; ++j) acc[h][j] = 0ull;
 
     for (int mc = 0; mc < M; mc += PL_MCHUNK) {
         const int mn = min(PL_MCHUNK, M - mc);
         __syncthreads();
         for (int i = threadIdx.x; i < PL_H * PL_MCHUNK; i += PL_THREADS) {
-            int h = i / PL_MCHUNK, mm = i % PL_MCHUNK;
+            const int h = i % PL_H, mm = i / PL_H;   // consecutive threads: consecutive smem words
             bool ok = h < nhl && mm < mn;
             long o = (long)(h0 + h) * M + mc + mm;
+            const float2 wv = ok ? w_tab[o] : make_float2(0.f, 0.f);
             s_rho[mm][h] = ok ? rho_tab[o] : 0;
-            s_w[mm][h] = ok ? w_tab[o] : make_float2(0.f, 0.f);
+            s_w[mm][h] = wv;
+            s_jw[mm][h] = make_float2(-wv.y, wv.x);
+        }
+        __syncthreads();
+        if (threadIdx.x < PL_MCHUNK) {
+            int same = 1;
+#pragma unroll
+            for (int h = 1; h < PL_H; ++h) same &= s_rho[threadIdx.x][h] == s_rho[threadIdx.x][0];
+            s_same[threadIdx.x] = same;
         }
         __syncthreads();
         auto load_row = [&](int mm, int r, float2 (&v)[PL_J]) {
@@ -61,39 +90,72 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
                 v[j] = ((unsigned)n < (unsigned)N) ? __ldg(row + n) : make_float2(0.f, 0.f);
             }
         };
-        // two pulses of look-ahead: the samples of pulses mm+1 and mm+2 (at the first
-        // hypothesis' shift) are in flight while pulse mm is accumulated
-        int r1 = s_rho[0][0], r2 = mn > 1 ? s_rho[1][0] : 0;
-        float2 pre1[PL_J], pre2[PL_J];
-        load_row(0, r1, pre1);
-        if (mn > 1) load_row(1, r2, pre2);
-        for (int mm = 0; mm < mn; ++mm) {
-            int prev = r1;
-            float2 sv[PL_J];
+        // Accumulate pulse mm whose samples (at the first hypothesis' shift) are in sv.
+        auto pulse = [&](int mm, const float2 (&sv0)[PL_J]) {
+            // (re, re) and (im, im) of every sample, reused by all hypotheses of the pulse
+            uint64_t sr[PL_J], si[PL_J];
 #pragma unroll
             for (int j = 0; j < PL_J; ++j) {
-                sv[j] = pre1[j];
-                pre1[j] = pre2[j];
+                sr[j] = pack2(sv0[j].x, sv0[j].x);
+                si[j] = pack2(sv0[j].y, sv0[j].y);
             }
-            r1 = r2;
-            if (mm + 2 < mn) {
-                r2 = s_rho[mm + 2][0];
-                load_row(mm + 2, r2, pre2);
+            if (s_same[mm]) {                // CTA-uniform: one row of samples for all hypotheses
+                const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0]);
+                const ulonglong2 *jp = reinterpret_cast<const ulonglong2 *>(&s_jw[mm][0]);
+#pragma unroll
+                for (int h2 = 0; h2 < PL_H / 2; ++h2) {
+                    const ulonglong2 w2 = wp[h2], j2 = jp[h2];
+#pragma unroll
+                    for (int j = 0; j < PL_J; ++j) {
+                        ffma2(acc[2 * h2][j], si[j], j2.x);
+                        ffma2(acc[2 * h2][j], sr[j], w2.x);
+                        ffma2(acc[2 * h2 + 1][j], si[j], j2.y);
+                        ffma2(acc[2 * h2 + 1][j], sr[j], w2.y);
+                    }
+                }
+                return;
             }
+            int prev = s_rho[mm][0];
 #pragma unroll
             for (int h = 0; h < PL_H; ++h) {
                 const int r = s_rho[mm][h];
                 if (r != prev) {             // CTA-uniform branch
                     prev = r;
+                    float2 sv[PL_J];
                     load_row(mm, r, sv);
+#pragma unroll
+                    for (int j = 0; j < PL_J; ++j) {
+                        sr[j] = pack2(sv[j].x, sv[j].x);
+                        si[j] = pack2(sv[j].y, sv[j].y);
+                    }
                 }
-                const float2 w = s_w[mm][h];
+                const uint64_t w = *reinterpret_cast<const uint64_t *>(&s_w[mm][h]);
+                const uint64_t jw = *reinterpret_cast<const uint64_t *>(&s_jw[mm][h]);
+                // acc += im * (j w), then acc += re * w: per component the same two
+                // roundings, in the same order, as fmaf(re, w, fmaf(-im, w.im, acc)) etc.
 #pragma unroll
                 for (int j = 0; j < PL_J; ++j) {
-                    acc[h][j].x = fmaf(sv[j].x, w.x, fmaf(-sv[j].y, w.y, acc[h][j].x));
-                    acc[h][j].y = fmaf(sv[j].x, w.y, fmaf(sv[j].y, w.x, acc[h][j].y));
+                    ffma2(acc[h][j], si[j], jw);
+                    ffma2(acc[h][j], sr[j], w);
                 }
             }
+        };
+        // two pulses of look-ahead, two buffers that alternate: the samples of pulses
+        // mm+1 and mm+2 are in flight while pulse mm is accumulated
+        float2 pa[PL_J], pb[PL_J];
+        load_row(0, s_rho[0][0], pa);
+        if (mn > 1) load_row(1, s_rho[1][0], pb);
+        for (int mm = 0; mm < mn; mm += 2) {
+            float2 sv[PL_J];
+#pragma unroll
+            for (int j = 0; j < PL_J; ++j) sv[j] = pa[j];
+            if (mm + 2 < mn) load_row(mm + 2, s_rho[mm + 2][0], pa);
+            pulse(mm, sv);
+            if (mm + 1 >= mn) break;
+#pragma unroll
+            for (int j = 0; j < PL_J; ++j) sv[j] = pb[j];
+            if (mm + 3 < mn) load_row(mm + 3, s_rho[mm + 3][0], pb);
+            pulse(mm + 1, sv);
         }
     }
 
@@ -105,9 +167,10 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
 #pragma unroll
         for (int h = 0; h < PL_H; ++h) {
             if (h >= nhl) break;
+            const float2 a = unpack2(acc[h][j]);
             const long o = (long)(h0 + h) * r0_count + jj;
-            if (Y) Y[o] = cmul(e, acc[h][j]);
-            if (P) P[o] = acc[h][j].x * acc[h][j].x + acc[h][j].y * acc[h][j].y;
+            if (Y) Y[o] = cmul(e, a);
+            if (P) P[o] = a.x * a.x + a.y * a.y;
         }
     }
 }
