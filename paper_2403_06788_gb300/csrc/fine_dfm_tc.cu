@@ -252,6 +252,29 @@ __device__ __forceinline__ void st_global_v4(uint16_t *dst, uint32_t a, uint32_t
     asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "r"(a), "r"(b), "r"(c), "r"(d)
                  : "memory");
 }
+// L2 policies of kernel a: the split operand streams through L2 (evict first) so that the
+// echo rows every cell gathers from stay resident (evict last).
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_global_v4_hint(uint16_t *dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                                  uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(a), "r"(b), "r"(c),
+                 "r"(d), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float2 ld_global_nc_hint(const float2 *src, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(src), "l"(pol));
+    return v;
+}
 
 __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_constant__ TcBatch B,
                                                                 uint16_t *__restrict__ Zhi,
@@ -308,6 +331,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     uint16_t *zh = Zhi + row * (size_t)B.zld + g * 8;
     uint16_t *zl = Zlo + row * (size_t)B.zld + g * 8;
 
+    const uint64_t pol_z = l2_policy_evict_first();
     auto split_store = [&](int kt, const float (&re)[8], const float (&im)[8]) {
         uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
@@ -316,10 +340,10 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
             split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
         }
         const int o = kt * TC_BK;
-        st_global_v4(zh + o, rh[0], rh[1], rh[2], rh[3]);
-        st_global_v4(zl + o, rl[0], rl[1], rl[2], rl[3]);
-        st_global_v4(zh + o + 32, ih[0], ih[1], ih[2], ih[3]);
-        st_global_v4(zl + o + 32, il[0], il[1], il[2], il[3]);
+        st_global_v4_hint(zh + o, rh[0], rh[1], rh[2], rh[3], pol_z);
+        st_global_v4_hint(zl + o, rl[0], rl[1], rl[2], rl[3], pol_z);
+        st_global_v4_hint(zh + o + 32, ih[0], ih[1], ih[2], ih[3], pol_z);
+        st_global_v4_hint(zl + o + 32, il[0], il[1], il[2], il[3], pol_z);
     };
 
     // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
@@ -331,11 +355,12 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
         const float2 *src = p.echo + nbase;
         const long N = p.N;
         const int KT = p.KT;
+        const uint64_t pol_e = l2_policy_evict_last();
         auto ld = [&](int kt, float2 (&v)[8]) {
             const int m0 = kt * 32 + g * 8;
             const float2 *rowp = src + (long)m0 * N;
 #pragma unroll
-            for (int i = 0; i < 8; ++i, rowp += N) v[i] = __ldg(rowp + s_rho[m0 + i]);
+            for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
         };
         auto cv = [&](int kt, const float2 (&v)[8]) {
             const int m0 = kt * 32 + g * 8;
