@@ -172,6 +172,129 @@ def run_reference(args):
     return 0
 
 
+def _timed(fn, reps, stream):
+    """Average CUDA-event time (ms) of fn() over reps calls after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_suite(args):
+    """The other workloads of the method, one JSON line: the M=2048 x N=8192 precision case
+    (one coarse-v row of cells per call, both split precisions, sampled error against the
+    oracle), 64 uneven CPIs in one graph-captured batched call (1024 range bins of interest
+    per CPI), and the differentiation pipeline at M=1024 x N=4096 (forward, top-1000 CFAR,
+    adjoint, 20 refinement steps)."""
+    import torch
+    import paper_2403_06788_gb300 as g
+    import synth
+    dev = torch.device("cuda", 0)
+    g.load()
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    # ------------------------------------------------ precision workload, one coarse-v row
+    sc = synth.ds_precision_m2048()
+    R, ds = sc.radar, sc.ds
+    s = synth.make_echo(R, sc.targets, sc.seed)
+    echo = torch.from_numpy(s).to(dev)
+    t = max(sc.targets, key=lambda t: abs(t.amp))
+    pg = ds.plain_equivalent()
+    i_row = min(int((t.v - pg.v.start) // ds.vc.step), ds.vc.count - 1)
+    cb, cc = i_row * ds.ac.count, ds.ac.count
+    nv, na = ds.Fv, ds.ac.count * ds.Fa
+    Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device=dev)
+    units = cc * ds.n_fine * ds.r0_count * R.M
+    prec = {}
+    rng = np.random.default_rng(0)
+    vloc, af = rng.integers(0, nv, 6), rng.integers(0, na, 6)
+    Yo = None
+    if not args.no_cpu:
+        import oracle
+        from oracle.wrap import ds_rows_of_canonical
+        cell, fine = ds_rows_of_canonical(ds, np.asarray(vloc) + i_row * ds.Fv, np.asarray(af))
+        Yo = oracle.dsgrft_rows(R, s, ds, cell, fine)
+    for p in ("bf16x3", "fp16x3"):
+        ms = _timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, cb, cc, p, Y, None), 3, stream)
+        err = None
+        if Yo is not None:
+            Yg = Y[torch.as_tensor(vloc, device=dev), torch.as_tensor(af, device=dev)].cpu().numpy()
+            err = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
+        prec[p] = {"ms_per_call": ms, "value": units / (1e-3 * ms), "max_rel_peak_err_sampled": err}
+    out["precision_m2048"] = {"workload": "DS-GRFT M=2048 x N=8192, coarse 32 x 8, fine 256 x 64; one call = "
+                                          "one coarse-v row (8 cells, 2.2e12 hypothesis-pulses, Y written)",
+                              "unit": UNIT, "full_grid_calls": ds.vc.count, **prec}
+    del Y, echo
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ 64 uneven CPIs, one captured batched call
+    cpis = synth.ds_batch(n_cpi=64)
+    grid = cpis[0].ds
+    nvb, nab = grid.vc.count * grid.Fv, grid.ac.count * grid.Fa
+    batch, units = [], 0
+    for sc in cpis:
+        N = sc.radar.N
+        r0c = min(1024, N)
+        e = torch.from_numpy(synth.make_echo(sc.radar, sc.targets, sc.seed)).to(dev)
+        P = torch.empty((nvb, nab, r0c), device=dev)
+        batch.append({"echo": e, "P": P, "Y": None, "r0_begin": (N - r0c) // 2, "r0_count": r0c})
+        units += nvb * nab * r0c * sc.radar.M
+    g.dsgrft_fine_dfm_batched(cpis[0].radar, grid, batch, "bf16x3")         # sizes the workspace, tunes
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        g.dsgrft_fine_dfm_batched(cpis[0].radar, grid, batch, "bf16x3")
+    ms = _timed(graph.replay, 3, stream)
+    out["batch_64"] = {"workload": "64 CPIs, M ~ U{256..2048}, N ~ U{1024..8192}, coarse 32 x 8, fine 64 x 16, "
+                                   "1024 range bins of interest per CPI, one graph-captured batched call",
+                       "unit": UNIT, "ms_per_call": ms, "value": units / (1e-3 * ms),
+                       "status": g.grft_sync_status()}
+    del batch, graph
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ differentiation pipeline
+    sc = synth.ds_adjoint_m1024()
+    R, ds = sc.radar, sc.ds
+    pg = ds.plain_equivalent()
+    echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
+    P = torch.empty((ds.vc.count * ds.Fv, ds.ac.count * ds.Fa, ds.r0_count), device=dev)
+    det = torch.zeros(1000 * g._abi.DET_BYTES, dtype=torch.uint8, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    cfar = synth.CFAR(2, 16, 1e-6)
+    units = ds.n_cells * ds.n_fine * ds.r0_count * R.M
+    ms_fwd = _timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.n_cells, "bf16x3", None, P), 3, stream)
+    ms_det = _timed(lambda: g.detect_peaks(P, cfar, 1000, axes=pg, dr_m=R.dr_m, out=det, n_out=nout), 3, stream)
+    dets, total = g.decode_detections(det, nout, 1000)
+    th0 = torch.from_numpy(np.stack([dets["r0_m"], dets["v"], dets["a"]], axis=1).astype(np.float64)).to(dev)
+    K = th0.shape[0]
+    gt = torch.empty((K, 3), dtype=torch.float64, device=dev)
+    ms_adj = _timed(lambda: g.dsgrft_backward(R, echo, th0, 1, grad_theta=gt), 3, stream)
+    cellw = [R.dr_m, pg.v.step, pg.a.step]
+    Pr = torch.empty(K, device=dev)
+    th = th0.clone()
+
+    def refine():
+        th.copy_(th0)
+        g.dsgrft_refine(R, echo, th, cellw, 20, 1, Pr)
+    ms_ref = _timed(refine, 3, stream)
+    out["differentiation_m1024"] = {
+        "workload": "DS-GRFT M=1024 x N=4096 (2^30 hypotheses), top-1000 CA-CFAR, adjoint at the detections, "
+                    "20 ascent steps (linear gather)",
+        "detections": int(K), "forward_ms": ms_fwd, "forward_value": units / (1e-3 * ms_fwd), "unit": UNIT,
+        "detect_ms": ms_det, "adjoint_ms": ms_adj, "refine_20_steps_ms": ms_ref,
+        "status": g.grft_sync_status()}
+    print(json.dumps({"suite": out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,11 +310,17 @@ def main():
     ap.add_argument("--cells", type=int, default=0,
                     help="restrict to the first N coarse cells (small profiling case; not a bench line)")
     ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--suite", action="store_true",
+                    help="time the precision, batching and differentiation workloads (one JSON line)")
+    ap.add_argument("--coarse-rm-steps", type=int, default=3,
+                    help="timed calls of the standalone coarse-RM gather (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite:
+        return run_suite(args)
 
     import torch
     import torch.distributed as dist
@@ -307,6 +436,27 @@ def main():
         torch.cuda.synchronize()
         plain_ms = a_ev.elapsed_time(b_ev) / args.plain_steps
 
+    # ---------------------------------------------------------------- standalone coarse RM gather
+    # (kernel a materialising Z = s[m][n0 + rho_c(m)] w_c(m) for every cell: HBM-write bound)
+    crm_ms, crm_bytes = None, 0
+    if args.coarse_rm_steps > 0:
+        Z = torch.empty((ncell, R.M, ds.r0_count), dtype=torch.complex64, device=dev)
+        g.dsgrft_coarse_rm(R, echo, ds, 0, ncell, Z)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(args.coarse_rm_steps):
+            flush.fill_(1)
+            a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_ev.record(stream)
+            g.dsgrft_coarse_rm(R, echo, ds, 0, ncell, Z)
+            b_ev.record(stream)
+            torch.cuda.synchronize()
+            tot += a_ev.elapsed_time(b_ev)
+        crm_ms = tot / args.coarse_rm_steps
+        crm_bytes = Z.numel() * 8 + echo.numel() * 8
+        del Z
+        torch.cuda.empty_cache()
+
     # ---------------------------------------------------------------- accuracy vs the oracle (sampled)
     acc = None
     if rank == 0 and not args.no_cpu:
@@ -356,6 +506,25 @@ def main():
         # FP32 SIMT path: bound by FFMA issue, 152 SMs x 128 FMA/clk x 2 flop x max clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     value = world * units / (1e-3 * total_ms / args.steps)
+    # every hot kernel against its own bound: algorithmic bytes (HBM) or FLOP / event time
+    hbm = peaks.get("hbm_gbs", 6678.5)
+    fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    def _bw(name, nbytes, ms):
+        if not ms:
+            return None
+        gbs = nbytes / (1e-3 * ms) / 1e9
+        return {"bound": "hbm", "ms": ms, "achieved": gbs, "unit": "GB/s", "peak": hbm, "frac": gbs / hbm,
+                "algorithmic_bytes": nbytes}
+    hyps_step = nv * na * pg.r0_count
+    kernel_rooflines = {
+        "split (kernel a, split form)": _bw("split", ncell * ds.r0_count * R.M * 8 + echo.numel() * 8,
+                                            ktime["split"][1] / args.steps if ktime["split"][0] else None),
+        "cfar": _bw("cfar", hyps_step * 4, ktime["cfar"][1] / args.steps if ktime["cfar"][0] else None),
+        "coarse_rm (kernel a, standalone)": _bw("coarse_rm", crm_bytes, crm_ms) if crm_ms else None,
+        "plain_grft": None if plain_ms is None else {
+            "bound": "fp32 fma", "ms": plain_ms, "achieved": 8 * plain_units / (1e-3 * plain_ms) / 1e12,
+            "unit": "TFLOP/s", "peak": fma_peak, "frac": 8 * plain_units / (1e-3 * plain_ms) / 1e12 / fma_peak},
+    }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -383,6 +552,7 @@ def main():
         "plain_grft": None if plain_ms is None else {
             "value": plain_units / (1e-3 * plain_ms), "ms_per_step": plain_ms,
             "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units)},
+        "kernels": kernel_rooflines,
         "max_rel_peak_err": acc,
         "detections": {"total": ndet, "top1_p": float(dets["p"][0]) if len(dets) else None},
         "status": st,
