@@ -291,6 +291,26 @@ def run_suite(args):
         "detections": int(K), "forward_ms": ms_fwd, "forward_value": units / (1e-3 * ms_fwd), "unit": UNIT,
         "detect_ms": ms_det, "adjoint_ms": ms_adj, "refine_20_steps_ms": ms_ref,
         "status": g.grft_sync_status()}
+    del P, echo
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ FFT form of the fine stage vs the dense form
+    sc = synth.ds_m512()
+    R = sc.radar
+    L, Fv = 512, 96                                   # fine velocity step = one bin of 512
+    vstep = R.wavelength * R.prf_hz * Fv / (2 * L)
+    ds = synth.DSGrid(0, R.N, synth.Axis(-300.0 + vstep / 2, vstep, 32), sc.ds.ac, Fv, sc.ds.Fa)
+    echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
+    P = torch.empty((ds.vc.count * Fv, ds.ac.count * ds.Fa, ds.r0_count), device=dev)
+    units = ds.n_cells * ds.n_fine * ds.r0_count * R.M
+    ms_fft = _timed(lambda: g.dsgrft_fine_dfm_fft(R, echo, ds, 0, ds.n_cells, None, P), 3, stream)
+    ms_dense = _timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.n_cells, "bf16x3", None, P), 3, stream)
+    out["fft_form_m512"] = {
+        "workload": "DS-GRFT M=512 x N=4096, coarse 32 x 8, fine 96 x 16 (fine velocity step = one bin of a "
+                    "512-point transform), 1.6e9 hypotheses, P written",
+        "unit": UNIT, "fft_ms": ms_fft, "fft_value": units / (1e-3 * ms_fft),
+        "dense_bf16x3_ms": ms_dense, "dense_value": units / (1e-3 * ms_dense),
+        "status": g.grft_sync_status()}
     print(json.dumps({"suite": out}))
     return 0
 

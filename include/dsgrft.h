@@ -133,7 +133,8 @@ enum {
     GRFT_KERNEL_CFAR = 6,
     GRFT_KERNEL_TOPK = 7,
     GRFT_KERNEL_ADJOINT = 8,       /* trajectory sum, adjoint, refinement */
-    GRFT_KERNEL_COUNT = 9
+    GRFT_KERNEL_CONTRACT_FFT = 9,  /* FFT form of the fine stage (dsgrft_fine_dfm_fft) */
+    GRFT_KERNEL_COUNT = 10
 };
 int grft_timing(int enable);
 int grft_timing_get(int kernel, int32_t *launches, double *total_ms);
@@ -198,6 +199,18 @@ int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_d
 int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo,
                     const grft_dsgrid *grid, int32_t cell_begin, int32_t cell_count,
                     grft_precision precision, grft_c32 *Y, float *P, void *stream);
+
+/* Fine Doppler-migration correction in the FFT form of the GFT (Def. 1, Alg. 2): per cell,
+ * range bin and fine acceleration, the coarse-corrected pulses are multiplied by the
+ * acceleration dechirp exp(j 4 pi (da_q t_m^2 / 2) / lambda) and transformed over slow
+ * time; transform bin (k - Fv/2) mod L is fine velocity k.  The grid's fine velocity step
+ * vc.step / Fv must be one Doppler bin of an L-point transform, lambda PRF / (2 L), with
+ * L = 256 or 512, M <= L (zero padded), Fv <= L and Fv even; otherwise GRFT_EUNSUPPORTED
+ * is returned before anything is enqueued.  Same hypotheses, output layout and argument
+ * meaning as dsgrft_fine_dfm with Z = NULL (the gather is fused); FP32 SIMT arithmetic,
+ * equal to the dense form to FP32 rounding. */
+int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                        int32_t cell_begin, int32_t cell_count, grft_c32 *Y, float *P, void *stream);
 
 /* Many CPIs (uneven M, N) in one persistent launch (graph-capturable after a first
  * uncaptured call of the same shape).  radar's M and N are ignored (per item); grid's

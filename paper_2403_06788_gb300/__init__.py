@@ -21,7 +21,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
-           "dsgrft_fine_dfm_batched", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
+           "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
            "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
 
@@ -150,6 +150,15 @@ def dsgrft_fine_dfm(radar, Z, echo, grid, cell_begin, cell_count, precision, Y=N
                                  _ptr(echo, torch.complex64, "echo"), C.byref(G), int(cell_begin),
                                  int(cell_count), _precision(precision), _ptr(Y, torch.complex64, "Y"),
                                  _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft_fine_dfm")
+
+
+def dsgrft_fine_dfm_fft(radar, echo, grid, cell_begin, cell_count, Y=None, P=None, stream=None):
+    """FFT form of the fine stage (Alg. 2); the grid's fine velocity step must be one Doppler
+    bin of a 256- or 512-point transform (else GrftError with GRFT_EUNSUPPORTED)."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dsgrft_fine_dfm_fft(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
+                                     int(cell_begin), int(cell_count), _ptr(Y, torch.complex64, "Y"),
+                                     _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft_fine_dfm_fft")
 
 
 def dsgrft_fine_dfm_batched(radar, grid, items, precision, stream=None):

@@ -440,6 +440,46 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
 }
 
+int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                        int32_t cell_begin, int32_t cell_count, grft_c32 *Y, float *P, void *stream) {
+    if (!radar_ok(radar) || !echo || (!Y && !P) || !dsgrid_ok(grid, radar) || cell_begin < 0 ||
+        cell_count < 0 || (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count ||
+        cell_count > 65535)
+        return GRFT_EINVAL;
+    // transform length: the fine velocity step must be lambda PRF / (2 L) exactly
+    const double Lr = radar->c_mps * radar->prf_hz * grid->Fv / (2.0 * radar->fc_hz * grid->vc.step);
+    const int L = (int)std::lround(Lr);
+    if (!std::isfinite(Lr) || (L != 256 && L != 512) || std::fabs(Lr - L) > 1e-6 * L || radar->M > L ||
+        grid->Fv > L || (grid->Fv % 2) != 0)
+        return GRFT_EUNSUPPORTED;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(*radar);
+    const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)cell_count * R.M * sizeof(float2));
+    const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
+    const size_t ch_bytes = align_up((size_t)grid->Fa * L * sizeof(float2));
+    unsigned char *ws = (unsigned char *)workspace(c, rho_bytes + w_bytes + e0_bytes + ch_bytes);
+    if (!ws) return GRFT_ENOMEM;
+    int32_t *rho = (int32_t *)ws;
+    float2 *w = (float2 *)(ws + rho_bytes);
+    float2 *e0 = (float2 *)(ws + rho_bytes + w_bytes);
+    float2 *chirp = (float2 *)(ws + rho_bytes + w_bytes + e0_bytes);
+    if ((e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
+    if ((e = launch_range_phase(c, R, grid->r0_begin, grid->r0_count, e0))) return e;
+    if ((e = launch_gft_chirp(c, R, *grid, L, chirp))) return e;
+    DsOut out;
+    out.Y = (float2 *)Y;
+    out.P = P;
+    out.cell_begin = cell_begin;
+    out.i0 = cell_begin / grid->ac.count;
+    out.na_c = grid->ac.count;
+    out.Fv = grid->Fv;
+    out.Fa = grid->Fa;
+    return launch_ds_fft(c, R, (const float2 *)echo, *grid, cell_count, rho, w, chirp, e0, L, out);
+}
+
 int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
                             const grft_batch_item *items, int32_t n_items, grft_precision precision,
                             void *stream) {

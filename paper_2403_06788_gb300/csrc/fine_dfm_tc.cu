@@ -248,10 +248,6 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64
 }
 
 // =========================================================================== kernel a
-__device__ __forceinline__ void st_global_v4(uint16_t *dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
 // L2 policies of kernel a: the split operand streams through L2 (evict first) so that the
 // echo rows every cell gathers from stay resident (evict last).
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {

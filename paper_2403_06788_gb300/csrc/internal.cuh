@@ -110,6 +110,12 @@ struct DsOut {           // output placement of a DS call (v-slab of the canonic
     int Fv, Fa;
 };
 
+// FFT form of the fine stage (fine_dfm_fft.cu): chirp[Fa][L], then the transform kernel.
+int launch_gft_chirp(const Ctx &, const RadarD &, const grft_dsgrid &, int L, float2 *chirp);
+int launch_ds_fft(const Ctx &, const RadarD &, const float2 *echo, const grft_dsgrid &, int cell_count,
+                  const int32_t *rho, const float2 *w, const float2 *chirp, const float2 *e0, int L,
+                  const DsOut &out);
+
 int launch_ds_simt(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
                    const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
                    const float2 *D, const float2 *e0, const DsOut &out);

@@ -155,6 +155,34 @@ def test_coarse_rm_then_dechirp_sum_equals_dsgrft():
                 np.testing.assert_allclose(y, Yds[i * ds.Fv + k, l * ds.Fa + q], rtol=0, atol=1e-10)
 
 
+def test_fft_form_of_the_fine_stage_equals_dsgrft_rows():
+    """Alg. 2 (GFT): on a fine grid whose velocity step is one Doppler bin of an L-point
+    transform over slow time (dv = lambda PRF / (2 L)), the fine stage is the dechirp in
+    acceleration followed by a DFT over pulses, read at bins (k - Fv/2) mod L.  numpy's
+    inverse FFT of the two-stage form (L >= M, zero padded) equals the oracle's
+    per-hypothesis DS-GRFT sums."""
+    R = dataclasses.replace(synth.ds_m512().radar, M=48, N=160)
+    s = synth.make_echo(R, [Target(70.0, 30.0, 3.0, complex(1.5, -0.5))], 21)
+    lam, L, Fv = R.wavelength, 64, 16
+    vstep_c = lam * R.prf_hz * Fv / (2 * L)               # coarse step: Fv Doppler bins of L
+    ds = DSGrid(0, 128, Axis(-vstep_c, vstep_c, 3), Axis(-6.0, 6.0, 2), Fv, 4)
+    Z = oracle.coarse_rm(R, s, ds, 0, ds.n_cells)            # [c][m][n0]
+    Yds = oracle.dsgrft_full(R, s, ds)
+    t = np.arange(R.M) / R.prf_hz
+    n0 = np.arange(ds.r0_count)
+    e0 = np.exp(2j * np.pi * ((2 * n0 * R.dr_m / lam) % 1.0))
+    f_of_k = (np.arange(Fv) - Fv // 2) % L
+    for c in range(ds.n_cells):
+        i, l = divmod(c, ds.ac.count)
+        for q in range(ds.Fa):
+            da = (q - ds.Fa / 2) * ds.ac.step / ds.Fa
+            chirp = np.exp(4j * np.pi * (0.5 * da * t * t) / lam)
+            X = np.fft.ifft(Z[c] * chirp[:, None], n=L, axis=0) * L     # [f][n0]
+            y = e0 * X[f_of_k]                                          # [k][n0]
+            np.testing.assert_allclose(y, Yds[i * Fv:(i + 1) * Fv, l * ds.Fa + q], rtol=0,
+                                       atol=1e-10 * np.abs(Yds).max())
+
+
 # ---------------------------------------------------------------- P6: DS == GRFT where bins agree
 def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
     """Prop. 1/2: with the same bins the two sums have identical terms up to rounding."""
