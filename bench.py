@@ -305,6 +305,17 @@ def run_suite(args):
     units = ds.n_cells * ds.n_fine * ds.r0_count * R.M
     ms_fft = _timed(lambda: g.dsgrft_fine_dfm_fft(R, echo, ds, 0, ds.n_cells, None, P), 3, stream)
     ms_dense = _timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.n_cells, "bf16x3", None, P), 3, stream)
+    # ------------------------------------------------ frequency-domain coarse stage vs the gather
+    dsz = sc.ds
+    ncz = 32                                          # 32 cells x 512 x 4096 complex64 = 537 MB
+    Z = torch.empty((ncz, R.M, dsz.r0_count), dtype=torch.complex64, device=dev)
+    ms_fd = _timed(lambda: g.dsgrft_coarse_rm_fd(R, echo, dsz, 0, ncz, Z), 3, stream)
+    ms_td = _timed(lambda: g.dsgrft_coarse_rm(R, echo, dsz, 0, ncz, Z), 3, stream)
+    out["coarse_stage_m512"] = {
+        "workload": "coarse range-migration correction of 32 cells x 512 pulses x 4096 bins into Z (complex64)",
+        "frequency_domain_ms": ms_fd, "time_domain_gather_ms": ms_td,
+        "frequency_domain_rows_per_s": ncz * R.M / (1e-3 * ms_fd)}
+    del Z
     out["fft_form_m512"] = {
         "workload": "DS-GRFT M=512 x N=4096, coarse 32 x 8, fine 96 x 16 (fine velocity step = one bin of a "
                     "512-point transform), 1.6e9 hypotheses, P written",

@@ -187,6 +187,19 @@ int grft_plain_static(const grft_radar *radar, const grft_c32 *echo, const grft_
 int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
                      int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream);
 
+/* Coarse range-migration correction in the frequency domain, the mGIFT of Def. 2 with
+ * eq. H-RM and eq. pre-DFM (Alg. 1): per pulse the range spectrum S[m][k] (N-point DFT)
+ * times exp(j 2 pi k delta / N), delta = d_c(t_m) / dr, k in [-N/2, N/2), inverse DFT,
+ * times the coarse phase:
+ *   Z[c - cell_begin][m][j] = (1/N) sum_k S[m][k] exp(j 2 pi k (r0_begin + j + delta) / N)
+ *                             * exp(j 4 pi d_c(t_m) / lambda)
+ * the band-limited circular advance of each range profile by delta bins (no rounding of
+ * the bin shift).  Same output layout as dsgrft_coarse_rm, so dsgrft_fine_dfm with Z given
+ * runs the fine stage on it.  N must be a power of two <= 8192 (else GRFT_EUNSUPPORTED,
+ * nothing enqueued).  FP32 transforms, FP64 delta and phases. */
+int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                        int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream);
+
 /* Fine Doppler-migration correction, the GFT of Def. 1 / Alg. 2 as a dense contraction
  * against the dechirp matrix D[m][f] = exp(j 4 pi (dv_k t_m + da_q t_m^2 / 2) / lambda):
  *   Y(n0; c, f) = exp(j 4 pi n0 dr / lambda) * sum_m Zc[m][n0] D[m][f]          (Alg. 3)

@@ -5,14 +5,18 @@ import this package.  It shares no code with the CUDA library:
   * ``grft_oracle.c``  literal FP64 loops (plain GRFT, coarse RM gather, DS-GRFT,
     CA-CFAR + top-K, trajectory adjoint, refinement), built with gcc
     ``-O2 -fopenmp -ffp-contract=off`` so that every FP64 operation rounds once;
-  * ``brute.py``       an independent pure-numpy restatement for tiny shapes.
+  * ``brute.py``       an independent pure-numpy restatement for tiny shapes;
+  * ``fd.py``          the frequency-domain coarse stage (mGIFT with H_RM as a range-
+    spectrum phase ramp) and the fine stage on its output, numpy FFT in FP64.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 tests/test_oracle_pins.py (closed forms, library routines, brute force, invariants);
 none is "parity unpinned".
 """
+from .fd import coarse_rm_fd, dsgrft_rows_fd
 from .wrap import (bins_phases, coarse_rm, cfar_detect, dsgrft_rows, dsgrft_full, grft_plain_rows,
                    grft_plain_full, load, num_threads, refine, trajectory_grad)
 
-__all__ = ["bins_phases", "coarse_rm", "cfar_detect", "dsgrft_rows", "dsgrft_full",
+__all__ = ["bins_phases", "coarse_rm", "coarse_rm_fd", "cfar_detect", "dsgrft_rows", "dsgrft_rows_fd",
+           "dsgrft_full",
            "grft_plain_rows", "grft_plain_full", "load", "num_threads", "refine", "trajectory_grad"]

@@ -21,7 +21,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
-           "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
+           "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "dsgrft_coarse_rm_fd", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
            "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
 
@@ -150,6 +150,14 @@ def dsgrft_fine_dfm(radar, Z, echo, grid, cell_begin, cell_count, precision, Y=N
                                  _ptr(echo, torch.complex64, "echo"), C.byref(G), int(cell_begin),
                                  int(cell_count), _precision(precision), _ptr(Y, torch.complex64, "Y"),
                                  _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft_fine_dfm")
+
+
+def dsgrft_coarse_rm_fd(radar, echo, grid, cell_begin, cell_count, Z, stream=None):
+    """Frequency-domain coarse stage (mGIFT, Alg. 1) into Z [cell_count][M][r0_count]."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dsgrft_coarse_rm_fd(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
+                                     int(cell_begin), int(cell_count), _ptr(Z, torch.complex64, "Z"),
+                                     _stream(stream)), "dsgrft_coarse_rm_fd")
 
 
 def dsgrft_fine_dfm_fft(radar, echo, grid, cell_begin, cell_count, Y=None, P=None, stream=None):

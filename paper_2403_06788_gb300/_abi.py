@@ -74,6 +74,8 @@ SIGNATURES = {
                                    C.c_int32, _P, _P]),
     "dsgrft_fine_dfm": (C.c_int, [C.POINTER(grft_radar), _P, _P, C.POINTER(grft_dsgrid), C.c_int32,
                                   C.c_int32, C.c_int, _P, _P, _P]),
+    "dsgrft_coarse_rm_fd": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
+                                      C.c_int32, _P, _P]),
     "dsgrft_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                       C.c_int32, _P, _P, _P]),
     "dsgrft_fine_dfm_batched": (C.c_int, [C.POINTER(grft_radar), C.POINTER(grft_dsgrid),

@@ -440,6 +440,31 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
 }
 
+int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                        int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream) {
+    if (!radar_ok(radar) || !echo || !Z || !dsgrid_ok(grid, radar) || cell_begin < 0 || cell_count < 0 ||
+        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count)
+        return GRFT_EINVAL;
+    const int N = radar->N;
+    if (N < 2 || N > 8192 || (N & (N - 1)) != 0) return GRFT_EUNSUPPORTED;
+    if (cell_count == 0) return GRFT_OK;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const RadarD R = radar_d(*radar);
+    const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));
+    const size_t w_bytes = align_up((size_t)cell_count * R.M * sizeof(float2));
+    const size_t s_bytes = align_up((size_t)R.M * N * sizeof(float2));
+    unsigned char *ws = (unsigned char *)workspace(c, rho_bytes + w_bytes + s_bytes);
+    if (!ws) return GRFT_ENOMEM;
+    int32_t *rho = (int32_t *)ws;
+    float2 *w = (float2 *)(ws + rho_bytes);
+    float2 *S = (float2 *)(ws + rho_bytes + w_bytes);
+    if ((e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
+    if ((e = launch_range_fft(c, R, (const float2 *)echo, S))) return e;
+    return launch_rm_fd(c, R, *grid, cell_begin, cell_count, S, w, (float2 *)Z);
+}
+
 int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
                         int32_t cell_begin, int32_t cell_count, grft_c32 *Y, float *P, void *stream) {
     if (!radar_ok(radar) || !echo || (!Y && !P) || !dsgrid_ok(grid, radar) || cell_begin < 0 ||

@@ -1,0 +1,188 @@
+// Frequency-domain coarse range-migration correction, the mGIFT of Def. 2 with eq. H-RM and
+// eq. pre-DFM (Alg. 1), for N a power of two:
+//   S[m][k]    = sum_n s[m][n] exp(-j 2 pi k n / N)                          (range spectrum)
+//   Z[c][m][j] = (1/N) sum_k S[m][k] exp(+j 2 pi k (n + delta) / N) * w_c(m),   n = r0_begin + j
+// with delta = d_c(t_m) / dr (FP64), k in [-N/2, N/2): the band-limited circular advance of
+// each range profile by delta bins.  Two kernels, both one persistent CTA per row at a time
+// with the N samples in shared memory:
+//   k_range_fft  forward radix-2 decimation in frequency of each pulse row; the spectrum is
+//                stored in bit-reversed order (nothing is permuted);
+//   k_rm_fd      per (cell, pulse): the spectrum times the ramp exp(j 2 pi k frac(delta) / N)
+//                (two small per-row tables: a coarse and a fine factor, plus exp(-j pi f)),
+//                inverse radix-2 decimation in time from the bit-reversed order to natural
+//                order, then the integer part of delta as an index offset when the range
+//                window [r0_begin, r0_begin + r0_count) is written (times w_c and 1/N).
+// Twiddles (one table per stage span) are built once per CTA with sincospif.
+#include "internal.cuh"
+
+namespace grft {
+
+namespace {
+
+constexpr int FD_THREADS = 512;
+
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+
+__device__ __forceinline__ unsigned brev_bits(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+
+// Shared memory of a CTA: N data values, then N twiddles laid out per stage: the
+// butterflies of span h read tw[h + r] = exp(+j pi r / h), r < h, consecutive for
+// consecutive butterflies (no bank conflicts, unlike one table read at stride N / 2h).
+__device__ __forceinline__ void build_twiddles(float2 *tw, int N) {
+    for (int t = threadIdx.x; t < N; t += FD_THREADS) {
+        if (t == 0) {
+            tw[0] = make_float2(1.f, 0.f);
+            continue;
+        }
+        const int h = 1 << (31 - __clz(t)), r = t - h;
+        float sn, cs;
+        sincospif((float)r / (float)h, &sn, &cs);           // r / h exact (h a power of two)
+        tw[t] = make_float2(cs, sn);
+    }
+}
+
+// Forward DIF in place, natural order in, bit-reversed order out (exponent -).  Span
+// h = 2^lh: butterfly b pairs i = (b >> lh) 2h + (b & (h - 1)) with i + h.
+__device__ __forceinline__ void fft_dif_fwd(float2 *x, const float2 *tw, int logN) {
+    const int N = 1 << logN;
+    for (int lh = logN - 1; lh >= 0; --lh) {
+        const int h = 1 << lh;
+        for (int b = threadIdx.x; b < N / 2; b += FD_THREADS) {
+            const int r = b & (h - 1), i = ((b >> lh) << (lh + 1)) + r;
+            const float2 u = x[i], v = x[i + h];
+            x[i] = cadd2(u, v);
+            x[i + h] = cmul(csub2(u, v), conj2(tw[h + r]));
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse DIT in place, bit-reversed order in, natural order out (exponent +, unscaled).
+__device__ __forceinline__ void fft_dit_inv(float2 *x, const float2 *tw, int logN) {
+    const int N = 1 << logN;
+    for (int lh = 0; lh < logN; ++lh) {
+        const int h = 1 << lh;
+        for (int b = threadIdx.x; b < N / 2; b += FD_THREADS) {
+            const int r = b & (h - 1), i = ((b >> lh) << (lh + 1)) + r;
+            const float2 u = x[i], v = cmul(x[i + h], tw[h + r]);
+            x[i] = cadd2(u, v);
+            x[i + h] = csub2(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ __launch_bounds__(FD_THREADS) void k_range_fft(const float2 *__restrict__ echo, int M, int N,
+                                                        int logN, float2 *__restrict__ S) {
+    extern __shared__ float2 fd_smem[];
+    float2 *x = fd_smem, *tw = fd_smem + N;
+    build_twiddles(tw, N);
+    for (int m = blockIdx.x; m < M; m += gridDim.x) {
+        __syncthreads();
+        for (int n = threadIdx.x; n < N; n += FD_THREADS) x[n] = __ldg(echo + (long)m * N + n);
+        __syncthreads();
+        fft_dif_fwd(x, tw, logN);
+        for (int p = threadIdx.x; p < N; p += FD_THREADS) S[(long)m * N + p] = x[p];   // bit-reversed order
+    }
+}
+
+__global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
+                                                    int logN, const float2 *__restrict__ S,
+                                                    const float2 *__restrict__ w_c, float2 *__restrict__ Z) {
+    extern __shared__ float2 fd_smem[];
+    const int N = R.N;
+    float2 *x = fd_smem, *tw = fd_smem + N;
+    __shared__ float2 s_hi[128], s_lo[64];     // ramp factors exp(j 2 pi u f / N), u = 64 u_hi + u_lo
+    __shared__ long s_I;                        // integer advance of the row
+    __shared__ float s_f;                       // fractional advance of the row
+    build_twiddles(tw, N);
+    const long rows = (long)cell_count * R.M;
+    const float inv_n = 1.0f / (float)N;        // exact: N a power of two
+    for (long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int cl = (int)(row / R.M), m = (int)(row - (long)cl * R.M);
+        __syncthreads();                        // previous row's reads of x, s_hi, s_lo, s_I, s_f are done
+        if (threadIdx.x == 0) {                 // delta = d_c(t_m) / dr in FP64, once per row
+            const int c = cell_begin + cl;
+            const double vc = axis_value(g.vc.start, g.vc.step, c / g.ac.count);
+            const double ac = axis_value(g.ac.start, g.ac.step, c % g.ac.count);
+            const double delta = __ddiv_rn(displacement(vc, ac, slow_time(m, R.prf)), R.dr);
+            const double fl = floor(delta);
+            s_I = (long)fl;                     // integer advance
+            s_f = (float)__dsub_rn(delta, fl);  // fractional advance in [0, 1)
+        }
+        __syncthreads();
+        const long I = s_I;
+        const float f = s_f;
+        for (int u = threadIdx.x; u < 128 + 64; u += FD_THREADS) {
+            float sn, cs;
+            if (u < 128) {
+                sincospif(2.0f * (float)(64 * u) * f / (float)N, &sn, &cs);
+                s_hi[u] = make_float2(cs, sn);
+            } else {
+                sincospif(2.0f * (float)(u - 128) * f / (float)N, &sn, &cs);
+                s_lo[u - 128] = make_float2(cs, sn);
+            }
+        }
+        float sn0, cs0;
+        sincospif(-f, &sn0, &cs0);              // exp(-j pi f): k = u - N/2
+        const float2 c0 = make_float2(cs0, sn0);
+        __syncthreads();
+        const float2 *Sm = S + (long)m * N;
+        for (int p = threadIdx.x; p < N; p += FD_THREADS) {
+            const int k = (int)brev_bits((unsigned)p, logN);        // natural frequency of slot p
+            const int u = k < N / 2 ? k + N / 2 : k - N / 2;        // signed k + N/2
+            const float2 ramp = cmul(c0, cmul(s_hi[u >> 6], s_lo[u & 63]));
+            x[p] = cmul(__ldg(Sm + p), ramp);
+        }
+        __syncthreads();
+        fft_dit_inv(x, tw, logN);
+        const float2 wm = w_c[(long)cl * R.M + m];
+        const float2 sc = make_float2(wm.x * inv_n, wm.y * inv_n);
+        float2 *zrow = Z + row * g.r0_count;
+        for (int j = threadIdx.x; j < g.r0_count; j += FD_THREADS) {
+            long n = ((long)g.r0_begin + j + I) % N;
+            if (n < 0) n += N;
+            zrow[j] = cmul(x[n], sc);
+        }
+    }
+}
+
+}  // namespace
+
+size_t fd_smem_bytes(int N) { return 2 * (size_t)N * sizeof(float2); }
+
+int launch_range_fft(const Ctx &c, const RadarD &R, const float2 *echo, float2 *S) {
+    int logN = 0;
+    while ((1 << logN) < R.N) ++logN;
+    const size_t smem = fd_smem_bytes(R.N);
+    static bool attr[64] = {false};
+    if (c.device >= 64) return GRFT_EUNSUPPORTED;
+    if (!attr[c.device]) {                      // once per device, for the largest N served
+        const int most = (int)fd_smem_bytes(8192);
+        if (cudaFuncSetAttribute(k_range_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess ||
+            cudaFuncSetAttribute(k_rm_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
+            return GRFT_ECUDA;
+        attr[c.device] = true;
+    }
+    const int grid = R.M < 2 * c.num_sms ? R.M : 2 * c.num_sms;
+    KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
+    k_range_fft<<<grid, FD_THREADS, smem, c.stream>>>(echo, R.M, R.N, logN, S);
+    return check_launch();
+}
+
+int launch_rm_fd(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_begin, int cell_count,
+                 const float2 *S, const float2 *w, float2 *Z) {
+    int logN = 0;
+    while ((1 << logN) < R.N) ++logN;
+    const long rows = (long)cell_count * R.M;
+    if (rows == 0) return GRFT_OK;
+    const long cap = 2L * c.num_sms * 4;        // persistent: a few CTAs per SM
+    const int grid = (int)(rows < cap ? rows : cap);
+    KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
+    k_rm_fd<<<grid, FD_THREADS, fd_smem_bytes(R.N), c.stream>>>(R, g, cell_begin, cell_count, logN, S, w, Z);
+    return check_launch();
+}
+
+}  // namespace grft

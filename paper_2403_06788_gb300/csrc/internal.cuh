@@ -110,6 +110,12 @@ struct DsOut {           // output placement of a DS call (v-slab of the canonic
     int Fv, Fa;
 };
 
+// Frequency-domain coarse stage (coarse_rm_fd.cu): range spectra S[M][N] (bit-reversed
+// order), then Z[cell][m][j] for the cells.  N a power of two <= 8192.
+int launch_range_fft(const Ctx &, const RadarD &, const float2 *echo, float2 *S);
+int launch_rm_fd(const Ctx &, const RadarD &, const grft_dsgrid &, int cell_begin, int cell_count,
+                 const float2 *S, const float2 *w, float2 *Z);
+
 // FFT form of the fine stage (fine_dfm_fft.cu): chirp[Fa][L], then the transform kernel.
 int launch_gft_chirp(const Ctx &, const RadarD &, const grft_dsgrid &, int L, float2 *chirp);
 int launch_ds_fft(const Ctx &, const RadarD &, const float2 *echo, const grft_dsgrid &, int cell_count,

@@ -1,0 +1,81 @@
+"""GPU: the frequency-domain coarse stage (mGIFT with H_RM as a range-spectrum ramp, Alg. 1,
+dsgrft_coarse_rm_fd) against the FP64 numpy oracle (every output of a small case with a
+ragged range window; sampled pulses at M=512 x N=4096), the fine stage run on its output
+(dsgrft_fine_dfm with Z given) against the oracle's DS-GRFT rows of the same form, and the
+rejection of range lengths that are not a power of two."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import Axis, DSGrid, Radar, Target
+from tests.helpers import TOL_FP32, TOL_SPLIT, rel_peak_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    R = Radar(M=64, N=256, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    ds = DSGrid(5, 200, Axis(-120.0, 60.0, 3), Axis(-10.0, 20.0, 2), 4, 2)
+    s = synth.make_echo(R, [Target(90.3, -70.0, 6.0, complex(3.0, -1.0)),
+                            Target(170.6, 40.0, -4.0, complex(-1.0, 2.0))], 17)
+    return R, ds, s
+
+
+def test_fd_coarse_stage_every_output_small(cuda_lib):
+    g = cuda_lib
+    R, ds, s = _small()
+    Z = torch.zeros((ds.n_cells, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dsgrft_coarse_rm_fd(R, torch.from_numpy(s).cuda(), ds, 0, ds.n_cells, Z)
+    assert g.grft_sync_status() == 0
+    Zo = oracle.coarse_rm_fd(R, s, ds, 0, ds.n_cells)
+    assert rel_peak_err(Z.cpu().numpy(), Zo) <= TOL_FP32
+    # a cell sub-range: the same values for those cells
+    Zs = torch.zeros((2, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dsgrft_coarse_rm_fd(R, torch.from_numpy(s).cuda(), ds, 3, 2, Zs)
+    assert rel_peak_err(Zs.cpu().numpy(), Zo[3:5]) <= TOL_FP32
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16x3", TOL_SPLIT)])
+def test_fd_then_fine_stage_matches_oracle_rows(cuda_lib, precision, tol):
+    g = cuda_lib
+    R, ds, s = _small()
+    echo = torch.from_numpy(s).cuda()
+    Z = torch.empty((ds.n_cells, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dsgrft_coarse_rm_fd(R, echo, ds, 0, ds.n_cells, Z)
+    nv, na = ds.vc.count * ds.Fv, ds.ac.count * ds.Fa
+    Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dsgrft_fine_dfm(R, Z, echo, ds, 0, ds.n_cells, precision, Y, None)
+    assert g.grft_sync_status() == 0
+    vf, af = np.meshgrid(np.arange(nv), np.arange(na), indexing="ij")
+    from oracle.wrap import ds_rows_of_canonical
+    cell, fine = ds_rows_of_canonical(ds, vf.ravel(), af.ravel())
+    Yo = oracle.dsgrft_rows_fd(R, s, ds, cell, fine).reshape(nv, na, ds.r0_count)
+    assert rel_peak_err(Y.cpu().numpy(), Yo) <= tol
+
+
+def test_fd_coarse_stage_m512_sampled(cuda_lib):
+    g = cuda_lib
+    sc = synth.ds_m512()
+    R, ds = sc.radar, sc.ds
+    s = synth.make_echo(R, sc.targets, sc.seed)
+    cb, cc = 100, 4
+    Z = torch.empty((cc, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dsgrft_coarse_rm_fd(R, torch.from_numpy(s).cuda(), ds, cb, cc, Z)
+    assert g.grft_sync_status() == 0
+    Zo = oracle.coarse_rm_fd(R, s, ds, cb, cc)
+    ms = np.random.default_rng(5).integers(0, R.M, 24)
+    assert rel_peak_err(Z.cpu().numpy()[:, ms], Zo[:, ms]) <= TOL_FP32
+
+
+def test_fd_coarse_stage_rejects_non_power_of_two(cuda_lib):
+    g = cuda_lib
+    R = Radar(M=16, N=300, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    ds = DSGrid(0, 100, Axis(0.0, 10.0, 1), Axis(0.0, 1.0, 1), 2, 2)
+    Z = torch.empty((1, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    with pytest.raises(g.GrftError):
+        g.dsgrft_coarse_rm_fd(R, torch.zeros((R.M, R.N), dtype=torch.complex64, device="cuda"), ds, 0, 1, Z)
+    assert g.grft_sync_status() == 0

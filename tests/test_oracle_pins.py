@@ -183,6 +183,78 @@ def test_fft_form_of_the_fine_stage_equals_dsgrft_rows():
                                        atol=1e-10 * np.abs(Yds).max())
 
 
+def _fd_radar(M, N, prf=1000.0):
+    return Radar(M=M, N=N, fc_hz=1.5e9, prf_hz=prf, dr_m=15.0)
+
+
+def test_fd_coarse_stage_integer_shift_is_exact_circular_shift():
+    """Eq. H-RM with an integer advance delta = d/dr is exactly the circular shift of the
+    range profile: v_c t_m / dr = m for v_c = dr PRF, a_c = 0."""
+    R = _fd_radar(6, 32, prf=10.0)
+    rng = np.random.default_rng(3)
+    s = (rng.standard_normal((R.M, R.N)) + 1j * rng.standard_normal((R.M, R.N))).astype(np.complex64)
+    ds = DSGrid(0, R.N, Axis(R.dr_m * R.prf_hz, 1.0, 1), Axis(0.0, 1.0, 1), 2, 2)
+    Z = oracle.coarse_rm_fd(R, s, ds, 0, 1)[0]
+    t = np.arange(R.M) / R.prf_hz
+    d = ds.vc.start * t
+    w = np.exp(4j * np.pi * d / R.wavelength)
+    for m in range(R.M):
+        expect = np.roll(s[m].astype(np.complex128), -m) * w[m]
+        np.testing.assert_allclose(Z[m], expect, rtol=0, atol=1e-12 * np.abs(s).max())
+
+
+def test_fd_coarse_stage_shifts_a_range_frequency_by_its_phase():
+    """A single range frequency k0 (|k0| < N/2) advanced by a fractional delta is the same
+    frequency with phase 2 pi k0 delta / N (closed form)."""
+    R = _fd_radar(5, 64)
+    k0 = -11
+    n = np.arange(R.N)
+    s = np.tile(np.exp(2j * np.pi * k0 * n / R.N), (R.M, 1)).astype(np.complex128)
+    ds = DSGrid(3, 50, Axis(-37.3, 1.0, 1), Axis(4.1, 1.0, 1), 2, 2)
+    Z = oracle.coarse_rm_fd(R, s, ds, 0, 1)[0]
+    t = np.arange(R.M) / R.prf_hz
+    d = ds.vc.start * t + 0.5 * ds.ac.start * t * t
+    delta = d / R.dr_m
+    nn = ds.r0_begin + np.arange(ds.r0_count)
+    expect = np.exp(2j * np.pi * k0 * (nn[None, :] + delta[:, None]) / R.N) * \
+        np.exp(4j * np.pi * d / R.wavelength)[:, None]
+    np.testing.assert_allclose(Z, expect, rtol=0, atol=1e-11)
+
+
+def test_fd_coarse_stage_matches_direct_dft():
+    """Brute force: the spectrum and its shifted inverse written as O(N^2) sums."""
+    R = _fd_radar(3, 12)
+    rng = np.random.default_rng(8)
+    s = rng.standard_normal((R.M, R.N)) + 1j * rng.standard_normal((R.M, R.N))
+    ds = DSGrid(2, 7, Axis(55.0, 1.0, 1), Axis(-9.0, 1.0, 1), 2, 2)
+    Z = oracle.coarse_rm_fd(R, s, ds, 0, 1)[0]
+    N = R.N
+    ks = [k if k < N // 2 else k - N for k in range(N)]      # signed, Nyquist at -N/2
+    t = np.arange(R.M) / R.prf_hz
+    for m in range(R.M):
+        d = ds.vc.start * t[m] + 0.5 * ds.ac.start * t[m] ** 2
+        delta = d / R.dr_m
+        S = [sum(s[m, x] * np.exp(-2j * np.pi * k * x / N) for x in range(N)) for k in range(N)]
+        for j in range(ds.r0_count):
+            n = ds.r0_begin + j
+            z = sum(S[k] * np.exp(2j * np.pi * ks[k] * (n + delta) / N) for k in range(N)) / N
+            z *= np.exp(4j * np.pi * d / R.wavelength)
+            assert abs(z - Z[m, j]) < 1e-12 * max(1.0, abs(z))
+
+
+def test_fd_ds_rows_equal_td_rows_without_fractional_shift():
+    """With every coarse advance an integer number of bins the frequency- and time-domain
+    coarse stages coincide (circularly; no sample crosses the echo's ends here), so the
+    two DS-GRFT rows agree."""
+    R = _fd_radar(8, 64, prf=10.0)
+    s = synth.make_echo(R, [Target(20.0, 0.0, 0.0, complex(1.0, 0.5))], 4)
+    ds = DSGrid(0, 24, Axis(R.dr_m * R.prf_hz, 1.0, 1), Axis(0.0, 1.0, 1), 4, 2)
+    cell, fine = np.zeros(8, dtype=np.int32), np.arange(8)
+    Yfd = oracle.dsgrft_rows_fd(R, s, ds, cell, fine)
+    Ytd = oracle.dsgrft_rows(R, s, ds, cell, fine)
+    np.testing.assert_allclose(Yfd, Ytd, rtol=0, atol=1e-10 * np.abs(Ytd).max())
+
+
 # ---------------------------------------------------------------- P6: DS == GRFT where bins agree
 def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
     """Prop. 1/2: with the same bins the two sums have identical terms up to rounding."""
