@@ -56,8 +56,8 @@ long split_rows(long total_rows, long min_rows, long row_bytes, int &nbuf, bool 
 struct DevState {
     bool init = false;
     int *status = nullptr;
-    void *ws = nullptr;
-    size_t ws_size = 0;
+    void *ws[WS_SLOTS] = {nullptr, nullptr};    // one workspace per operation class
+    size_t ws_size[WS_SLOTS] = {0, 0};
     int num_sms = 0;
     int cc = 0;
 };
@@ -111,24 +111,25 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-void *workspace(const Ctx &ctx, size_t bytes) {
+void *workspace(const Ctx &ctx, size_t bytes, int slot) {
+    if (slot < 0 || slot >= WS_SLOTS) return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &d = g_dev[ctx.device];
-    if (bytes <= d.ws_size) return d.ws;
-    if (d.ws) {
+    if (bytes <= d.ws_size[slot]) return d.ws[slot];
+    if (d.ws[slot]) {
         cudaDeviceSynchronize();
-        cudaFree(d.ws);
-        d.ws = nullptr;
-        d.ws_size = 0;
+        cudaFree(d.ws[slot]);
+        d.ws[slot] = nullptr;
+        d.ws_size[slot] = 0;
     }
     size_t want = align_up(bytes, 64ull << 20);
-    if (cudaMalloc(&d.ws, want) != cudaSuccess) {
+    if (cudaMalloc(&d.ws[slot], want) != cudaSuccess) {
         cudaGetLastError();
-        d.ws = nullptr;
+        d.ws[slot] = nullptr;
         return nullptr;
     }
-    d.ws_size = want;
-    return d.ws;
+    d.ws_size[slot] = want;
+    return d.ws[slot];
 }
 
 namespace {
@@ -295,12 +296,12 @@ int grft_release_workspace(void) {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return GRFT_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &d = g_dev[dev];
-    if (d.ws) {
-        if (cudaDeviceSynchronize() != cudaSuccess) return GRFT_ECUDA;
-        cudaFree(d.ws);
+    if ((d.ws[0] || d.ws[1]) && cudaDeviceSynchronize() != cudaSuccess) return GRFT_ECUDA;
+    for (int i = 0; i < WS_SLOTS; ++i) {
+        if (d.ws[i]) cudaFree(d.ws[i]);
+        d.ws[i] = nullptr;
+        d.ws_size[i] = 0;
     }
-    d.ws = nullptr;
-    d.ws_size = 0;
     return GRFT_OK;
 }
 

@@ -574,7 +574,7 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
         return GRFT_EINVAL;
     if (cfar.mode == 0 && !(cfar.pfa > 0.0 && cfar.pfa < 1.0)) return GRFT_EINVAL;
     const size_t need = 256 + (size_t)CAND_CAP * (sizeof(float) + sizeof(int64_t));
-    unsigned char *ws = (unsigned char *)workspace(c, need);
+    unsigned char *ws = (unsigned char *)workspace(c, need, WS_DETECT);
     if (!ws) return GRFT_ENOMEM;
     int *count = (int *)ws;
     int64_t *cand_i = (int64_t *)(ws + 256);

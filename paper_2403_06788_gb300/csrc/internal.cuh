@@ -79,7 +79,12 @@ struct Ctx {                  // per-call device context
 
 // Workspace of this device, grown to at least `bytes` (synchronises the device when it
 // grows).  Returns nullptr on allocation failure.
-void *workspace(const Ctx &ctx, size_t bytes);
+// Per-device workspaces, grown on demand (a grow synchronises the device).  Slot 0 serves
+// the transforms (plain GRFT, coarse stages, fine stages), slot 1 the detection, so that a
+// detection and a transform of another CPI may run at the same time on two streams.
+constexpr int WS_SLOTS = 2;
+constexpr int WS_TRANSFORM = 0, WS_DETECT = 1;
+void *workspace(const Ctx &ctx, size_t bytes, int slot = WS_TRANSFORM);
 
 // Launchers (each returns a grft status; they only enqueue work).
 int launch_bins_phases(const Ctx &, const RadarD &, const double *v, const double *a, int nh,
