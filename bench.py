@@ -172,6 +172,31 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- multi-rank plumbing
+# One process per GPU; every rank processes its own CPI (weak scaling) and nothing crosses
+# ranks on the data path: the only collectives are the timing barrier and the max below.
+def rank_layout():
+    """(world, rank, local rank) from the launcher's environment; (1, 0, 0) without one."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds_per_step: float) -> float:
+    """Whole-job throughput: world ranks each process units_per_rank per step."""
+    return world * units_per_rank / seconds_per_step
+
+
 def _timed(fn, reps, stream):
     """Average CUDA-event time (ms) of fn() over reps calls after one untimed call."""
     import torch
@@ -359,9 +384,7 @@ def main():
     import paper_2403_06788_gb300 as g
     import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_layout()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -423,11 +446,7 @@ def main():
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     gemm_ms = [a.elapsed_time(b) for a, b, c in ev]
     det_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     st = g.grft_sync_status()
     dets, ndet = g.decode_detections(det_out, n_out, args.topk)
 
@@ -443,11 +462,7 @@ def main():
         det_host.copy_(det_out, non_blocking=True)
         n_host.copy_(n_out, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
 
     # ---------------------------------------------------------------- plain GRFT, same hypotheses
     plain_ms = None
@@ -536,7 +551,7 @@ def main():
     if args.precision == "fp32":
         # FP32 SIMT path: bound by FFMA issue, 152 SMs x 128 FMA/clk x 2 flop x max clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    value = world * units / (1e-3 * total_ms / args.steps)
+    value = job_rate(units, world, 1e-3 * total_ms / args.steps)
     # every hot kernel against its own bound: algorithmic bytes (HBM) or FLOP / event time
     hbm = peaks.get("hbm_gbs", 6678.5)
     fma_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -587,7 +602,7 @@ def main():
         "max_rel_peak_err": acc,
         "detections": {"total": ndet, "top1_p": float(dets["p"][0]) if len(dets) else None},
         "status": st,
-        "e2e": {"value": world * units / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(units, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": int(echo.numel() * 8),
                 "d2h_bytes_per_step": int(det_out.numel() + 4)},
         "gpu_launches": sum(v[0] for v in ktime.values()),
