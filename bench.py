@@ -172,6 +172,15 @@ def run_reference(args):
     return 0
 
 
+def residual_migration(radar, ds) -> dict:
+    """The dual-scale approximation's residual range migration (eq. Residual_RM_DeltaR): a
+    fine offset moves at most (dv_c T + da_c T^2 / 2) / 2 over the CPI, T = M / PRF; the
+    coarse bins stay valid for the fine hypotheses while that is at most dr / 2."""
+    T = radar.M / radar.prf_hz
+    res = 0.5 * (ds.vc.step * T + 0.5 * ds.ac.step * T * T)
+    return {"residual_m": res, "half_bin_m": 0.5 * radar.dr_m, "rm_bound_ok": bool(res <= 0.5 * radar.dr_m)}
+
+
 # ---------------------------------------------------------------- multi-rank plumbing
 # One process per GPU; every rank processes its own CPI (weak scaling) and nothing crosses
 # ranks on the data path: the only collectives are the timing barrier and the max below.
@@ -255,7 +264,8 @@ def run_suite(args):
         prec[p] = {"ms_per_call": ms, "value": units / (1e-3 * ms), "max_rel_peak_err_sampled": err}
     out["precision_m2048"] = {"workload": "DS-GRFT M=2048 x N=8192, coarse 32 x 8, fine 256 x 64; one call = "
                                           "one coarse-v row (8 cells, 2.2e12 hypothesis-pulses, Y written)",
-                              "unit": UNIT, "full_grid_calls": ds.vc.count, **prec}
+                              "unit": UNIT, "full_grid_calls": ds.vc.count,
+                              "range_migration": residual_migration(R, ds), **prec}
     del Y, echo
     torch.cuda.empty_cache()
 
@@ -313,6 +323,7 @@ def run_suite(args):
     out["differentiation_m1024"] = {
         "workload": "DS-GRFT M=1024 x N=4096 (2^30 hypotheses), top-1000 CA-CFAR, adjoint at the detections, "
                     "20 ascent steps (linear gather)",
+        "range_migration": residual_migration(R, ds),
         "detections": int(K), "forward_ms": ms_fwd, "forward_value": units / (1e-3 * ms_fwd), "unit": UNIT,
         "detect_ms": ms_det, "adjoint_ms": ms_adj, "refine_20_steps_ms": ms_ref,
         "status": g.grft_sync_status()}
@@ -579,7 +590,8 @@ def main():
                    "hypotheses": units // R.M, "pulses": R.M, "precision": args.precision,
                    "topk": args.topk, "cfar": "CA 2 guard / 16 train, pfa 1e-6",
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
-                   "parallelism": f"{world} independent CPI(s), one per GPU"},
+                   "parallelism": f"{world} independent CPI(s), one per GPU",
+                   "range_migration": residual_migration(R, ds)},
         "roofline": {"bound": "tensor" if args.precision != "fp32" else "alu",
                      "kernel": ("k_ds_tc (tcgen05 split-operand contraction + |Y|^2 epilogue), CUDA events "
                                 "around each launch on its stream" if n_c > 0 else
