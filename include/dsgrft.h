@@ -118,6 +118,11 @@ int grft_set_wait_limit(uint64_t cycles);
 /* Free this device's cached workspace (the next call reallocates it). */
 int grft_release_workspace(void);
 
+/* Release everything the library holds for the current device: the workspaces, the side
+ * stream and events of the split/contraction pipeline, and pending timing events (timing
+ * is switched off).  Synchronises the device; the next call sets up what it needs again. */
+int grft_shutdown(void);
+
 /* Per-kernel timing on the GPU (tracing): while enabled, every kernel the library launches
  * outside stream capture is bracketed by a pair of CUDA events recorded on the call's
  * stream.  grft_timing(1) enables and clears the totals, grft_timing(0) disables;

@@ -19,6 +19,7 @@ from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_L
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
 __all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
+           "grft_shutdown",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "dsgrft_coarse_rm_fd", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
@@ -94,6 +95,11 @@ def grft_set_wait_limit(cycles: int) -> None:
 
 def grft_release_workspace() -> None:
     check(load().grft_release_workspace(), "grft_release_workspace")
+
+
+def grft_shutdown() -> None:
+    """Release the current device's workspaces, pipeline stream/events and timing events."""
+    check(load().grft_shutdown(), "grft_shutdown")
 
 
 def grft_timing(enable: bool) -> None:

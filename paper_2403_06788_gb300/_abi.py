@@ -64,6 +64,7 @@ SIGNATURES = {
     "grft_sync_status": (C.c_int, [_P]),
     "grft_set_wait_limit": (C.c_int, [C.c_uint64]),
     "grft_release_workspace": (C.c_int, []),
+    "grft_shutdown": (C.c_int, []),
     "grft_selftest_wait": (C.c_int, [C.c_uint64, _P]),
     "grft_timing": (C.c_int, [C.c_int]),
     "grft_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),

@@ -286,6 +286,22 @@ int grft_sync_status(void *stream) {
     return h;
 }
 
+int grft_shutdown(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return GRFT_ECUDA;
+    int e = grft_release_workspace();
+    if (e) return e;
+    release_pipe(dev);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (const TimingRec &r : g_timing_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_timing_pending.clear();
+    g_timing_on = false;
+    return GRFT_OK;
+}
+
 int grft_set_wait_limit(uint64_t cycles) {
     g_wait_limit = cycles ? cycles : DEFAULT_WAIT_LIMIT;
     return GRFT_OK;

@@ -872,6 +872,20 @@ Pipe *get_pipe(int dev) {
 
 }  // namespace
 
+// Destroys the side stream and events of the split/contraction pipeline of a device (the
+// next call that needs them creates them again).  The device must be idle.
+void release_pipe(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    Pipe &p = g_pipe[dev];
+    if (!p.init) return;
+    cudaEvent_t evs[5] = {p.fork, p.split_done[0], p.split_done[1], p.gemm_done[0], p.gemm_done[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (p.side) cudaStreamDestroy(p.side);
+    p = Pipe();
+}
+
 int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],

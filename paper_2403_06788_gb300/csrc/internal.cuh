@@ -82,6 +82,7 @@ struct Ctx {                  // per-call device context
 // Per-device workspaces, grown on demand (a grow synchronises the device).  Slot 0 serves
 // the transforms (plain GRFT, coarse stages, fine stages), slot 1 the detection, so that a
 // detection and a transform of another CPI may run at the same time on two streams.
+void release_pipe(int dev);   // side stream and events of the split/contraction pipeline
 constexpr int WS_SLOTS = 2;
 constexpr int WS_TRANSFORM = 0, WS_DETECT = 1;
 void *workspace(const Ctx &ctx, size_t bytes, int slot = WS_TRANSFORM);

@@ -61,3 +61,16 @@ def test_timing_skips_captured_launches(cuda_lib):
     assert g.grft_timing_get("contract") == (0, 0.0)
     g.grft_timing(False)
     assert g.grft_sync_status() == 0
+
+
+def test_shutdown_releases_and_the_next_call_sets_up_again(cuda_lib):
+    g = cuda_lib
+    R, ds, echo = _case()
+    ref = g.dsgrft(R, echo, ds, precision="bf16x3")
+    g.grft_timing(True)
+    g.dsgrft(R, echo, ds, precision="bf16x3")
+    g.grft_shutdown()                                  # also drops pending timing events
+    again = g.dsgrft(R, echo, ds, precision="bf16x3")
+    assert torch.equal(ref, again)
+    assert g.grft_timing_get("contract") == (0, 0.0)    # timing is off after shutdown
+    assert g.grft_sync_status() == 0
