@@ -138,8 +138,9 @@ enum {
     GRFT_KERNEL_CFAR = 6,
     GRFT_KERNEL_TOPK = 7,
     GRFT_KERNEL_ADJOINT = 8,       /* trajectory sum, adjoint, refinement */
-    GRFT_KERNEL_CONTRACT_FFT = 9,  /* FFT form of the fine stage (dsgrft_fine_dfm_fft) */
-    GRFT_KERNEL_COUNT = 10
+    GRFT_KERNEL_CONTRACT_FFT = 9,  /* FFT form of the fine stage (dsgrft_fine_dfm_fft, dskt_fine_dfm_fft) */
+    GRFT_KERNEL_KEYSTONE = 10,     /* keystone transform (dskt_keystone) */
+    GRFT_KERNEL_COUNT = 11
 };
 int grft_timing(int enable);
 int grft_timing_get(int kernel, int32_t *launches, double *total_ms);
@@ -229,6 +230,50 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
  * equal to the dense form to FP32 rounding. */
 int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
                         int32_t cell_begin, int32_t cell_count, grft_c32 *Y, float *P, void *stream);
+
+/* ---------------------------------------------------------------- keystone branch (DS-KT-MFP)
+ *
+ * The dual-scale KT-MFP detector of Sec. III-B (eqs. velocity_Amb, Echo-after-KT, H-MFP,
+ * H-MFP-RM, KT-GRFT-GRFT) and Sec. IV (eq. Partition-Parameter-c1, Cor. 1, Prop. 3,
+ * Alg. 4), P = 2.  A KT grid is a grft_dsgrid whose coarse velocity axis is the folding
+ * factor: vc.step = V_a = lambda PRF / 2 (relative tolerance 1e-9) and vc.start = q_min V_a
+ * (q_min an integer within 1e-6), so cell (i, l) is (q = q_min + i, a_c = ac value l); the
+ * fine velocity is the baseband velocity c'_1 = (k - Fv/2) V_a / Fv on Fv = L transform
+ * bins; the fine acceleration is (q - Fa/2) ac.step / Fa as in the DS-GRFT grid (kappa = 1).
+ * Any other grid returns GRFT_EINVAL.  Sizes: M and N powers of two, 16 <= M <= 2048,
+ * 4 <= N <= 8192, else GRFT_EUNSUPPORTED (before anything is enqueued). */
+
+/* Range spectra and keystone transform (eq. Echo-after-KT).  echo: [M][N] device.  Skt:
+ * [M][N] device, written: range-frequency slot p of pulse row m' holds y_KT(f_k, t_m') for
+ * the frequency index k = bitrev_log2(N)(p) (signed k - N for k >= N/2, f_k = k f_s / N,
+ * f_s = c / (2 dr)), where the slow-time column of each frequency is resampled at
+ * t = fbar t', fbar = f_c / (f_c + f_k), as a band-limited periodic sequence of M samples
+ * (Doppler index in [-M/2, M/2)).  Uses the library workspace for the range spectra. */
+int dskt_keystone(const grft_radar *radar, const grft_c32 *echo, grft_c32 *Skt, void *stream);
+
+/* Coarse stage (Cor. 1: the mGIFT with H_KT,RM and the KT-MFP H_pre-DFM) for the cells
+ * [cell_begin, cell_begin + cell_count) of a KT grid, from Skt of dskt_keystone:
+ *   Z[c][m][j] = (1/N) sum_k Skt[m][k] exp(j 2 pi k_s (fbar_k q V_a t_m - (a_c/2) t_m^2) / (N dr))
+ *                      exp(j 2 pi k_s n / N) exp(j 4 pi (a_c/2) t_m^2 / lambda),
+ * n = r0_begin + j; Z is [cell_count][M][r0_count] device (the layout of dsgrft_coarse_rm). */
+int dskt_coarse_rm(const grft_radar *radar, const grft_c32 *Skt, const grft_dsgrid *grid,
+                   int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream);
+
+/* Fine stage (Prop. 3, the GFT of Def. 1 in its FFT form, Alg. 2) on Z of dskt_coarse_rm:
+ *   Y(n0; c, k, q) = sum_m Z[c][m][n0] exp(j 4 pi ((k - Fv/2) (V_a / Fv) t_m + da_q t_m^2 / 2) / lambda)
+ * (no range phase of n0, as in eq. KT-GRFT-GRFT), with L = Fv in {64, 128, 256, 512} and
+ * M <= L, else GRFT_EUNSUPPORTED; cell_count <= 65535.  Output layout and Y / P semantics
+ * are those of dsgrft_fine_dfm (a v-slab of the canonical layout starting at coarse row
+ * cell_begin / ac.count).  FP32 SIMT. */
+int dskt_fine_dfm_fft(const grft_radar *radar, const grft_c32 *Z, const grft_dsgrid *grid,
+                      int32_t cell_begin, int32_t cell_count, grft_c32 *Y, float *P, void *stream);
+
+/* The whole DS-KT-MFP map of Alg. 4 on one echo: dskt_keystone, then dskt_coarse_rm and
+ * dskt_fine_dfm_fft over all cells, in chunks of whole folding-factor rows sized to the
+ * library's split budget.  Y [nq Fv][nac Fa][r0_count] and/or P (same layout) device.
+ * Uses the library workspace (Skt, the range spectra / coarse output, the chirp table). */
+int dskt_mfp(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid, grft_c32 *Y,
+             float *P, void *stream);
 
 /* Many CPIs (uneven M, N) in one persistent launch (graph-capturable after a first
  * uncaptured call of the same shape).  radar's M and N are ignored (per item); grid's

@@ -18,7 +18,8 @@ from . import _abi
 from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_LINEAR,
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
-__all__ = ["load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
+__all__ = ["dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
+           "load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
            "grft_shutdown",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
@@ -173,6 +174,55 @@ def dsgrft_fine_dfm_fft(radar, echo, grid, cell_begin, cell_count, Y=None, P=Non
     check(load().dsgrft_fine_dfm_fft(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
                                      int(cell_begin), int(cell_count), _ptr(Y, torch.complex64, "Y"),
                                      _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft_fine_dfm_fft")
+
+
+def dskt_keystone(radar, echo, Skt, stream=None):
+    """Range spectra and keystone transform (eq. Echo-after-KT) into Skt [M][N]; range-
+    frequency slot p holds frequency index bitrev(p) (see spectral_slots)."""
+    R = _radar(radar)
+    check(load().dskt_keystone(C.byref(R), _ptr(echo, torch.complex64, "echo"), _ptr(Skt, torch.complex64, "Skt"),
+                               _stream(stream)), "dskt_keystone")
+
+
+def spectral_slots(N: int):
+    """Frequency index (FFT order, 0..N-1) held by each range-frequency slot of Skt: the
+    bit reversal of the slot over log2(N) bits (host list)."""
+    bits = int(N).bit_length() - 1
+    return [int(format(p, f"0{bits}b")[::-1], 2) if bits else 0 for p in range(int(N))]
+
+
+def dskt_coarse_rm(radar, Skt, grid, cell_begin, cell_count, Z, stream=None):
+    """Coarse stage of DS-KT-MFP (Cor. 1: H_KT,RM and H_pre-DFM) into Z [cell_count][M][r0_count]."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dskt_coarse_rm(C.byref(R), _ptr(Skt, torch.complex64, "Skt"), C.byref(G), int(cell_begin),
+                                int(cell_count), _ptr(Z, torch.complex64, "Z"), _stream(stream)), "dskt_coarse_rm")
+
+
+def dskt_fine_dfm_fft(radar, Z, grid, cell_begin, cell_count, Y=None, P=None, stream=None):
+    """Fine stage of DS-KT-MFP (Prop. 3, FFT form of the GFT) on Z of dskt_coarse_rm."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dskt_fine_dfm_fft(C.byref(R), _ptr(Z, torch.complex64, "Z"), C.byref(G), int(cell_begin),
+                                   int(cell_count), _ptr(Y, torch.complex64, "Y"), _ptr(P, torch.float32, "P"),
+                                   _stream(stream)), "dskt_fine_dfm_fft")
+
+
+def dskt_mfp(radar, echo, grid, Y=None, P=None, stream=None):
+    """The whole DS-KT-MFP map (Alg. 4) into Y and/or P [nq Fv][nac Fa][r0_count]."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dskt_mfp(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
+                          _ptr(Y, torch.complex64, "Y"), _ptr(P, torch.float32, "P"), _stream(stream)), "dskt_mfp")
+
+
+def dsktmfp(radar, echo, grid, want_Y=False, want_P=True):
+    """DS-KT-MFP over the whole keystone grid; returns P [v_full][a_full][r0] (and Y)."""
+    nv, na = int(grid.vc.count) * int(grid.Fv), int(grid.ac.count) * int(grid.Fa)
+    shape = (nv, na, int(grid.r0_count))
+    P = torch.empty(shape, dtype=torch.float32, device=echo.device) if want_P else None
+    Y = torch.empty(shape, dtype=torch.complex64, device=echo.device) if want_Y else None
+    dskt_mfp(radar, echo, grid, Y, P)
+    if want_Y and want_P:
+        return P, Y
+    return Y if want_Y else P
 
 
 def dsgrft_fine_dfm_batched(radar, grid, items, precision, stream=None):

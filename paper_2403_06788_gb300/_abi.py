@@ -17,7 +17,7 @@ GRFT_FP32, GRFT_BF16X3, GRFT_FP16X3 = 0, 1, 2
 GRFT_GATHER_NEAREST, GRFT_GATHER_LINEAR = 0, 1
 PRECISIONS = {"fp32": GRFT_FP32, "bf16x3": GRFT_BF16X3, "fp16x3": GRFT_FP16X3}
 KERNELS = {"tables": 0, "plain": 1, "coarse_rm": 2, "split": 3, "contract": 4, "contract_fp32": 5,
-           "cfar": 6, "topk": 7, "adjoint": 8, "contract_fft": 9}
+           "cfar": 6, "topk": 7, "adjoint": 8, "contract_fft": 9, "keystone": 10}
 
 
 class grft_axis(C.Structure):
@@ -79,6 +79,11 @@ SIGNATURES = {
                                       C.c_int32, _P, _P]),
     "dsgrft_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                       C.c_int32, _P, _P, _P]),
+    "dskt_keystone": (C.c_int, [C.POINTER(grft_radar), _P, _P, _P]),
+    "dskt_coarse_rm": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32, _P, _P]),
+    "dskt_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32,
+                                    _P, _P, _P]),
+    "dskt_mfp": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), _P, _P, _P]),
     "dsgrft_fine_dfm_batched": (C.c_int, [C.POINTER(grft_radar), C.POINTER(grft_dsgrid),
                                           C.POINTER(grft_batch_item), C.c_int32, C.c_int, _P]),
     "detect_peaks": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(grft_cfar),

@@ -522,6 +522,134 @@ int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grf
     return launch_ds_fft(c, R, (const float2 *)echo, *grid, cell_count, rho, w, chirp, e0, L, out);
 }
 
+namespace {
+
+bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
+
+// A KT grid: coarse velocity axis = folding factor q, vc.step = V_a, vc.start = q_min V_a.
+bool ktgrid_ok(const grft_dsgrid *g, const grft_radar *r) {
+    if (!dsgrid_ok(g, r)) return false;
+    const double va = r->c_mps / r->fc_hz * r->prf_hz / 2.0;
+    const double q = g->vc.start / va;
+    return std::fabs(g->vc.step - va) <= 1e-9 * va && std::fabs(q - std::rint(q)) <= 1e-6;
+}
+
+int kt_sizes(const grft_radar *r) {
+    return pow2_in(r->M, 16, 2048) && pow2_in(r->N, 4, 8192) ? GRFT_OK : GRFT_EUNSUPPORTED;
+}
+
+bool cells_ok(const grft_dsgrid *g, int32_t cell_begin, int32_t cell_count) {
+    return cell_begin >= 0 && cell_count >= 0 &&
+           (long)cell_begin + cell_count <= (long)g->vc.count * g->ac.count;
+}
+
+// Fine stage of a KT grid: transform length L = Fv, M <= L.
+int kt_fine_length(const grft_radar *r, const grft_dsgrid *g) {
+    const int L = g->Fv;
+    return (L == 64 || L == 128 || L == 256 || L == 512) && r->M <= L ? L : 0;
+}
+
+int kt_fine(const Ctx &c, const RadarD &R, const float2 *Z, const grft_dsgrid &g, int cell_begin, int cell_count,
+            int L, const float2 *chirp, float2 *Y, float *P) {
+    DsOut out;
+    out.Y = Y;
+    out.P = P;
+    out.cell_begin = cell_begin;
+    out.i0 = cell_begin / g.ac.count;
+    out.na_c = g.ac.count;
+    out.Fv = g.Fv;
+    out.Fa = g.Fa;
+    return launch_ds_fft_z(c, R, Z, g, cell_count, chirp, L, out);
+}
+
+}  // namespace
+
+int dskt_keystone(const grft_radar *radar, const grft_c32 *echo, grft_c32 *Skt, void *stream) {
+    if (!radar_ok(radar) || !echo || !Skt) return GRFT_EINVAL;
+    int e = kt_sizes(radar);
+    if (e) return e;
+    Ctx c;
+    if ((e = make_ctx(stream, c))) return e;
+    const RadarD R = radar_d(*radar);
+    float2 *S = (float2 *)workspace(c, (size_t)R.M * R.N * sizeof(float2));
+    if (!S) return GRFT_ENOMEM;
+    if ((e = launch_range_fft(c, R, (const float2 *)echo, S))) return e;
+    return launch_keystone(c, R, S, (float2 *)Skt);
+}
+
+int dskt_coarse_rm(const grft_radar *radar, const grft_c32 *Skt, const grft_dsgrid *grid, int32_t cell_begin,
+                   int32_t cell_count, grft_c32 *Z, void *stream) {
+    if (!radar_ok(radar) || !Skt || !Z || !ktgrid_ok(grid, radar) || !cells_ok(grid, cell_begin, cell_count))
+        return GRFT_EINVAL;
+    int e = kt_sizes(radar);
+    if (e) return e;
+    if (cell_count == 0) return GRFT_OK;
+    Ctx c;
+    if ((e = make_ctx(stream, c))) return e;
+    return launch_rm_kt(c, radar_d(*radar), *grid, cell_begin, cell_count, (const float2 *)Skt, (float2 *)Z);
+}
+
+int dskt_fine_dfm_fft(const grft_radar *radar, const grft_c32 *Z, const grft_dsgrid *grid, int32_t cell_begin,
+                      int32_t cell_count, grft_c32 *Y, float *P, void *stream) {
+    if (!radar_ok(radar) || !Z || (!Y && !P) || !ktgrid_ok(grid, radar) || !cells_ok(grid, cell_begin, cell_count) ||
+        cell_count > 65535)
+        return GRFT_EINVAL;
+    int e = kt_sizes(radar);
+    if (e) return e;
+    const int L = kt_fine_length(radar, grid);
+    if (!L) return GRFT_EUNSUPPORTED;
+    if (cell_count == 0) return GRFT_OK;
+    Ctx c;
+    if ((e = make_ctx(stream, c))) return e;
+    const RadarD R = radar_d(*radar);
+    float2 *chirp = (float2 *)workspace(c, (size_t)grid->Fa * L * sizeof(float2));
+    if (!chirp) return GRFT_ENOMEM;
+    if ((e = launch_gft_chirp(c, R, *grid, L, chirp))) return e;
+    return kt_fine(c, R, (const float2 *)Z, *grid, cell_begin, cell_count, L, chirp, (float2 *)Y, P);
+}
+
+int dskt_mfp(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid, grft_c32 *Y, float *P,
+             void *stream) {
+    if (!radar_ok(radar) || !echo || (!Y && !P) || !ktgrid_ok(grid, radar)) return GRFT_EINVAL;
+    int e = kt_sizes(radar);
+    if (e) return e;
+    const int L = kt_fine_length(radar, grid);
+    if (!L) return GRFT_EUNSUPPORTED;
+    Ctx c;
+    if ((e = make_ctx(stream, c))) return e;
+    const RadarD R = radar_d(*radar);
+    const int nac = grid->ac.count;
+    // whole folding-factor rows per chunk, the coarse output within the split budget
+    const size_t row_bytes = (size_t)nac * R.M * grid->r0_count * sizeof(float2);
+    long rows = (long)(split_budget() / row_bytes);
+    if (rows < 1) rows = 1;
+    if (rows > grid->vc.count) rows = grid->vc.count;
+    if (rows * nac > 65535) rows = 65535 / nac;
+    if (rows < 1) return GRFT_EUNSUPPORTED;
+    const size_t ch_bytes = align_up((size_t)grid->Fa * L * sizeof(float2));
+    const size_t kt_bytes = align_up((size_t)R.M * R.N * sizeof(float2));
+    size_t z_bytes = align_up((size_t)rows * row_bytes);
+    if (z_bytes < kt_bytes) z_bytes = kt_bytes;                 // the range spectra share it
+    unsigned char *ws = (unsigned char *)workspace(c, ch_bytes + kt_bytes + z_bytes);
+    if (!ws) return GRFT_ENOMEM;
+    float2 *chirp = (float2 *)ws;
+    float2 *Skt = (float2 *)(ws + ch_bytes);
+    float2 *Z = (float2 *)(ws + ch_bytes + kt_bytes);
+    if ((e = launch_range_fft(c, R, (const float2 *)echo, Z))) return e;
+    if ((e = launch_keystone(c, R, Z, Skt))) return e;
+    if ((e = launch_gft_chirp(c, R, *grid, L, chirp))) return e;
+    const long slab = (long)grid->Fv * nac * grid->Fa * grid->r0_count;   // outputs per coarse row
+    for (int i0 = 0; i0 < grid->vc.count; i0 += (int)rows) {
+        const int n = (int)(i0 + rows <= grid->vc.count ? rows : grid->vc.count - i0);
+        const int cb = i0 * nac, cc = n * nac;
+        if ((e = launch_rm_kt(c, R, *grid, cb, cc, Skt, Z))) return e;
+        if ((e = kt_fine(c, R, Z, *grid, cb, cc, L, chirp, Y ? (float2 *)Y + i0 * slab : nullptr,
+                         P ? P + i0 * slab : nullptr)))
+            return e;
+    }
+    return GRFT_OK;
+}
+
 int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
                             const grft_batch_item *items, int32_t n_items, grft_precision precision,
                             void *stream) {

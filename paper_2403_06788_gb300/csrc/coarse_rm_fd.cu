@@ -12,8 +12,9 @@
 //                inverse radix-2 decimation in time from the bit-reversed order to natural
 //                order, then the integer part of delta as an index offset when the range
 //                window [r0_begin, r0_begin + r0_count) is written (times w_c and 1/N).
-// Twiddles (one table per stage span) are built once per CTA with sincospif.
-#include "internal.cuh"
+// Twiddles (one table per stage span) are built once per CTA with sincospif; the
+// transforms are those of fft_smem.cuh.
+#include "fft_smem.cuh"
 
 namespace grft {
 
@@ -21,69 +22,16 @@ namespace {
 
 constexpr int FD_THREADS = 512;
 
-__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
-
-__device__ __forceinline__ unsigned brev_bits(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
-
-// Shared memory of a CTA: N data values, then N twiddles laid out per stage: the
-// butterflies of span h read tw[h + r] = exp(+j pi r / h), r < h, consecutive for
-// consecutive butterflies (no bank conflicts, unlike one table read at stride N / 2h).
-__device__ __forceinline__ void build_twiddles(float2 *tw, int N) {
-    for (int t = threadIdx.x; t < N; t += FD_THREADS) {
-        if (t == 0) {
-            tw[0] = make_float2(1.f, 0.f);
-            continue;
-        }
-        const int h = 1 << (31 - __clz(t)), r = t - h;
-        float sn, cs;
-        sincospif((float)r / (float)h, &sn, &cs);           // r / h exact (h a power of two)
-        tw[t] = make_float2(cs, sn);
-    }
-}
-
-// Forward DIF in place, natural order in, bit-reversed order out (exponent -).  Span
-// h = 2^lh: butterfly b pairs i = (b >> lh) 2h + (b & (h - 1)) with i + h.
-__device__ __forceinline__ void fft_dif_fwd(float2 *x, const float2 *tw, int logN) {
-    const int N = 1 << logN;
-    for (int lh = logN - 1; lh >= 0; --lh) {
-        const int h = 1 << lh;
-        for (int b = threadIdx.x; b < N / 2; b += FD_THREADS) {
-            const int r = b & (h - 1), i = ((b >> lh) << (lh + 1)) + r;
-            const float2 u = x[i], v = x[i + h];
-            x[i] = cadd2(u, v);
-            x[i + h] = cmul(csub2(u, v), conj2(tw[h + r]));
-        }
-        __syncthreads();
-    }
-}
-
-// Inverse DIT in place, bit-reversed order in, natural order out (exponent +, unscaled).
-__device__ __forceinline__ void fft_dit_inv(float2 *x, const float2 *tw, int logN) {
-    const int N = 1 << logN;
-    for (int lh = 0; lh < logN; ++lh) {
-        const int h = 1 << lh;
-        for (int b = threadIdx.x; b < N / 2; b += FD_THREADS) {
-            const int r = b & (h - 1), i = ((b >> lh) << (lh + 1)) + r;
-            const float2 u = x[i], v = cmul(x[i + h], tw[h + r]);
-            x[i] = cadd2(u, v);
-            x[i + h] = csub2(u, v);
-        }
-        __syncthreads();
-    }
-}
-
 __global__ __launch_bounds__(FD_THREADS) void k_range_fft(const float2 *__restrict__ echo, int M, int N,
                                                         int logN, float2 *__restrict__ S) {
     extern __shared__ float2 fd_smem[];
     float2 *x = fd_smem, *tw = fd_smem + N;
-    build_twiddles(tw, N);
+    build_twiddles<FD_THREADS>(tw, N);
     for (int m = blockIdx.x; m < M; m += gridDim.x) {
         __syncthreads();
         for (int n = threadIdx.x; n < N; n += FD_THREADS) x[n] = __ldg(echo + (long)m * N + n);
         __syncthreads();
-        fft_dif_fwd(x, tw, logN);
+        fft_dif_fwd<FD_THREADS>(x, 1, N, tw, logN);
         for (int p = threadIdx.x; p < N; p += FD_THREADS) S[(long)m * N + p] = x[p];   // bit-reversed order
     }
 }
@@ -97,7 +45,7 @@ __global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, i
     __shared__ float2 s_hi[128], s_lo[64];     // ramp factors exp(j 2 pi u f / N), u = 64 u_hi + u_lo
     __shared__ long s_I;                        // integer advance of the row
     __shared__ float s_f;                       // fractional advance of the row
-    build_twiddles(tw, N);
+    build_twiddles<FD_THREADS>(tw, N);
     const long rows = (long)cell_count * R.M;
     const float inv_n = 1.0f / (float)N;        // exact: N a power of two
     for (long row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -137,7 +85,7 @@ __global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, i
             x[p] = cmul(__ldg(Sm + p), ramp);
         }
         __syncthreads();
-        fft_dit_inv(x, tw, logN);
+        fft_dit_inv<FD_THREADS>(x, 1, N, tw, logN);
         const float2 wm = w_c[(long)cl * R.M + m];
         const float2 sc = make_float2(wm.x * inv_n, wm.y * inv_n);
         float2 *zrow = Z + row * g.r0_count;

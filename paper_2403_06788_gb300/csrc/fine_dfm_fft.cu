@@ -66,8 +66,11 @@ __device__ __forceinline__ void dft_regs_dif(float2 (&a)[P], const float2 *__res
     }
 }
 
-template <int P>
-__global__ __launch_bounds__(GF_THREADS) void k_gft_fft(const float2 *__restrict__ echo, int M, int N,
+// FROM_Z: the pulses come from a coarse output Z[cell][M][r0_count] (src = Z; rho and w
+// unused); otherwise they are gathered from the echo (src = echo) as s[m][n0 + rho] w.
+// e0 == nullptr: Y carries no range phase.
+template <int P, bool FROM_Z>
+__global__ __launch_bounds__(GF_THREADS) void k_gft_fft(const float2 *__restrict__ src, int M, int N,
                                                       const int32_t *__restrict__ rho,
                                                       const float2 *__restrict__ w,
                                                       const float2 *__restrict__ chirp,
@@ -96,8 +99,12 @@ __global__ __launch_bounds__(GF_THREADS) void k_gft_fft(const float2 *__restrict
         const int m = 32 * n1 + lane;
         float2 v = make_float2(0.f, 0.f);
         if (jok && m < M) {
-            const int n = r0_begin + j + rho[tab + m];
-            if ((unsigned)n < (unsigned)N) v = cmul(__ldg(echo + (long)m * N + n), w[tab + m]);
+            if (FROM_Z) {
+                v = __ldg(src + (tab + m) * r0_count + j);
+            } else {
+                const int n = r0_begin + j + rho[tab + m];
+                if ((unsigned)n < (unsigned)N) v = cmul(__ldg(src + (long)m * N + n), w[tab + m]);
+            }
         }
         x[n1] = v;
     }
@@ -105,7 +112,7 @@ __global__ __launch_bounds__(GF_THREADS) void k_gft_fft(const float2 *__restrict
     const int iv = c / out.na_c - out.i0, il = c % out.na_c;
     const int Fv = out.Fv, Fa = out.Fa;
     const int na_full = out.na_c * Fa;
-    const float2 ej = jok ? e0[j] : make_float2(1.f, 0.f);
+    const float2 ej = (jok && e0) ? e0[j] : make_float2(1.f, 0.f);
     const int f2 = (int)(__brev((unsigned)lane) >> 27);   // bin index across lanes after the DIF
     // twiddles of the cross-lane stages h = 16, 8, 4, 2: exp(j 2 pi (l mod h) / 2h)
     float2 tdif[4];
@@ -160,21 +167,45 @@ int launch_gft_chirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int L,
     return check_launch();
 }
 
-int launch_ds_fft(const Ctx &c, const RadarD &R, const float2 *echo, const grft_dsgrid &g, int cell_count,
-                  const int32_t *rho, const float2 *w, const float2 *chirp, const float2 *e0, int L,
-                  const DsOut &out) {
+template <bool FROM_Z>
+static int launch_gft(const Ctx &c, const RadarD &R, const float2 *src, const grft_dsgrid &g, int cell_count,
+                      const int32_t *rho, const float2 *w, const float2 *chirp, const float2 *e0, int L,
+                      const DsOut &out) {
     if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
     const dim3 grid((g.r0_count + GF_WARPS - 1) / GF_WARPS, cell_count);
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT_FFT);
-    if (L == 256)
-        k_gft_fft<8><<<grid, GF_THREADS, 0, c.stream>>>(echo, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
-                                                        g.r0_count, out);
-    else if (L == 512)
-        k_gft_fft<16><<<grid, GF_THREADS, 0, c.stream>>>(echo, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
-                                                         g.r0_count, out);
-    else
+    switch (L) {
+    case 64:
+        k_gft_fft<2, FROM_Z><<<grid, GF_THREADS, 0, c.stream>>>(src, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
+                                                                g.r0_count, out);
+        break;
+    case 128:
+        k_gft_fft<4, FROM_Z><<<grid, GF_THREADS, 0, c.stream>>>(src, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
+                                                                g.r0_count, out);
+        break;
+    case 256:
+        k_gft_fft<8, FROM_Z><<<grid, GF_THREADS, 0, c.stream>>>(src, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
+                                                                g.r0_count, out);
+        break;
+    case 512:
+        k_gft_fft<16, FROM_Z><<<grid, GF_THREADS, 0, c.stream>>>(src, R.M, R.N, rho, w, chirp, e0, g.r0_begin,
+                                                                 g.r0_count, out);
+        break;
+    default:
         return GRFT_EUNSUPPORTED;
+    }
     return check_launch();
+}
+
+int launch_ds_fft(const Ctx &c, const RadarD &R, const float2 *echo, const grft_dsgrid &g, int cell_count,
+                  const int32_t *rho, const float2 *w, const float2 *chirp, const float2 *e0, int L,
+                  const DsOut &out) {
+    return launch_gft<false>(c, R, echo, g, cell_count, rho, w, chirp, e0, L, out);
+}
+
+int launch_ds_fft_z(const Ctx &c, const RadarD &R, const float2 *Z, const grft_dsgrid &g, int cell_count,
+                    const float2 *chirp, int L, const DsOut &out) {
+    return launch_gft<true>(c, R, Z, g, cell_count, nullptr, nullptr, chirp, nullptr, L, out);
 }
 
 }  // namespace grft

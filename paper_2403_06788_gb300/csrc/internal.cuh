@@ -128,6 +128,16 @@ int launch_ds_fft(const Ctx &, const RadarD &, const float2 *echo, const grft_ds
                   const int32_t *rho, const float2 *w, const float2 *chirp, const float2 *e0, int L,
                   const DsOut &out);
 
+// The same transform on a coarse output Z[cell][M][r0_count], without a range phase.
+int launch_ds_fft_z(const Ctx &, const RadarD &, const float2 *Z, const grft_dsgrid &, int cell_count,
+                    const float2 *chirp, int L, const DsOut &out);
+
+// Keystone branch (kt.cu): Skt[M][N] (slot order of launch_range_fft) from the range spectra,
+// then the coarse H_KT,RM stage Z[cell][m][j].  M, N powers of two, M <= 2048, N <= 8192.
+int launch_keystone(const Ctx &, const RadarD &, const float2 *S, float2 *Skt);
+int launch_rm_kt(const Ctx &, const RadarD &, const grft_dsgrid &, int cell_begin, int cell_count,
+                 const float2 *Skt, float2 *Z);
+
 int launch_ds_simt(const Ctx &, const RadarD &, const float2 *echo, const float2 *Z,
                    const grft_dsgrid &, int cell_count, const int32_t *rho, const float2 *w,
                    const float2 *D, const float2 *e0, const DsOut &out);

@@ -241,5 +241,42 @@ def ds_adjoint_m1024(run: int = 0) -> Scenario:
     return Scenario("ds_adjoint_m1024", radar, tg, seed, plain=pg, ds=ds, snr_db=snrs)
 
 
+def kt_grid(radar: Radar, q_min: int, q_count: int, ac: Axis, Fa: int, L: int | None = None,
+            r0_begin: int = 0, r0_count: int | None = None) -> DSGrid:
+    """Keystone-branch (DS-KT-MFP) grid as a DSGrid: the coarse velocity axis is the folding
+    factor, centres q V_a for q = q_min .. q_min + q_count - 1 (V_a = lambda PRF / 2, eq.
+    velocity_Amb); the fine velocity is the baseband velocity on L = Fv transform bins of
+    V_a / L over [-V_a/2, V_a/2) (eq. Space_baseband_velocity); L defaults to the smallest
+    power of two >= M.  Its plain-equivalent velocity axis starts at (q_min - 1/2) V_a."""
+    va = radar.wavelength * radar.prf_hz / 2.0
+    if L is None:
+        L = 1 << max(0, (radar.M - 1).bit_length())
+    return DSGrid(r0_begin, radar.N - r0_begin if r0_count is None else r0_count,
+                  Axis(q_min * va, va, q_count), ac, L, Fa)
+
+
+def dskt_m64(run: int = 0) -> Scenario:
+    """Keystone-branch parity case on the plain_m64 radar (M=64, N=256, f_c=1 GHz, PRF=500 Hz,
+    dr=15 m, V_a=75 m/s): 3 targets with v in [-200, 200] m/s, a in [-15, 15] m/s^2, SNR 10 dB;
+    q in [-3, 3], 4 coarse a cells over [-20, 20] m/s^2, Fa=4, L=64."""
+    radar = Radar(M=64, N=256, fc_hz=1.0e9, prf_hz=500.0, dr_m=15.0)
+    seed = 1000 * 6 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tg, snrs = _random_targets(rng, radar, 3, 10.0, 10.0, vlim=200.0, alim=15.0)
+    ds = kt_grid(radar, -3, 7, Axis(-15.0, 10.0, 4), 4)
+    return Scenario("dskt_m64", radar, tg, seed, plain=ds.plain_equivalent(), ds=ds, snr_db=snrs)
+
+
+def dskt_m512(run: int = 0) -> Scenario:
+    """Keystone branch on the ds_m512 echo (same radar, seed and 8 targets): q in [-3, 3]
+    (V_a = 100 m/s, so the fine velocity covers [-350, 350) m/s in 3584 bins of 0.195 m/s),
+    the coarse a axis of ds_m512 (8 cells of 5 m/s^2), Fa=16, L=512: 4096 r0 x 3584 v x 128 a
+    = 1.88e9 hypotheses."""
+    base = ds_m512(run)
+    ds = kt_grid(base.radar, -3, 7, base.ds.ac, 16, 512)
+    return Scenario("dskt_m512", base.radar, base.targets, base.seed, plain=ds.plain_equivalent(), ds=ds,
+                    snr_db=base.snr_db)
+
+
 def scaled(s: Scenario, **radar_overrides) -> Scenario:
     return dataclasses.replace(s, radar=dataclasses.replace(s.radar, **radar_overrides))
