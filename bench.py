@@ -225,8 +225,10 @@ def run_suite(args):
     """The other workloads of the method, one JSON line: the M=2048 x N=8192 precision case
     (one coarse-v row of cells per call, both split precisions, sampled error against the
     oracle), 64 uneven CPIs in one graph-captured batched call (1024 range bins of interest
-    per CPI), and the differentiation pipeline at M=1024 x N=4096 (forward, top-1000 CFAR,
-    adjoint, 20 refinement steps)."""
+    per CPI), the differentiation pipeline at M=1024 x N=4096 (forward, top-1000 CFAR,
+    adjoint, 20 refinement steps), the FFT form of the fine stage and the frequency-domain
+    coarse stage against their dense / gather forms, and the keystone branch (DS-KT-MFP)
+    over its 1.88e9-hypothesis grid."""
     import torch
     import paper_2403_06788_gb300 as g
     import synth
@@ -359,7 +361,85 @@ def run_suite(args):
         "unit": UNIT, "fft_ms": ms_fft, "fft_value": units / (1e-3 * ms_fft),
         "dense_bf16x3_ms": ms_dense, "dense_value": units / (1e-3 * ms_dense),
         "status": g.grft_sync_status()}
+    del P, echo
+    torch.cuda.empty_cache()
+
+    out["keystone_m512"] = measure_kt(rows=0, steps=3, warmup=1)
     print(json.dumps({"suite": out}))
+    return 0
+
+
+def measure_kt(rows=0, steps=3, warmup=3):
+    """The keystone branch (DS-KT-MFP, Alg. 4) on the ds_m512 echo: dskt_mfp over q in
+    [-3, 3] (rows > 0: the first `rows` folding factors only, a profiling case) x 8 coarse a
+    cells, 512 baseband v bins x 16 fine a per cell, 4096 r0, P written (7.5 GB, larger than
+    L2), then top-1000 CA-CFAR.  CUDA events around `steps` steps after `warmup`; per-kernel
+    times from the library's own events; the fine-stage kernel's algorithmic bytes and FLOP."""
+    import dataclasses
+    import torch
+    import paper_2403_06788_gb300 as g
+    import synth
+    dev = torch.device("cuda", 0)
+    g.load()
+    stream = torch.cuda.current_stream()
+    sc = synth.dskt_m512()
+    R, ds = sc.radar, sc.ds
+    if rows > 0:
+        ds = dataclasses.replace(ds, vc=synth.Axis(ds.vc.start, ds.vc.step, min(rows, ds.vc.count)))
+    pgk = ds.plain_equivalent()
+    echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
+    P = torch.empty((ds.vc.count * ds.Fv, ds.ac.count * ds.Fa, ds.r0_count), device=dev)
+    det = torch.zeros(1000 * g._abi.DET_BYTES, dtype=torch.uint8, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    cfar = synth.CFAR(2, 16, 1e-6)
+    for _ in range(max(warmup, 1)):
+        g.dskt_mfp(R, echo, ds, None, P)
+        g.detect_peaks(P, cfar, 1000, axes=pgk, dr_m=R.dr_m, out=det, n_out=nout)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    g.grft_timing(True)
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        g.dskt_mfp(R, echo, ds, None, P)
+        e1.record(stream)
+        g.detect_peaks(P, cfar, 1000, axes=pgk, dr_m=R.dr_m, out=det, n_out=nout)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    kt = {k: g.grft_timing_get(k) for k in ("tables", "keystone", "coarse_rm", "contract_fft", "cfar", "topk")}
+    g.grft_timing(False)
+    map_ms = sum(a.elapsed_time(b) for a, b, c in ev) / steps
+    det_ms = sum(b.elapsed_time(c) for a, b, c in ev) / steps
+    dets, total = g.decode_detections(det, nout, 1000)
+    found = 0
+    for t in sc.targets:
+        found += int(((np.abs(dets["r0_m"] / R.dr_m - t.r0_bins) <= 1.0) & (np.abs(dets["v"] - t.v) <= 2 * pgk.v.step)
+                      & (np.abs(dets["a"] - t.a) <= 2 * pgk.a.step)).any())
+    units = ds.n_hyp * R.M
+    z_bytes = ds.n_cells * R.M * ds.r0_count * 8
+    L = ds.Fv
+    fine_ms = kt["contract_fft"][1] / max(kt["contract_fft"][0], 1)
+    fine_bytes = z_bytes + ds.n_hyp * 4
+    fine_flop = ds.n_cells * ds.r0_count * ds.Fa * (10.0 * (L // 2) * int(math.log2(L)) + 6.0 * L)
+    res = {
+        "workload": f"DS-KT-MFP on the ds_m512 echo (M=512 x N=4096): keystone transform, q in "
+                    f"[-3, {ds.vc.count - 4}] x 8 coarse a cells (H_KT,RM coarse stage), 512 baseband v bins "
+                    f"x 16 fine a per cell (FFT form), 4096 r0: {ds.n_hyp:.3g} hypotheses, P written; then "
+                    "top-1000 CA-CFAR",
+        "unit": UNIT, "steps": steps, "map_ms": map_ms, "detect_ms": det_ms, "value": units / (1e-3 * map_ms),
+        "step_value": units / (1e-3 * (map_ms + det_ms)),
+        "kernels_ms_per_step": {k: v[1] / steps for k, v in kt.items()},
+        "fine_stage": {"bytes_per_launch": fine_bytes, "flop_per_launch": fine_flop, "ms_per_launch": fine_ms,
+                       "achieved_gbs": fine_bytes / (1e-3 * fine_ms) / 1e9,
+                       "achieved_tflops": fine_flop / (1e-3 * fine_ms) / 1e12},
+        "targets_found": f"{found}/{len(sc.targets)}", "detections": int(total),
+        "status": g.grft_sync_status()}
+    del P, echo
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_kt(args):
+    print(json.dumps({"keystone": measure_kt(args.kt_rows, args.steps, args.warmup)}))
     return 0
 
 
@@ -440,6 +520,10 @@ def main():
     ap.add_argument("--pd-snr", default="-18,-15,-13,-11,-9,-6")
     ap.add_argument("--suite", action="store_true",
                     help="time the precision, batching and differentiation workloads (one JSON line)")
+    ap.add_argument("--kt", action="store_true",
+                    help="time the keystone branch (DS-KT-MFP map + detection) alone (one JSON line)")
+    ap.add_argument("--kt-rows", type=int, default=0,
+                    help="with --kt: the first N folding factors only (small profiling case)")
     ap.add_argument("--coarse-rm-steps", type=int, default=3,
                     help="timed calls of the standalone coarse-RM gather (0: skip)")
     args = ap.parse_args()
@@ -449,6 +533,8 @@ def main():
         return run_reference(args)
     if args.suite:
         return run_suite(args)
+    if args.kt:
+        return run_kt(args)
     if args.pd:
         return run_pd(args)
 

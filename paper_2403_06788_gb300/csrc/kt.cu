@@ -21,9 +21,10 @@
 //   exp(+j 2 pi k_s (fbar vq t - c_2,c t^2) / (N dr))
 //     = exp(+j 2 pi k_s D / N) * exp(+j 2 pi E_k delta1),
 //   delta1 = vq t / dr, D = delta1 - c_2,c t^2 / dr, E_k = k_s eps_k / N,
-// i.e. the band-limited advance by D bins (fractional part as a ramp, integer part as an
-// index offset on output, as in k_rm_fd) times a small dispersive factor; then the inverse
-// transform, the range window, times H_pre-DFM = exp(j 4 pi c_2,c t^2 / lambda) and 1/N.
+// i.e. the band-limited advance by D bins (fractional part f as a ramp, integer part as an
+// index offset on output, as in k_rm_fd) times a small dispersive factor, one sincospi of
+// k_s f / N + E_k delta1 turns per element; then the inverse transform, the range window,
+// times H_pre-DFM = exp(j 4 pi c_2,c t^2 / lambda) and 1/N.
 #include "fft_smem.cuh"
 
 namespace grft {
@@ -123,7 +124,6 @@ __global__ __launch_bounds__(KT_THREADS) void k_rm_kt(RadarD R, grft_dsgrid g, i
     const int N = R.N;
     float2 *x = kt_smem, *tw = kt_smem + N;
     float *E = (float *)(kt_smem + 2L * N);    // E[p] = k_s eps_k / N
-    __shared__ float2 s_hi[128], s_lo[64];     // ramp factors exp(j 2 pi u f / N), u = 64 u_hi + u_lo
     __shared__ long s_I;                        // integer advance of the row
     __shared__ float s_f, s_d1;                 // fractional advance, delta1
     __shared__ float2 s_w;                      // H_pre-DFM of the row
@@ -155,28 +155,15 @@ __global__ __launch_bounds__(KT_THREADS) void k_rm_kt(RadarD R, grft_dsgrid g, i
         __syncthreads();
         const long I = s_I;
         const float f = s_f, d1 = s_d1;
-        for (int u = threadIdx.x; u < 128 + 64; u += KT_THREADS) {
-            float sn, cs;
-            if (u < 128) {
-                sincospif(2.0f * (float)(64 * u) * f / (float)N, &sn, &cs);
-                s_hi[u] = make_float2(cs, sn);
-            } else {
-                sincospif(2.0f * (float)(u - 128) * f / (float)N, &sn, &cs);
-                s_lo[u - 128] = make_float2(cs, sn);
-            }
-        }
-        float sn0, cs0;
-        sincospif(-f, &sn0, &cs0);              // exp(-j pi f): k_s = u - N/2
-        const float2 c0 = make_float2(cs0, sn0);
-        __syncthreads();
         const float2 *Sm = Skt + (long)m * N;
         for (int p = threadIdx.x; p < N; p += KT_THREADS) {
             const int k = (int)brev_bits((unsigned)p, logN);
-            const int u = k < N / 2 ? k + N / 2 : k - N / 2;      // signed k + N/2
-            float sd, cd;
-            sincospif(2.0f * E[p] * d1, &sd, &cd);                 // dispersive part, |angle| << 1 turn
-            const float2 ramp = cmul(cmul(c0, cmul(s_hi[u >> 6], s_lo[u & 63])), make_float2(cd, sd));
-            x[p] = cmul(__ldg(Sm + p), ramp);
+            const int ks = k < N / 2 ? k : k - N;
+            // turns of the ramp: k_s f / N (|.| <= 1/2) + the dispersive E_k delta1 (small)
+            const float phi = fmaf(E[p], d1, (float)ks * f * inv_n);
+            float sn, cs;
+            sincospif(2.0f * phi, &sn, &cs);
+            x[p] = cmul(__ldg(Sm + p), make_float2(cs, sn));
         }
         __syncthreads();
         fft_dit_inv<KT_THREADS>(x, 1, N, tw, logN);
