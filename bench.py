@@ -333,39 +333,68 @@ def run_suite(args):
     del P, echo
     torch.cuda.empty_cache()
 
-    # ------------------------------------------------ FFT form of the fine stage vs the dense form
+    out.update(measure_forms(0, 3, 1))
+    out["keystone_m512"] = measure_kt(rows=0, steps=3, warmup=1)
+    print(json.dumps({"suite": out}))
+    return 0
+
+
+def measure_forms(cells=0, steps=3, warmup=1):
+    """The paper's own forms of the two stages on the M=512 x N=4096 echo: the FFT form of
+    the fine stage (Alg. 2; fine velocity step one bin of a 512-point transform, 96 x 16 fine
+    hypotheses per cell) against the dense split-BF16 contraction of the same hypotheses, and
+    the frequency-domain coarse stage (Alg. 1) against the time-domain TMA gather, into Z.
+    cells > 0: the first `cells` coarse cells only (a profiling case); else all 256 for the
+    fine stage and 32 for the coarse stage (Z of 32 cells = 537 MB)."""
+    import torch
+    import paper_2403_06788_gb300 as g
+    import synth
+    dev = torch.device("cuda", 0)
+    g.load()
+    stream = torch.cuda.current_stream()
     sc = synth.ds_m512()
     R = sc.radar
     L, Fv = 512, 96                                   # fine velocity step = one bin of 512
     vstep = R.wavelength * R.prf_hz * Fv / (2 * L)
     ds = synth.DSGrid(0, R.N, synth.Axis(-300.0 + vstep / 2, vstep, 32), sc.ds.ac, Fv, sc.ds.Fa)
+    nc = ds.n_cells if cells <= 0 else min(cells, ds.n_cells)
+    nrow = (nc + ds.ac.count - 1) // ds.ac.count
     echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
-    P = torch.empty((ds.vc.count * Fv, ds.ac.count * ds.Fa, ds.r0_count), device=dev)
-    units = ds.n_cells * ds.n_fine * ds.r0_count * R.M
-    ms_fft = _timed(lambda: g.dsgrft_fine_dfm_fft(R, echo, ds, 0, ds.n_cells, None, P), 3, stream)
-    ms_dense = _timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.n_cells, "bf16x3", None, P), 3, stream)
-    # ------------------------------------------------ frequency-domain coarse stage vs the gather
-    dsz = sc.ds
-    ncz = 32                                          # 32 cells x 512 x 4096 complex64 = 537 MB
-    Z = torch.empty((ncz, R.M, dsz.r0_count), dtype=torch.complex64, device=dev)
-    ms_fd = _timed(lambda: g.dsgrft_coarse_rm_fd(R, echo, dsz, 0, ncz, Z), 3, stream)
-    ms_td = _timed(lambda: g.dsgrft_coarse_rm(R, echo, dsz, 0, ncz, Z), 3, stream)
-    out["coarse_stage_m512"] = {
-        "workload": "coarse range-migration correction of 32 cells x 512 pulses x 4096 bins into Z (complex64)",
-        "frequency_domain_ms": ms_fd, "time_domain_gather_ms": ms_td,
-        "frequency_domain_rows_per_s": ncz * R.M / (1e-3 * ms_fd)}
-    del Z
-    out["fft_form_m512"] = {
-        "workload": "DS-GRFT M=512 x N=4096, coarse 32 x 8, fine 96 x 16 (fine velocity step = one bin of a "
-                    "512-point transform), 1.6e9 hypotheses, P written",
-        "unit": UNIT, "fft_ms": ms_fft, "fft_value": units / (1e-3 * ms_fft),
-        "dense_bf16x3_ms": ms_dense, "dense_value": units / (1e-3 * ms_dense),
-        "status": g.grft_sync_status()}
-    del P, echo
-    torch.cuda.empty_cache()
+    P = torch.empty((nrow * Fv, ds.ac.count * ds.Fa, ds.r0_count), device=dev)
+    units = nc * ds.n_fine * ds.r0_count * R.M
 
-    out["keystone_m512"] = measure_kt(rows=0, steps=3, warmup=1)
-    print(json.dumps({"suite": out}))
+    def timed(fn):
+        for _ in range(max(warmup, 1)):
+            fn()
+        return _timed(fn, steps, stream)
+    ms_fft = timed(lambda: g.dsgrft_fine_dfm_fft(R, echo, ds, 0, nc, None, P))
+    ms_dense = timed(lambda: g.dsgrft_fine_dfm(R, None, echo, ds, 0, nc, "bf16x3", None, P))
+    del P
+    torch.cuda.empty_cache()
+    dsz = sc.ds
+    ncz = 32 if cells <= 0 else min(cells, 32)
+    Z = torch.empty((ncz, R.M, dsz.r0_count), dtype=torch.complex64, device=dev)
+    ms_fd = timed(lambda: g.dsgrft_coarse_rm_fd(R, echo, dsz, 0, ncz, Z))
+    ms_td = timed(lambda: g.dsgrft_coarse_rm(R, echo, dsz, 0, ncz, Z))
+    del Z, echo
+    torch.cuda.empty_cache()
+    return {
+        "coarse_stage_m512": {
+            "workload": f"coarse range-migration correction of {ncz} cells x 512 pulses x 4096 bins into Z "
+                        "(complex64)",
+            "frequency_domain_ms": ms_fd, "time_domain_gather_ms": ms_td,
+            "frequency_domain_rows_per_s": ncz * R.M / (1e-3 * ms_fd)},
+        "fft_form_m512": {
+            "workload": f"DS-GRFT M=512 x N=4096, {nc} coarse cells (of 32 x 8), fine 96 x 16 (fine velocity step = "
+                        "one bin of a 512-point transform), P written",
+            "hypotheses": nc * ds.n_fine * ds.r0_count,
+            "unit": UNIT, "fft_ms": ms_fft, "fft_value": units / (1e-3 * ms_fft),
+            "dense_bf16x3_ms": ms_dense, "dense_value": units / (1e-3 * ms_dense),
+            "status": g.grft_sync_status()}}
+
+
+def run_forms(args):
+    print(json.dumps({"forms": measure_forms(args.cells, args.steps, args.warmup)}))
     return 0
 
 
@@ -520,6 +549,9 @@ def main():
     ap.add_argument("--pd-snr", default="-18,-15,-13,-11,-9,-6")
     ap.add_argument("--suite", action="store_true",
                     help="time the precision, batching and differentiation workloads (one JSON line)")
+    ap.add_argument("--forms", action="store_true",
+                    help="time the FFT-form fine stage and the frequency-domain coarse stage against the dense "
+                         "and gather forms (one JSON line; --cells N: the first N cells)")
     ap.add_argument("--kt", action="store_true",
                     help="time the keystone branch (DS-KT-MFP map + detection) alone (one JSON line)")
     ap.add_argument("--kt-rows", type=int, default=0,
@@ -535,6 +567,8 @@ def main():
         return run_suite(args)
     if args.kt:
         return run_kt(args)
+    if args.forms:
+        return run_forms(args)
     if args.pd:
         return run_pd(args)
 
