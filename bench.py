@@ -473,11 +473,13 @@ def run_kt(args):
 
 
 def run_pd(args):
-    """Detection probability against SNR for plain GRFT and DS-GRFT on the same hypotheses
-    (the paper's Monte-Carlo comparison, Sec. VI): M=256 x N=512, one target per trial at a
-    random on-grid (r0, v, a), CN(0,1) noise, the fixed LRT threshold -M ln(Pfa) on |Y|^2
-    with the 3x3x3 local maximum; a trial detects when a detection lies within one cell of
-    the truth on every axis.  One JSON line."""
+    """Detection probability against SNR for plain GRFT, DS-GRFT (time-domain coarse gather
+    and, as the paper computes it, frequency-domain coarse stage) and DS-KT-MFP (the paper's
+    Monte-Carlo comparison, Sec. VI): M=256 x N=512, one target per trial at a random
+    on-grid (r0, v, a), CN(0,1) noise, the fixed LRT threshold -M ln(Pfa) on |Y|^2 with the
+    3x3x3 local maximum; a trial detects when a detection lies within one cell of the truth
+    on every axis.  The keystone grid (q in [-1, 1], 256 baseband bins of V_a / 256 = the
+    DS-GRFT fine velocity step) contains every DS-GRFT hypothesis.  One JSON line."""
     import torch
     import paper_2403_06788_gb300 as g
     import synth
@@ -492,13 +494,19 @@ def run_pd(args):
     cf = synth.CFAR(2, 16, pfa_cell, fixed_thresh=thresh, mode=1)
     K = 64
     P = torch.empty((nv, na, R.N), device=dev)
+    ktg = synth.kt_grid(R, -1, 3, ds.ac, ds.Fa, 256)
+    kpg = ktg.plain_equivalent()
+    kv_off = int(round((pg.v.start - kpg.v.start) / kpg.v.step))   # same velocity lattice
+    assert abs(kpg.v.step - pg.v.step) < 1e-12 and abs(kpg.v.start + kv_off * kpg.v.step - pg.v.start) < 1e-9
+    Pk = torch.empty((kpg.v.count, na, R.N), device=dev)
+    Zfd = torch.empty((ds.n_cells, R.M, R.N), dtype=torch.complex64, device=dev)
     gen = torch.Generator(device=dev)
     rng = np.random.default_rng(7000)
     snrs = [float(x) for x in args.pd_snr.split(",")]
     margin = synth.walk_margin_bins(R, 100.0, 20.0) + 2
     res = {}
     for snr in snrs:
-        hits = {"grft": 0, "dsgrft": 0}
+        hits = {"grft": 0, "dsgrft": 0, "dsgrft_fd": 0, "dsktmfp": 0}
         for trial in range(args.pd_trials):
             j = int(rng.integers(1, nv - 1))
             k = int(rng.integers(1, na - 1))
@@ -509,20 +517,33 @@ def run_pd(args):
             gen.manual_seed(1_000_003 * (trial + 1) + int(1000 * (snr + 100)))
             wn = torch.randn((R.M, R.N, 2), generator=gen, device=dev) * math.sqrt(0.5)
             echo = (sig + torch.complex(wn[..., 0], wn[..., 1])).contiguous()
-            for name in ("grft", "dsgrft"):
+            for name in ("grft", "dsgrft", "dsgrft_fd", "dsktmfp"):
+                jt = j
                 if name == "grft":
                     g.grft_plain(R, echo, pg, None, P)
-                else:
+                    out, n = g.detect_peaks(P, cf, K)
+                elif name == "dsgrft":
                     g.dsgrft_fine_dfm(R, None, echo, ds, 0, ds.n_cells, "bf16x3", None, P)
-                out, n = g.detect_peaks(P, cf, K)
+                    out, n = g.detect_peaks(P, cf, K)
+                elif name == "dsgrft_fd":               # the paper's form: mGIFT in range frequency
+                    g.dsgrft_coarse_rm_fd(R, echo, ds, 0, ds.n_cells, Zfd)
+                    g.dsgrft_fine_dfm(R, Zfd, echo, ds, 0, ds.n_cells, "bf16x3", None, P)
+                    out, n = g.detect_peaks(P, cf, K)
+                else:
+                    g.dskt_mfp(R, echo, ktg, None, Pk)
+                    out, n = g.detect_peaks(Pk, cf, K)
+                    jt = j + kv_off
                 dets, _ = g.decode_detections(out, n, K)
-                near = (np.abs(dets["n0"].astype(int) - n0) <= 1) & (np.abs(dets["vi"].astype(int) - j) <= 1) & \
+                near = (np.abs(dets["n0"].astype(int) - n0) <= 1) & (np.abs(dets["vi"].astype(int) - jt) <= 1) & \
                     (np.abs(dets["ai"].astype(int) - k) <= 1)
                 hits[name] += int(near.any())
         res[f"{snr:g}"] = {name: hits[name] / args.pd_trials for name in hits}
     print(json.dumps({"pd": {
-        "workload": "M=256 x N=512, f_c 1.5 GHz, PRF 1 kHz; coarse 8 x 2, fine 64 x 8 (512 v x 16 a x 512 r0); "
-                    "one on-grid target per trial, CN(0,1) noise, fixed threshold -M ln(1e-6) + local maximum",
+        "workload": "M=256 x N=512, f_c 1.5 GHz, PRF 1 kHz; GRFT / DS-GRFT (time-domain gather; dsgrft_fd: "
+                    "frequency-domain coarse stage): coarse 8 x 2, fine 64 x 8 (512 v x 16 a "
+                    "x 512 r0); DS-KT-MFP: q in [-1, 1] x 2 a cells, 256 baseband v x 8 a (768 v x 16 a x 512 r0, "
+                    "same lattice); one on-grid target per trial, CN(0,1) noise, fixed threshold -M ln(1e-6) + "
+                    "local maximum",
         "snr_db_per_sample": snrs, "trials_per_snr": args.pd_trials, "pd": res,
         "range_migration": residual_migration(R, ds), "status": g.grft_sync_status()}}))
     return 0
