@@ -79,7 +79,10 @@ typedef struct { int32_t r0_begin, r0_count; grft_axis vc, ac; int32_t Fv, Fa; }
 typedef enum {
     GRFT_FP32 = 0,   /* FP32 SIMT contraction (FFMA) */
     GRFT_BF16X3 = 1, /* tcgen05 tensor cores, hi/lo-split BF16 operands, 3 products, FP32 accumulate */
-    GRFT_FP16X3 = 2  /* tcgen05 tensor cores, hi/lo-split FP16 operands, 3 products, FP32 accumulate */
+    GRFT_FP16X3 = 2, /* tcgen05 tensor cores, hi/lo-split FP16 operands, 3 products, FP32 accumulate */
+    GRFT_FP16X1 = 3  /* tcgen05 tensor cores, FP16 operands (one rounding each), 1 product, FP32
+                        accumulate: not the split form; within the 2e-3-of-peak bound of the split
+                        path on the benchmark workloads (measured errors in the tests) */
 } grft_precision;
 
 typedef enum { GRFT_GATHER_NEAREST = 0, GRFT_GATHER_LINEAR = 1 } grft_gather;

@@ -390,7 +390,8 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
         cell_begin < 0 || cell_count < 0 ||
         (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count || cell_count > 65535)
         return GRFT_EINVAL;
-    if (precision != GRFT_FP32 && precision != GRFT_BF16X3 && precision != GRFT_FP16X3)
+    if (precision != GRFT_FP32 && precision != GRFT_BF16X3 && precision != GRFT_FP16X3 &&
+        precision != GRFT_FP16X1)
         return GRFT_EINVAL;
     Ctx c;
     int e = make_ctx(stream, c);
@@ -439,7 +440,8 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     unsigned char *zp = dptr + 2 * d_bytes;
     uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
-    const bool fp16 = precision == GRFT_FP16X3;
+    const bool fp16 = precision == GRFT_FP16X3 || precision == GRFT_FP16X1;
+    const int nprod = precision == GRFT_FP16X1 ? 1 : 3;
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
     DsTcItem it;
     it.echo = (const float2 *)echo;
@@ -454,7 +456,7 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     it.cell_begin = cell_begin;
     it.cell_count = cell_count;
     it.i0 = cell_begin / grid->ac.count;
-    return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
+    return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, nprod, Zhi, Zlo, z_rows);
 }
 
 int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
@@ -654,7 +656,7 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
                             const grft_batch_item *items, int32_t n_items, grft_precision precision,
                             void *stream) {
     if (!radar || !grid || !items || n_items <= 0 || n_items > 256) return GRFT_EINVAL;
-    if (precision != GRFT_BF16X3 && precision != GRFT_FP16X3) return GRFT_EINVAL;
+    if (precision != GRFT_BF16X3 && precision != GRFT_FP16X3 && precision != GRFT_FP16X1) return GRFT_EINVAL;
     int Mmax = 0, Nmax = 0;
     long rpad_max = 0;
     for (int i = 0; i < n_items; ++i) {
@@ -703,7 +705,8 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     unsigned char *zp = dptr + 2 * d_bytes;
     uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
-    const bool fp16 = precision == GRFT_FP16X3;
+    const bool fp16 = precision == GRFT_FP16X3 || precision == GRFT_FP16X1;
+    const int nprod = precision == GRFT_FP16X1 ? 1 : 3;
     if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
     if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;
     if ((e = launch_dechirp_split(c, R, g, Mpad, Fpad, fp16, Bhi, Blo))) return e;
@@ -724,7 +727,7 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
         it.cell_count = ncell;
         it.i0 = 0;
     }
-    return launch_ds_tc(c, list, n_items, g, rho, w, 0, Mmax, Bhi, Blo, Mpad, fp16, Zhi, Zlo, z_rows);
+    return launch_ds_tc(c, list, n_items, g, rho, w, 0, Mmax, Bhi, Blo, Mpad, fp16, nprod, Zhi, Zlo, z_rows);
 }
 
 int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft_cfar *cfar,

@@ -8,7 +8,9 @@
 // It runs as one real GEMM (the "4M" form) with K' = 2M and N' = 2F:
 //   [Re Zc | Im Zc] (rows n0)  x  [[Re D, Im D], [-Im D, Re D]]  =  [Re Y~ | Im Y~]
 // and each real operand x is split as hi = round16(x), lo = round16(x - hi) (BF16 or FP16),
-// accumulating hi*hi + hi*lo + lo*hi in FP32 (three tcgen05.mma per K step).
+// accumulating hi*hi + hi*lo + lo*hi in FP32 (three tcgen05.mma per K step).  The
+// single-product FP16 mode (NP = 1) keeps only hi*hi: one tcgen05.mma per K step, no lo
+// planes loaded or written.
 //
 // k_coarse_split (kernel a, the mGIFT of Alg. 1 in the time domain): one CTA per (cell,
 //   128-bin tile).  It gathers every bin's samples at n0 + rho_c(m) from the L2-resident
@@ -53,8 +55,8 @@ constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unw
 // BN real columns per tile (BN/2 fine hypotheses) and ST pipeline stages.
 // ... and BK real k per stage: 64 (128-byte swizzle rows) or 32 (64-byte swizzle rows, so
 // twice the stages fit the same shared memory).
-constexpr size_t tc_smem_bytes(int BN, int ST, int BK) {
-    return (size_t)ST * (2 * (size_t)TC_BM * BK * 2 + 2 * (size_t)BN * BK * 2) + 1024;
+constexpr size_t tc_smem_bytes(int BN, int ST, int BK, int NP) {
+    return (size_t)ST * ((NP == 3 ? 2 : 1) * ((size_t)TC_BM * BK * 2 + (size_t)BN * BK * 2)) + 1024;
 }
 
 constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
@@ -87,6 +89,7 @@ struct TcBatch {
     int n_items, total_ctas, total_tiles;
     int tiles_n, F, Fv, Fa, na_c;
     int fp16;
+    int nprod;              // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only (no lo planes)
     uint32_t idesc;
     int *status;
     uint64_t wait_limit;
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     uint16_t *zl = Zlo + row * (size_t)B.zld + g * 8;
 
     const uint64_t pol_z = l2_policy_evict_first();
+    const bool with_lo = B.nprod == 3;          // block-uniform
     auto split_store = [&](int kt, const float (&re)[8], const float (&im)[8]) {
         uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
@@ -337,9 +341,11 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
         }
         const int o = kt * TC_BK;
         st_global_v4_hint(zh + o, rh[0], rh[1], rh[2], rh[3], pol_z);
-        st_global_v4_hint(zl + o, rl[0], rl[1], rl[2], rl[3], pol_z);
         st_global_v4_hint(zh + o + 32, ih[0], ih[1], ih[2], ih[3], pol_z);
-        st_global_v4_hint(zl + o + 32, il[0], il[1], il[2], il[3], pol_z);
+        if (with_lo) {
+            st_global_v4_hint(zl + o, rl[0], rl[1], rl[2], rl[3], pol_z);
+            st_global_v4_hint(zl + o + 32, il[0], il[1], il[2], il[3], pol_z);
+        }
     };
 
     // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
 }
 
 // =========================================================================== kernel b
-template <int BN, int ST, int CL, int BK>
+template <int BN, int ST, int CL, int BK, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
             const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
@@ -427,11 +433,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr int TC_STAGES = ST;
     constexpr uint32_t TC_A_BYTES = TC_BM * BK * 2;    // per plane
     constexpr uint32_t TC_B_BYTES = BN * BK * 2;       // per plane
-    constexpr uint32_t TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+    constexpr uint32_t NPL = NP == 3 ? 2 : 1;          // planes per operand (hi, lo)
+    constexpr uint32_t TC_STAGE_BYTES = NPL * (TC_A_BYTES + TC_B_BYTES);
+    constexpr uint32_t TC_B_OFF = NPL * TC_A_BYTES;    // B planes follow the A planes
     constexpr int KSUB = 64 / BK;                      // stages per 32-pulse group
     constexpr uint32_t TC_TMEM_COLS = 2 * BN;          // two accumulators
     static_assert(BN % 32 == 0 && BN <= 256 && TC_TMEM_COLS >= 32, "tile");
     static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
+    static_assert(NP == 3 || NP == 1, "three products (split) or one (FP16)");
     constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
     constexpr uint32_t TC_B_PART = TC_B_BYTES / CL;    // rows of B this CTA fetches (per plane)
     extern __shared__ unsigned char smem_raw[];
@@ -497,17 +506,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     unsigned char *st = smem + s * TC_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
                     tma_load_2d(st, &mapAhi, kt * BK, arow, &full[s]);
-                    tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * BK, arow, &full[s]);
+                    if (NP == 3) tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * BK, arow, &full[s]);
                     if (CL == 1) {
-                        tma_load_2d(st + 2 * TC_A_BYTES, &mapBhi, kt * BK, nt * TC_BN, &full[s]);
-                        tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &mapBlo, kt * BK, nt * TC_BN,
-                                    &full[s]);
+                        tma_load_2d(st + TC_B_OFF, &mapBhi, kt * BK, nt * TC_BN, &full[s]);
+                        if (NP == 3)
+                            tma_load_2d(st + TC_B_OFF + TC_B_BYTES, &mapBlo, kt * BK, nt * TC_BN, &full[s]);
                     } else {   // this CTA's share of the B rows, delivered to every CTA of the cluster
                         const int brow = nt * TC_BN + rank * (TC_BN / CL);
-                        tma_load_2d_mc(st + 2 * TC_A_BYTES + rank * TC_B_PART, &mapBhi, kt * BK, brow,
-                                       &full[s], CL_MASK);
-                        tma_load_2d_mc(st + 2 * TC_A_BYTES + TC_B_BYTES + rank * TC_B_PART, &mapBlo, kt * BK,
-                                       brow, &full[s], CL_MASK);
+                        tma_load_2d_mc(st + TC_B_OFF + rank * TC_B_PART, &mapBhi, kt * BK, brow, &full[s],
+                                       CL_MASK);
+                        if (NP == 3)
+                            tma_load_2d_mc(st + TC_B_OFF + TC_B_BYTES + rank * TC_B_PART, &mapBlo, kt * BK, brow,
+                                           &full[s], CL_MASK);
                     }
                     last_it = it;
                 }
@@ -544,14 +554,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t st = sbase + s * TC_STAGE_BYTES;
                     const uint32_t a_hi = st, a_lo = st + TC_A_BYTES;
-                    const uint32_t b_hi = st + 2 * TC_A_BYTES, b_lo = b_hi + TC_B_BYTES;
+                    const uint32_t b_hi = st + TC_B_OFF, b_lo = b_hi + TC_B_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t off = kk * 32;   // 16 elements x 2 bytes inside the swizzle row
                         umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_hi + off), B.idesc,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_lo + off), B.idesc, 1u);
-                        umma_f16(d_tmem, umma_desc<BK>(a_lo + off), umma_desc<BK>(b_hi + off), B.idesc, 1u);
+                        if (NP == 3) {
+                            umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_lo + off), B.idesc, 1u);
+                            umma_f16(d_tmem, umma_desc<BK>(a_lo + off), umma_desc<BK>(b_hi + off), B.idesc, 1u);
+                        }
                     }
                     issued_any = true;
                     if (CL == 1)
@@ -749,13 +761,14 @@ int tune_variant(const Ctx &c, const TcBatch &, Run run) {
     return best;
 }
 
-template <int BN, int ST, int CL, int BK>
+template <int BN, int ST, int CL, int BK, int NP>
 int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
     static bool attr[64] = {false};
     static int max_clusters[64] = {0};
-    const size_t smem = tc_smem_bytes(BN, ST, BK);
-    if (!set_smem_attr((const void *)k_ds_tc<BN, ST, CL, BK>, smem, c.device, attr)) return GRFT_ECUDA;
+    const size_t smem = tc_smem_bytes(BN, ST, BK, NP);
+    static_assert(tc_smem_bytes(BN, ST, BK, NP) <= 227 * 1024, "shared memory");
+    if (!set_smem_attr((const void *)k_ds_tc<BN, ST, CL, BK, NP>, smem, c.device, attr)) return GRFT_ECUDA;
     const uint64_t kdim = 2ull * Mpad;
     const CUtensorMapSwizzle sw = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     CUtensorMap mzh, mzl, mbh, mbl;
@@ -797,7 +810,7 @@ int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
         if (max_clusters[c.device] <= 0) {
             cfg.gridDim = dim3(CL * (c.num_sms / CL));
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k_ds_tc<BN, ST, CL, BK>, &cfg) != cudaSuccess || n <= 0)
+            if (cudaOccupancyMaxActiveClusters(&n, k_ds_tc<BN, ST, CL, BK, NP>, &cfg) != cudaSuccess || n <= 0)
                 return GRFT_ECUDA;
             max_clusters[c.device] = n;
         }
@@ -806,19 +819,28 @@ int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
     const int groups = bb.total_tiles < slots ? bb.total_tiles : slots;
     cfg.gridDim = dim3(CL * groups);
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
-    if (cudaLaunchKernelEx(&cfg, k_ds_tc<BN, ST, CL, BK>, mzh, mzl, mbh, mbl, bb) != cudaSuccess)
+    if (cudaLaunchKernelEx(&cfg, k_ds_tc<BN, ST, CL, BK, NP>, mzh, mzl, mbh, mbl, bb) != cudaSuccess)
         return GRFT_ECUDA;
     return check_launch();
 }
 
 int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo,
                         long zrows, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    if (b.nprod == 1) {   // no lo planes: twice the stages in the same shared memory
+        switch (variant) {
+            case 1: return launch_gemm<128, 6, 1, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 2: return launch_gemm<256, 4, 2, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 3: return launch_gemm<256, 8, 1, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 4: return launch_gemm<256, 8, 2, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            default: return launch_gemm<256, 4, 1, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        }
+    }
     switch (variant) {
-        case 1: return launch_gemm<128, 3, 1, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 2: return launch_gemm<256, 2, 2, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 3: return launch_gemm<256, 4, 1, 32>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 4: return launch_gemm<256, 4, 2, 32>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        default: return launch_gemm<256, 2, 1, 64>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 1: return launch_gemm<128, 3, 1, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 2: return launch_gemm<256, 2, 2, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 3: return launch_gemm<256, 4, 1, 32, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 4: return launch_gemm<256, 4, 2, 32, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        default: return launch_gemm<256, 2, 1, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
     }
 }
 
@@ -888,8 +910,8 @@ void release_pipe(int dev) {
 
 int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
-                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],
-                 long z_rows_cap) {
+                 const uint16_t *Blo, int Mpad, bool fp16, int nprod, uint16_t *const Zhi[2],
+                 uint16_t *const Zlo[2], long z_rows_cap) {
     const int F = g.Fv * g.Fa;
     const int Fpad = (F + 127) / 128 * 128;
     TcBatch b;
@@ -904,6 +926,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     b.Fa = g.Fa;
     b.na_c = g.ac.count;
     b.fp16 = fp16 ? 1 : 0;
+    b.nprod = nprod;
     b.idesc = 0;                     // set per variant by launch_gemm
     b.status = c.status;
     b.wait_limit = c.wait_limit;
@@ -920,7 +943,8 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         while (rmax < tm) rmax <<= 1;
         if (items[i].cell_count > 0) total_rows += (long)items[i].cell_count * tm * TC_BM;
     }
-    const TuneKey key(Mpad, Fpad, rmax, fp16 ? 1 : 0);
+    // precision bucket: 0 split BF16, 1 split FP16, 3 single-product FP16
+    const TuneKey key(Mpad, Fpad, rmax, (fp16 ? 1 : 0) + (nprod == 1 ? 2 : 0));
     int variant = tune_lookup(key);
     if (variant < 0 && !tune_enabled()) variant = 0;
     if (const char *fv = getenv("DSGRFT_TILE_VARIANT")) {   // explicit choice (tests, experiments)

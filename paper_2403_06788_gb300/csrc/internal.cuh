@@ -162,8 +162,8 @@ int ds_tc_r0_pad(int r0_count);
 constexpr int DS_TC_MAX_ITEMS = 64;    // CPIs per tensor-core launch (kernel-parameter table)
 int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
-                 const uint16_t *Blo, int Mpad, bool fp16, uint16_t *const Zhi[2], uint16_t *const Zlo[2],
-                 long z_rows_cap);
+                 const uint16_t *Blo, int Mpad, bool fp16, int nprod, uint16_t *const Zhi[2],
+                 uint16_t *const Zlo[2], long z_rows_cap);   // nprod: 3 (split) or 1 (FP16 hi only)
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);

@@ -22,30 +22,31 @@ from synth import Axis, DSGrid, Radar, Target
 R = Radar(M=300, N=1000, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
 ds = DSGrid(10, int(sys.argv[2]), Axis(-40.0, 18.75, 3), Axis(-2.5, 5.0, 2), 32, 8)
 s = synth.make_echo(R, [Target(400.0, -20.0, 1.0, complex(3.0, 0.0))], 9)
-Y = g.dsgrft(R, torch.from_numpy(s).cuda(), ds, precision="bf16x3", want_Y=True, want_P=False)
+Y = g.dsgrft(R, torch.from_numpy(s).cuda(), ds, precision=sys.argv[3], want_Y=True, want_P=False)
 assert g.grft_sync_status() == 0
 np.save(sys.argv[1], Y.cpu().numpy())
 """
 
 
-def _run(tmp, name, r0_count=900, **env):
+def _run(tmp, name, r0_count=900, precision="bf16x3", **env):
     out = os.path.join(tmp, name + ".npy")
     e = dict(os.environ)
     e.update({k: str(v) for k, v in env.items()})
-    r = subprocess.run([sys.executable, "-c", CODE % ROOT, out, str(r0_count)], env=e, capture_output=True,
+    r = subprocess.run([sys.executable, "-c", CODE % ROOT, out, str(r0_count), precision], env=e, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     import numpy as np
     return np.load(out)
 
 
-@pytest.mark.parametrize("r0_count", [900, 800])    # 8 bin tiles; 7 (the last pair unpaired)
-def test_tile_variants_are_bit_identical(cuda_lib, tmp_path, r0_count):
+@pytest.mark.parametrize("r0_count,precision", [(900, "bf16x3"), (800, "bf16x3"), (900, "fp16x1")])
+def test_tile_variants_are_bit_identical(cuda_lib, tmp_path, r0_count, precision):
+    # 8 bin tiles; 7 (the last pair unpaired); the single-product variants (twice the stages)
     import numpy as np
-    y0 = _run(str(tmp_path), "v0", r0_count, DSGRFT_TILE_VARIANT=0)
+    y0 = _run(str(tmp_path), "v0", r0_count, precision, DSGRFT_TILE_VARIANT=0)
     assert np.isfinite(y0).all() and np.abs(y0).max() > 0
     for v in range(1, 5):
-        yv = _run(str(tmp_path), "v%d" % v, r0_count, DSGRFT_TILE_VARIANT=v)
+        yv = _run(str(tmp_path), "v%d" % v, r0_count, precision, DSGRFT_TILE_VARIANT=v)
         assert np.array_equal(y0, yv), v
 
 

@@ -13,7 +13,7 @@ from tests.helpers import TOL_FP32, TOL_SPLIT, rel_peak_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": TOL_FP32, "bf16x3": TOL_SPLIT, "fp16x3": TOL_SPLIT}
+TOL = {"fp32": TOL_FP32, "bf16x3": TOL_SPLIT, "fp16x3": TOL_SPLIT, "fp16x1": TOL_SPLIT}
 
 
 def _small_case(M=100, N=700, r0b=17, r0c=300, Fv=16, Fa=16, nvc=3, nac=2, seed=3):
@@ -26,7 +26,7 @@ def _small_case(M=100, N=700, r0b=17, r0c=300, Fv=16, Fa=16, nvc=3, nac=2, seed=
     return R, ds, s
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16x3", "fp16x1"])
 def test_ds_fused_small_every_output(cuda_lib, precision):
     g = cuda_lib
     R, ds, s = _small_case()
@@ -37,9 +37,12 @@ def test_ds_fused_small_every_output(cuda_lib, precision):
     err = rel_peak_err(Y.cpu().numpy(), Yo)
     assert err <= TOL[precision], err
     assert rel_peak_err(P.cpu().numpy(), np.abs(Yo) ** 2) <= 2 * TOL[precision]
-    if precision != "fp32":
+    if precision in ("bf16x3", "fp16x3"):
         # the split path is far better than its 2e-3 bound; guard against silent regressions
         assert err <= 1e-4, err
+    if precision == "fp16x1":
+        # one FP16 rounding per operand: about 2^-12 per term, well inside the 2e-3 bound
+        assert err <= 5e-4, err
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
@@ -107,7 +110,7 @@ def test_ds_fine_grid_padding_and_single_cell(cuda_lib):
     g = cuda_lib
     R, ds, s = _small_case(M=33, Fv=5, Fa=3, nvc=1, nac=1, r0c=129)
     es = torch.from_numpy(s).cuda()
-    for prec in ("fp32", "bf16x3", "fp16x3"):
+    for prec in ("fp32", "bf16x3", "fp16x3", "fp16x1"):
         Y = g.dsgrft(R, es, ds, precision=prec, want_Y=True, want_P=False)
         assert rel_peak_err(Y.cpu().numpy(), oracle.dsgrft_full(R, s, ds)) <= TOL[prec]
 
@@ -131,10 +134,12 @@ def test_ds_full_ds_m512_sampled(cuda_lib):
     from oracle.wrap import ds_rows_of_canonical
     cell, fine = ds_rows_of_canonical(ds, vf, af)
     Yo = oracle.dsgrft_rows(R, s, ds, cell, fine)
-    for prec in ("bf16x3", "fp32"):
+    for prec in ("bf16x3", "fp32", "fp16x1"):
         Y = g.dsgrft(R, es, ds, precision=prec, want_Y=True, want_P=False)
         assert g.grft_sync_status() == 0
         Yg = Y[torch.as_tensor(vf, device="cuda"), torch.as_tensor(af, device="cuda")].cpu().numpy()
-        assert rel_peak_err(Yg, Yo) <= TOL[prec]
+        err = rel_peak_err(Yg, Yo)
+        print(prec, "max rel peak error on sampled rows:", err)
+        assert err <= TOL[prec]
         del Y
         torch.cuda.empty_cache()
