@@ -573,6 +573,8 @@ def main():
     ap.add_argument("--forms", action="store_true",
                     help="time the FFT-form fine stage and the frequency-domain coarse stage against the dense "
                          "and gather forms (one JSON line; --cells N: the first N cells)")
+    ap.add_argument("--other-precisions", type=int, default=1,
+                    help="1: also time the step in the other contraction mode (fp16x1 beside bf16x3)")
     ap.add_argument("--kt", action="store_true",
                     help="time the keystone branch (DS-KT-MFP map + detection) alone (one JSON line)")
     ap.add_argument("--kt-rows", type=int, default=0,
@@ -735,6 +737,44 @@ def main():
         del Y
         acc = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
 
+    # ---------------------------------------------------------------- the other contraction modes
+    # (same step, same workload): fp16x1 = one FP16 product per MAC, not the split form of the
+    # headline; its value, contraction time and sampled error are reported beside it
+    others = {}
+    if world == 1 and args.other_precisions:
+        for op in [p for p in ("fp16x1", "bf16x3") if p != args.precision][:1]:
+            def step_o():
+                g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, op, None, P)
+                g.detect_peaks(P, cfar, args.topk, axes=pg, dr_m=R.dr_m, out=det_out, n_out=n_out)
+            for _ in range(args.warmup):
+                step_o()
+            torch.cuda.synchronize()
+            k2 = max(3, args.steps // 2)
+            evo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k2)]
+            g.grft_timing(True)
+            for i in range(k2):
+                flush.fill_(i & 255)
+                evo[i][0].record(stream)
+                step_o()
+                evo[i][1].record(stream)
+            torch.cuda.synchronize()
+            nco, mco = g.grft_timing_get("contract")
+            g.grft_timing(False)
+            ms_o = sum(a.elapsed_time(b) for a, b in evo) / k2
+            err_o = None
+            if rank == 0 and not args.no_cpu:
+                Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device=dev)
+                g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, op, Y, None)
+                Yg = Y[torch.as_tensor(vf, device=dev), torch.as_tensor(af, device=dev)].cpu().numpy()
+                del Y
+                err_o = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
+            c_s = 1e-3 * mco / max(nco, 1)
+            alg_o = FLOP_PER_HYP_PULSE * units / max(nco / k2, 1)
+            peak_o = _peaks()[0].get("bf16_tflops", 1956.7)
+            others[op] = {"products_per_mac": 1 if op == "fp16x1" else 3, "value": units / (1e-3 * ms_o),
+                          "ms_per_step": ms_o, "contract_ms": 1e3 * c_s,
+                          "roofline_frac": alg_o / c_s / 1e12 / peak_o, "max_rel_peak_err": err_o, "steps": k2}
+
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -816,6 +856,7 @@ def main():
             "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units)},
         "kernels": kernel_rooflines,
         "max_rel_peak_err": acc,
+        "other_precisions": others or None,
         "detections": {"total": ndet, "top1_p": float(dets["p"][0]) if len(dets) else None},
         "status": st,
         "e2e": {"value": job_rate(units, world, e2e_s), "unit": UNIT,
