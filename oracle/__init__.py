@@ -15,12 +15,12 @@ Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 tests/test_oracle_pins.py and tests/test_oracle_kt_pins.py (closed forms, library routines, brute force, invariants);
 none is "parity unpinned".
 """
-from .fd import coarse_rm_fd, dsgrft_rows_fd
+from .fd import coarse_rm_fd, dsgrft_rows_fd, fine_scale
 from .kt import blind_speed, dskt_map, dskt_rows, fbar, keystone, keystone_columns, kt_coarse_rm, kt_fine_rows
 from .wrap import (bins_phases, coarse_rm, cfar_detect, dsgrft_rows, dsgrft_full, grft_plain_rows,
                    grft_plain_full, load, num_threads, refine, trajectory_grad)
 
 __all__ = ["blind_speed", "dskt_map", "dskt_rows", "fbar", "keystone", "keystone_columns", "kt_coarse_rm",
-           "kt_fine_rows", "bins_phases", "coarse_rm", "coarse_rm_fd", "cfar_detect", "dsgrft_rows", "dsgrft_rows_fd",
+           "kt_fine_rows", "fine_scale", "bins_phases", "coarse_rm", "coarse_rm_fd", "cfar_detect", "dsgrft_rows", "dsgrft_rows_fd",
            "dsgrft_full",
            "grft_plain_rows", "grft_plain_full", "load", "num_threads", "refine", "trajectory_grad"]

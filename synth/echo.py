@@ -27,10 +27,25 @@ def _carrier(R: np.ndarray, lam: float) -> np.ndarray:
     return np.exp(-2j * np.pi * frac)
 
 
+def _dirichlet_positive(x: np.ndarray, N: int) -> np.ndarray:
+    """(1/N) sum_{k=0}^{N-1} exp(j 2 pi k x / N): the range profile of a unit echo whose
+    spectrum covers the positive band k = 0..N-1 (the asinc envelope with its linear phase)."""
+    x = np.asarray(x, dtype=np.float64)
+    r = x - N * np.rint(x / N)                          # periodic in N
+    out = np.ones_like(r, dtype=np.complex128)
+    nz = np.abs(r) > 1e-12
+    rn = r[nz]
+    out[nz] = np.exp(1j * np.pi * (N - 1) * rn / N) * np.sin(np.pi * rn) / (N * np.sin(np.pi * rn / N))
+    return out
+
+
 def make_echo(radar: Radar, targets: Iterable[Target], seed: int, noise: bool = True,
               window: int = 64, envelope: str = "sinc") -> np.ndarray:
-    """Return s[M][N] complex64.  envelope='sinc' (default) or 'delta' (a unit sample
-    at the nearest bin, used by noiseless closed-form tests)."""
+    """Return s[M][N] complex64.  envelope='sinc' (default), 'delta' (a unit sample at the
+    nearest bin, used by noiseless closed-form tests) or 'asinc' (paper eq. received signal:
+    the range IFFT of the discrete positive band f_k = k f_s / N, k = 0..N-1, of the
+    frequency-domain echo exp(-j 4 pi (f_k + f_c) R / c) -- a periodic-sinc envelope with the
+    extra linear phase, over the whole range axis)."""
     M, N = radar.M, radar.N
     out = np.zeros((M, N), dtype=np.complex128)
     t = np.arange(M, dtype=np.float64) / radar.prf_hz
@@ -39,6 +54,10 @@ def make_echo(radar: Radar, targets: Iterable[Target], seed: int, noise: bool = 
         R = tg.r0_bins * radar.dr_m + tg.v * t + 0.5 * tg.a * t * t
         x = R / radar.dr_m
         ph = tg.amp * _carrier(R, lam)
+        if envelope == "asinc":
+            n = np.arange(N, dtype=np.float64)
+            out += ph[:, None] * _dirichlet_positive(n[None, :] - x[:, None], N)
+            continue
         if envelope == "delta":
             n = np.floor(x + 0.5).astype(np.int64)
             ok = (n >= 0) & (n < N)

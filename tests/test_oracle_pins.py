@@ -255,6 +255,71 @@ def test_fd_ds_rows_equal_td_rows_without_fractional_shift():
     np.testing.assert_allclose(Yfd, Ytd, rtol=0, atol=1e-10 * np.abs(Ytd).max())
 
 
+def test_positive_band_echo_spectrum_is_the_paper_echo():
+    """The asinc echo (eq. received signal) is the range IFFT of eq. Rx-OFDM-Fre1 over the
+    discrete band f_k = k f_s / N, k = 0..N-1: its FFT is A exp(-j 4 pi (f_k + f_c) R / c)."""
+    R = _fd_radar(4, 64)
+    tg = Target(17.3, 40.0, 3.0, complex(0.6, -0.8))
+    s = synth.make_echo(R, [tg], 0, noise=False, envelope="asinc").astype(np.complex128)
+    S = np.fft.fft(s, axis=1)
+    t = np.arange(R.M) / R.prf_hz
+    Rt = tg.r0_bins * R.dr_m + tg.v * t + 0.5 * tg.a * t * t
+    fs = R.c_mps / (2.0 * R.dr_m)
+    fk = np.arange(R.N) * fs / R.N
+    want = tg.amp * np.exp(-4j * np.pi * np.outer(Rt, fk + R.fc_hz) / R.c_mps)
+    np.testing.assert_allclose(S, want, rtol=0, atol=2e-5)     # complex64 echo
+
+
+@pytest.mark.parametrize("k0", [11, 50])
+def test_fd_coarse_stage_positive_band_shifts_by_unsigned_frequency(k0):
+    """Over the positive band the spectrum index k0 stands for k0 f_s / N even when
+    k0 >= N/2: a fractional advance delta gives the phase 2 pi k0 delta / N (and not
+    2 pi (k0 - N) delta / N as over the baseband reading)."""
+    R = _fd_radar(5, 64)
+    n = np.arange(R.N)
+    s = np.tile(np.exp(2j * np.pi * k0 * n / R.N), (R.M, 1)).astype(np.complex128)
+    ds = DSGrid(3, 50, Axis(-37.3, 1.0, 1), Axis(4.1, 1.0, 1), 2, 2)
+    Z = oracle.coarse_rm_fd(R, s, ds, 0, 1, band="positive")[0]
+    t = np.arange(R.M) / R.prf_hz
+    d = ds.vc.start * t + 0.5 * ds.ac.start * t * t
+    delta = d / R.dr_m
+    nn = ds.r0_begin + np.arange(ds.r0_count)
+    expect = np.exp(2j * np.pi * k0 * (nn[None, :] + delta[:, None]) / R.N) * \
+        np.exp(4j * np.pi * d / R.wavelength)[:, None]
+    np.testing.assert_allclose(Z, expect, rtol=0, atol=1e-11)
+    if k0 >= R.N // 2:                                         # the baseband reading differs
+        Zb = oracle.coarse_rm_fd(R, s, ds, 0, 1)[0]
+        assert np.max(np.abs(Zb - expect)) > 1e-3                # |exp(-j 2 pi delta) - 1|
+
+
+def test_fine_scale_restores_the_coherence_of_a_positive_band_coarse_stage():
+    """A noiseless asinc target at a fine-cell corner of a coarse cell (residual migration
+    a third of a bin): after the positive-band coarse stage, fine offsets scaled by
+    1 + B_r / (2 f_c) sum it more coherently than unscaled ones, and those more than the
+    factor 1 - B_r / (2 f_c) printed in Prop. 1; at the cell centre the three agree."""
+    sc = synth.ds_m512()
+    R, ds = sc.radar, sc.ds
+    i, l = 20, 3
+    vc = ds.vc.start + i * ds.vc.step
+    ac = ds.ac.start + l * ds.ac.step
+    B = R.c_mps / (2.0 * R.dr_m)
+    assert abs(oracle.fine_scale(R, "positive") - (1.0 + B / (2.0 * R.fc_hz))) < 1e-15
+    assert oracle.fine_scale(R, "baseband") == 1.0
+    cell = i * ds.ac.count + l
+    for (k, q), corner in (((0, 0), True), ((32, 8), False)):
+        dv = (k - ds.Fv / 2) * ds.vc.step / ds.Fv
+        da = (q - ds.Fa / 2) * ds.ac.step / ds.Fa
+        tg = Target(2000.0, vc + dv, ac + da, complex(1.0, 0.0))
+        s = synth.make_echo(R, [tg], 0, noise=False, envelope="asinc")
+        f = k * ds.Fa + q
+        mag = [abs(oracle.dsgrft_rows_fd(R, s, ds, [cell], [f], band="positive", kap=kap)[0][2000]) / R.M
+               for kap in (oracle.fine_scale(R, "positive"), 1.0, 1.0 - B / (2.0 * R.fc_hz))]
+        if corner:
+            assert mag[0] > 0.93 and mag[0] > mag[1] + 0.03 and mag[1] > mag[2] + 0.05, mag
+        else:
+            assert min(mag) > 0.9999, mag
+
+
 # ---------------------------------------------------------------- P6: DS == GRFT where bins agree
 def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
     """Prop. 1/2: with the same bins the two sums have identical terms up to rounding."""
