@@ -209,6 +209,27 @@ int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_d
 int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
                         int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream);
 
+/* The range frequencies the spectrum index k stands for: baseband k in [-N/2, N/2), or the
+ * paper's discrete band f_k = k f_s / N, k = 0..N-1, of eq. Rx-OFDM-Fre1 (the echo of
+ * eq. received signal, asinc envelope with its linear phase). */
+typedef enum { GRFT_BAND_BASEBAND = 0, GRFT_BAND_POSITIVE = 1 } grft_band;
+
+/* dsgrft_coarse_rm_fd with the band chosen (GRFT_BAND_BASEBAND is dsgrft_coarse_rm_fd):
+ * over the positive band k runs over [0, N) in the ramp exp(j 2 pi k delta / N). */
+int dsgrft_coarse_rm_fd_ex(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                           int32_t cell_begin, int32_t cell_count, grft_band band, grft_c32 *Z, void *stream);
+
+/* Fine stage on Z of dsgrft_coarse_rm_fd_ex with the same band (Prop. 1): dsgrft_fine_dfm with
+ * Z given and the fine offsets of H_DFM scaled by 1 + B_r / (2 f_c), B_r = c / (2 dr), for the
+ * positive band (1 for baseband): after a positive-band coarse stage the residual range term
+ * c_f t^p of a cell leaves the phase -(4 pi / lambda) (1 + B_r / (2 f_c)) c_f t^p at the peak
+ * bin.  (Prop. 1 prints kappa = 1 - B_r / (2 f_c), the factor of the keystone branch, Cor. 1,
+ * whose residual range term has the opposite sign.)  Output layout, hypotheses' labels and
+ * precisions as dsgrft_fine_dfm. */
+int dsgrft_fine_dfm_fd(const grft_radar *radar, const grft_c32 *Z, const grft_dsgrid *grid, int32_t cell_begin,
+                       int32_t cell_count, grft_band band, grft_precision precision, grft_c32 *Y, float *P,
+                       void *stream);
+
 /* Fine Doppler-migration correction, the GFT of Def. 1 / Alg. 2 as a dense contraction
  * against the dechirp matrix D[m][f] = exp(j 4 pi (dv_k t_m + da_q t_m^2 / 2) / lambda):
  *   Y(n0; c, f) = exp(j 4 pi n0 dr / lambda) * sum_m Zc[m][n0] D[m][f]          (Alg. 3)

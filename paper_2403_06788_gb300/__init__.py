@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X1, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_LINEAR,
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
-__all__ = ["dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
+__all__ = ["dsgrft_coarse_rm_fd_ex", "dsgrft_fine_dfm_fd", "dsgrft_fd", "dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
            "load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
            "grft_shutdown",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
@@ -165,6 +165,41 @@ def dsgrft_coarse_rm_fd(radar, echo, grid, cell_begin, cell_count, Z, stream=Non
     check(load().dsgrft_coarse_rm_fd(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
                                      int(cell_begin), int(cell_count), _ptr(Z, torch.complex64, "Z"),
                                      _stream(stream)), "dsgrft_coarse_rm_fd")
+
+
+def dsgrft_coarse_rm_fd_ex(radar, echo, grid, cell_begin, cell_count, band, Z, stream=None):
+    """Frequency-domain coarse stage over `band` ('baseband' or 'positive', the paper's
+    discrete band k = 0..N-1) into Z [cell_count][M][r0_count]."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dsgrft_coarse_rm_fd_ex(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
+                                        int(cell_begin), int(cell_count), _abi.BANDS[band],
+                                        _ptr(Z, torch.complex64, "Z"), _stream(stream)), "dsgrft_coarse_rm_fd_ex")
+
+
+def dsgrft_fine_dfm_fd(radar, Z, grid, cell_begin, cell_count, band, precision, Y=None, P=None, stream=None):
+    """Fine stage on Z of dsgrft_coarse_rm_fd_ex with the same band (fine offsets scaled for
+    the positive band, Prop. 1)."""
+    R, G = _radar(radar), _dsgrid(grid)
+    check(load().dsgrft_fine_dfm_fd(C.byref(R), _ptr(Z, torch.complex64, "Z"), C.byref(G), int(cell_begin),
+                                    int(cell_count), _abi.BANDS[band], _precision(precision),
+                                    _ptr(Y, torch.complex64, "Y"), _ptr(P, torch.float32, "P"), _stream(stream)),
+          "dsgrft_fine_dfm_fd")
+
+
+def dsgrft_fd(radar, echo, grid, band="baseband", precision="bf16x3", want_Y=False, want_P=True):
+    """DS-GRFT with the frequency-domain coarse stage (the paper's form, Alg. 1 + Alg. 3) over
+    the whole grid; returns P [v_full][a_full][r0] (and Y)."""
+    nv, na = int(grid.vc.count) * int(grid.Fv), int(grid.ac.count) * int(grid.Fa)
+    shape = (nv, na, int(grid.r0_count))
+    P = torch.empty(shape, dtype=torch.float32, device=echo.device) if want_P else None
+    Y = torch.empty(shape, dtype=torch.complex64, device=echo.device) if want_Y else None
+    ncell = int(grid.vc.count) * int(grid.ac.count)
+    Z = torch.empty((ncell, int(echo.shape[0]), int(grid.r0_count)), dtype=torch.complex64, device=echo.device)
+    dsgrft_coarse_rm_fd_ex(radar, echo, grid, 0, ncell, band, Z)
+    dsgrft_fine_dfm_fd(radar, Z, grid, 0, ncell, band, precision, Y, P)
+    if want_Y and want_P:
+        return P, Y
+    return Y if want_Y else P
 
 
 def dsgrft_fine_dfm_fft(radar, echo, grid, cell_begin, cell_count, Y=None, P=None, stream=None):

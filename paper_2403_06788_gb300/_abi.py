@@ -15,6 +15,7 @@ GRFT_OK, GRFT_EINVAL, GRFT_ENOMEM, GRFT_ECUDA, GRFT_ETIMEOUT, GRFT_EUNSUPPORTED,
     0, -1, -2, -3, -4, -5, -6)
 GRFT_FP32, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X1 = 0, 1, 2, 3
 GRFT_GATHER_NEAREST, GRFT_GATHER_LINEAR = 0, 1
+BANDS = {"baseband": 0, "positive": 1}
 PRECISIONS = {"fp32": GRFT_FP32, "bf16x3": GRFT_BF16X3, "fp16x3": GRFT_FP16X3, "fp16x1": GRFT_FP16X1}
 KERNELS = {"tables": 0, "plain": 1, "coarse_rm": 2, "split": 3, "contract": 4, "contract_fp32": 5,
            "cfar": 6, "topk": 7, "adjoint": 8, "contract_fft": 9, "keystone": 10}
@@ -77,6 +78,10 @@ SIGNATURES = {
                                   C.c_int32, C.c_int, _P, _P, _P]),
     "dsgrft_coarse_rm_fd": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                       C.c_int32, _P, _P]),
+    "dsgrft_coarse_rm_fd_ex": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32,
+                                         C.c_int, _P, _P]),
+    "dsgrft_fine_dfm_fd": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32,
+                                     C.c_int, C.c_int, _P, _P, _P]),
     "dsgrft_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                       C.c_int32, _P, _P, _P]),
     "dskt_keystone": (C.c_int, [C.POINTER(grft_radar), _P, _P, _P]),

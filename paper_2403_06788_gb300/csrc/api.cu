@@ -459,10 +459,11 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, nprod, Zhi, Zlo, z_rows);
 }
 
-int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
-                        int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream) {
+int dsgrft_coarse_rm_fd_ex(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                           int32_t cell_begin, int32_t cell_count, grft_band band, grft_c32 *Z, void *stream) {
     if (!radar_ok(radar) || !echo || !Z || !dsgrid_ok(grid, radar) || cell_begin < 0 || cell_count < 0 ||
-        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count)
+        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count ||
+        (band != GRFT_BAND_BASEBAND && band != GRFT_BAND_POSITIVE))
         return GRFT_EINVAL;
     const int N = radar->N;
     if (N < 2 || N > 8192 || (N & (N - 1)) != 0) return GRFT_EUNSUPPORTED;
@@ -481,7 +482,26 @@ int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grf
     float2 *S = (float2 *)(ws + rho_bytes + w_bytes);
     if ((e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
     if ((e = launch_range_fft(c, R, (const float2 *)echo, S))) return e;
-    return launch_rm_fd(c, R, *grid, cell_begin, cell_count, S, w, (float2 *)Z);
+    return launch_rm_fd(c, R, *grid, cell_begin, cell_count, S, w, (float2 *)Z, band == GRFT_BAND_POSITIVE);
+}
+
+int dsgrft_coarse_rm_fd(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                        int32_t cell_begin, int32_t cell_count, grft_c32 *Z, void *stream) {
+    return dsgrft_coarse_rm_fd_ex(radar, echo, grid, cell_begin, cell_count, GRFT_BAND_BASEBAND, Z, stream);
+}
+
+int dsgrft_fine_dfm_fd(const grft_radar *radar, const grft_c32 *Z, const grft_dsgrid *grid, int32_t cell_begin,
+                       int32_t cell_count, grft_band band, grft_precision precision, grft_c32 *Y, float *P,
+                       void *stream) {
+    if (!radar_ok(radar) || !Z || !grid || (band != GRFT_BAND_BASEBAND && band != GRFT_BAND_POSITIVE))
+        return GRFT_EINVAL;
+    grft_dsgrid g = *grid;
+    if (band == GRFT_BAND_POSITIVE) {        // fine offsets scaled by 1 + B_r / (2 f_c), B_r = c / (2 dr)
+        const double s = 1.0 + radar->c_mps / (2.0 * radar->dr_m) / (2.0 * radar->fc_hz);
+        g.vc.step *= s;
+        g.ac.step *= s;
+    }
+    return dsgrft_fine_dfm(radar, Z, nullptr, &g, cell_begin, cell_count, precision, Y, P, stream);
 }
 
 int dsgrft_fine_dfm_fft(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,

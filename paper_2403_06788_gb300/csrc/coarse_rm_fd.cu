@@ -2,8 +2,9 @@
 // eq. pre-DFM (Alg. 1), for N a power of two:
 //   S[m][k]    = sum_n s[m][n] exp(-j 2 pi k n / N)                          (range spectrum)
 //   Z[c][m][j] = (1/N) sum_k S[m][k] exp(+j 2 pi k (n + delta) / N) * w_c(m),   n = r0_begin + j
-// with delta = d_c(t_m) / dr (FP64), k in [-N/2, N/2): the band-limited circular advance of
-// each range profile by delta bins.  Two kernels, both one persistent CTA per row at a time
+// with delta = d_c(t_m) / dr (FP64), k in [-N/2, N/2) (baseband) or in [0, N) (the paper's
+// positive band f_k = k f_s / N): the band-limited circular advance of each range profile
+// by delta bins.  Two kernels, both one persistent CTA per row at a time
 // with the N samples in shared memory:
 //   k_range_fft  forward radix-2 decimation in frequency of each pulse row; the spectrum is
 //                stored in bit-reversed order (nothing is permuted);
@@ -37,7 +38,7 @@ __global__ __launch_bounds__(FD_THREADS) void k_range_fft(const float2 *__restri
 }
 
 __global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
-                                                    int logN, const float2 *__restrict__ S,
+                                                    int logN, int positive, const float2 *__restrict__ S,
                                                     const float2 *__restrict__ w_c, float2 *__restrict__ Z) {
     extern __shared__ float2 fd_smem[];
     const int N = R.N;
@@ -74,13 +75,13 @@ __global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, i
             }
         }
         float sn0, cs0;
-        sincospif(-f, &sn0, &cs0);              // exp(-j pi f): k = u - N/2
+        sincospif(positive ? 0.0f : -f, &sn0, &cs0);   // baseband: exp(-j pi f), k = u - N/2
         const float2 c0 = make_float2(cs0, sn0);
         __syncthreads();
         const float2 *Sm = S + (long)m * N;
         for (int p = threadIdx.x; p < N; p += FD_THREADS) {
             const int k = (int)brev_bits((unsigned)p, logN);        // natural frequency of slot p
-            const int u = k < N / 2 ? k + N / 2 : k - N / 2;        // signed k + N/2
+            const int u = positive ? k : (k < N / 2 ? k + N / 2 : k - N / 2);   // positive: k; else signed k + N/2
             const float2 ramp = cmul(c0, cmul(s_hi[u >> 6], s_lo[u & 63]));
             x[p] = cmul(__ldg(Sm + p), ramp);
         }
@@ -121,7 +122,7 @@ int launch_range_fft(const Ctx &c, const RadarD &R, const float2 *echo, float2 *
 }
 
 int launch_rm_fd(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_begin, int cell_count,
-                 const float2 *S, const float2 *w, float2 *Z) {
+                 const float2 *S, const float2 *w, float2 *Z, bool positive) {
     int logN = 0;
     while ((1 << logN) < R.N) ++logN;
     const long rows = (long)cell_count * R.M;
@@ -129,7 +130,8 @@ int launch_rm_fd(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_b
     const long cap = 2L * c.num_sms * 4;        // persistent: a few CTAs per SM
     const int grid = (int)(rows < cap ? rows : cap);
     KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
-    k_rm_fd<<<grid, FD_THREADS, fd_smem_bytes(R.N), c.stream>>>(R, g, cell_begin, cell_count, logN, S, w, Z);
+    k_rm_fd<<<grid, FD_THREADS, fd_smem_bytes(R.N), c.stream>>>(R, g, cell_begin, cell_count, logN,
+                                                                 positive ? 1 : 0, S, w, Z);
     return check_launch();
 }
 

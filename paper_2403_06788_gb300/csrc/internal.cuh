@@ -120,7 +120,7 @@ struct DsOut {           // output placement of a DS call (v-slab of the canonic
 // order), then Z[cell][m][j] for the cells.  N a power of two <= 8192.
 int launch_range_fft(const Ctx &, const RadarD &, const float2 *echo, float2 *S);
 int launch_rm_fd(const Ctx &, const RadarD &, const grft_dsgrid &, int cell_begin, int cell_count,
-                 const float2 *S, const float2 *w, float2 *Z);
+                 const float2 *S, const float2 *w, float2 *Z, bool positive);   // positive: k in [0, N)
 
 // FFT form of the fine stage (fine_dfm_fft.cu): chirp[Fa][L], then the transform kernel.
 int launch_gft_chirp(const Ctx &, const RadarD &, const grft_dsgrid &, int L, float2 *chirp);
