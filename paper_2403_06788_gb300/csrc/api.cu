@@ -210,6 +210,27 @@ bool encode_tma_2d(CUtensorMap *map, CUtensorMapDataType dtype, void *base, uint
     return r == CUDA_SUCCESS;
 }
 
+bool encode_tma_3d(CUtensorMap *map, CUtensorMapDataType dtype, void *base, const uint64_t dims[3],
+                   const uint64_t strides_bytes[2], const uint32_t box[3], CUtensorMapSwizzle swizzle) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !ptr)
+            return false;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+    cuuint64_t st[2] = {strides_bytes[0], strides_bytes[1]};
+    cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, dtype, 3, base, d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 namespace {
 
 // Waits on an mbarrier phase that nothing completes, bounded by `limit` SM cycles: the

@@ -9,12 +9,15 @@
 // the threshold test compare themselves with their 26 neighbours and are appended to a
 // candidate list with a warp-aggregated atomic (one atomicAdd per warp via __ballot_sync).
 // HBM-bound: P is read once.
+// k_cfar_tma (rows of a multiple of 32 bins) / k_cfar_pipe / k_cfar_warp: the default
+// 2-guard / 16-train test, one warp per 1024-bin chunk (below).
 // k_topk: one CTA.  Up to 8192 candidates are sorted in shared memory (bitonic, by power
 // descending, index ascending); beyond that a 4-pass radix select over the power bits
 // finds the K-th largest value first and only the survivors are sorted.
 #include <cstdint>
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace grft {
 
@@ -437,6 +440,112 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_pipe(const float *__rest
     cp_async_wait<0>();
 }
 
+// Rows of a multiple of 32 bins: the same pipeline with each chunk moved by one tensor-map
+// copy.  The chunk's 1024 bins, viewed as 32 lines of 32 floats (a 3-D map {32, nr0/32,
+// rows}), land with the 128-byte swizzle, which is exactly the cp_pos layout above (16-byte
+// unit c of line l at c ^ (l & 7)); the 20 bins on either side come from a 2-D map {nr0,
+// rows} whose boxes past the row's ends are zero-filled by the copy engine.  Lane 0 issues
+// the three copies of a chunk on the stage's mbarrier; every wait is bounded (a wait that
+// runs out latches GRFT_ETIMEOUT, and the warp waits, again bounded, for the copies it
+// still has in flight before it leaves).
+constexpr size_t CT_CHUNK_BYTES = CW_CHUNK * sizeof(float);                      // 4096
+constexpr size_t CT_HALO_BYTES = 2 * CP_HALO * sizeof(float);                     // 160 copied per chunk
+constexpr size_t CT_HALO_SLOT = 128;                                              // a copy's destination: 128-byte aligned
+constexpr size_t CT_SMEM = 1024 + (size_t)(CW_THREADS / 32) * CP_STAGES * (CT_CHUNK_BYTES + 2 * CT_HALO_SLOT);
+
+template <int G, int T>
+__global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_tma(const __grid_constant__ CUtensorMap mapc,
+                                                          const __grid_constant__ CUtensorMap maph, CfarParams cp,
+                                                          int nch, int items, int *__restrict__ count,
+                                                          float *__restrict__ cand_p, int64_t *__restrict__ cand_i,
+                                                          int *status, uint64_t limit, const float *__restrict__ P) {
+    constexpr int H = G + T;
+    constexpr int WARPS = CW_THREADS / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(H <= CP_HALO && CP_HALO % 4 == 0 && CP_HALO <= 4 * 5, "halo copy");
+    extern __shared__ unsigned char ct_raw[];
+    __shared__ alignas(8) uint64_t bars[WARPS][CP_STAGES];
+    unsigned char *base = (unsigned char *)(((uintptr_t)ct_raw + 1023) & ~(uintptr_t)1023);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *chunks = reinterpret_cast<float *>(base) + (size_t)warp * CP_STAGES * CW_CHUNK;
+    // per (warp, stage): the left halo at a 128-byte slot, the right one at the next
+    unsigned char *halos = base + (size_t)WARPS * CP_STAGES * CT_CHUNK_BYTES +
+                           (size_t)warp * CP_STAGES * 2 * CT_HALO_SLOT;
+    uint64_t *bar = bars[warp];
+    if (lane == 0) {
+        for (int st = 0; st < CP_STAGES; ++st) mbar_init(&bar[st], 1);
+        fence_mbarrier_init();
+    }
+    __syncwarp();
+    const int gw = blockIdx.x * WARPS + warp;
+    const int W = gridDim.x * WARPS;
+
+    auto prefetch = [&](int i, int stage) {
+        if (lane == 0 && i < items) {
+            const unsigned row = (unsigned)i / (unsigned)nch;
+            const int c0 = (int)((unsigned)i - row * (unsigned)nch) * CW_CHUNK;
+            mbar_arrive_expect_tx(&bar[stage], (uint32_t)(CT_CHUNK_BYTES + CT_HALO_BYTES));
+            tma_load_3d(chunks + stage * CW_CHUNK, &mapc, 0, c0 / 32, (int)row, &bar[stage]);
+            unsigned char *hs = halos + stage * 2 * CT_HALO_SLOT;
+            tma_load_2d(hs, &maph, c0 - CP_HALO, (int)row, &bar[stage]);
+            tma_load_2d(hs + CT_HALO_SLOT, &maph, c0 + CW_CHUNK, (int)row, &bar[stage]);
+        }
+    };
+
+#pragma unroll
+    for (int t = 0; t < CP_STAGES - 1; ++t) prefetch(gw + t * W, t);
+    int t = 0;
+    bool ok = true;
+    for (;; ++t) {
+        const int i = gw + t * W;               // items + W < 2^31 (host check)
+        if (i >= items) break;                  // warp-uniform
+        const int stage = t % CP_STAGES;
+        const uint32_t parity = (uint32_t)(t / CP_STAGES) & 1u;
+        int good = 1;
+        if (lane == 0) good = mbar_wait(&bar[stage], parity, limit) ? 1 : 0;
+        good = __shfl_sync(FULL, good, 0);
+        if (!good) {
+            if (lane == 0) latch_error(status, GRFT_ETIMEOUT);
+            ok = false;
+            break;
+        }
+        mbar_try_wait(&bar[stage], parity);     // completed: every lane acquires the copied data
+        const float *st = chunks + stage * CW_CHUNK;
+        const float *hsl = reinterpret_cast<const float *>(halos + stage * 2 * CT_HALO_SLOT);
+        const float *hsr = reinterpret_cast<const float *>(halos + stage * 2 * CT_HALO_SLOT + CT_HALO_SLOT);
+        float x[CW_LANE];
+#pragma unroll
+        for (int c = 0; c < CW_LANE / 4; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(st + cp_pos(lane, c));
+            x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+        }
+        float lv[CP_HALO], rv[CP_HALO];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float4 a = *reinterpret_cast<const float4 *>(lane == 0 ? hsl + 4 * c : st + cp_pos(lane - 1, 3 + c));
+            const float4 b = *reinterpret_cast<const float4 *>(lane == 31 ? hsr + 4 * c : st + cp_pos(lane + 1, c));
+            lv[4 * c] = a.x; lv[4 * c + 1] = a.y; lv[4 * c + 2] = a.z; lv[4 * c + 3] = a.w;
+            rv[4 * c] = b.x; rv[4 * c + 1] = b.y; rv[4 * c + 2] = b.z; rv[4 * c + 3] = b.w;
+        }
+        float hl[H], hr[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            hl[k] = lv[CP_HALO - H + k];
+            hr[k] = rv[k];
+        }
+        __syncwarp();                           // all reads of this stage done before it is refilled
+        prefetch(gw + (t + CP_STAGES - 1) * W, (t + CP_STAGES - 1) % CP_STAGES);
+        const unsigned row = (unsigned)i / (unsigned)nch;
+        cfar_chunk<G, T>(x, hl, hr, P, cp, (long)row, (int)((unsigned)i - row * (unsigned)nch) * CW_CHUNK,
+                         count, cand_p, cand_i, status);
+    }
+    if (!ok && lane == 0) {                     // copies still in flight: items t .. t + STAGES - 2
+        for (int u = t; u < t + CP_STAGES - 1; ++u)
+            if (gw + u * W < items) mbar_wait(&bar[u % CP_STAGES], (uint32_t)(u / CP_STAGES) & 1u, limit);
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ bool before(float pa, int64_t ia, float pb, int64_t ib) {
     return pa > pb || (pa == pb && ia < ib);
 }
@@ -596,16 +705,38 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
             const long warps = rows * nch;
             const long blocks = (warps + CW_THREADS / 32 - 1) / (CW_THREADS / 32);
             if (blocks > 0x7fffffffL) return GRFT_EINVAL;
-            static bool pipe_attr[64] = {false};
+            static bool pipe_attr[64] = {false}, tma_attr[64] = {false};
             const bool aligned = (nr0 % 4) == 0 && (((uintptr_t)P) & 15) == 0 && c.device < 64 &&
                                  warps + 2L * c.num_sms * (CW_THREADS / 32) * CP_STAGES < 0x7fffffffL;
+            CUtensorMap mapc, maph;
+            bool use_tma = aligned && (nr0 % 32) == 0;
+            if (use_tma) {
+                const uint64_t dims[3] = {32, (uint64_t)nr0 / 32, (uint64_t)rows};
+                const uint64_t strides[2] = {128, (uint64_t)nr0 * sizeof(float)};
+                const uint32_t box[3] = {32, 32, 1};
+                use_tma = encode_tma_3d(&mapc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (void *)P, dims, strides, box,
+                                        CU_TENSOR_MAP_SWIZZLE_128B) &&
+                          encode_tma_2d(&maph, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (void *)P, (uint64_t)nr0,
+                                        (uint64_t)rows, (uint64_t)nr0 * sizeof(float), CP_HALO, 1,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE);
+            }
+            if (use_tma && !tma_attr[c.device]) {
+                if (cudaFuncSetAttribute(k_cfar_tma<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CT_SMEM) != cudaSuccess)
+                    return GRFT_ECUDA;
+                tma_attr[c.device] = true;
+            }
             if (aligned && !pipe_attr[c.device]) {
                 if (cudaFuncSetAttribute(k_cfar_pipe<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)CP_SMEM) != cudaSuccess)
                     return GRFT_ECUDA;
                 pipe_attr[c.device] = true;
             }
-            if (aligned) {
+            if (use_tma) {
+                const long pblocks = blocks < 2L * c.num_sms ? blocks : 2L * c.num_sms;
+                k_cfar_tma<2, 16><<<(unsigned)pblocks, CW_THREADS, CT_SMEM, c.stream>>>(
+                    mapc, maph, cp, nch, (int)warps, count, cand_p, cand_i, c.status, c.wait_limit, P);
+            } else if (aligned) {
                 const long pblocks = blocks < 2L * c.num_sms ? blocks : 2L * c.num_sms;
                 k_cfar_pipe<2, 16><<<(unsigned)pblocks, CW_THREADS, CP_SMEM, c.stream>>>(P, cp, nch, (int)warps,
                                                                                       count, cand_p, cand_i,

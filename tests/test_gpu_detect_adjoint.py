@@ -31,10 +31,12 @@ def _ambiguous(P, cfar, idx_set_diff):
     return all(out)
 
 
-@pytest.mark.parametrize("nr0", [4096, 3001, 2052, 1043, 50])
+@pytest.mark.parametrize("nr0", [4096, 2080, 96, 32, 3001, 2052, 1043, 50])
 def test_cfar_topk_matches_oracle_on_same_power(cuda_lib, nr0):
-    """Row lengths: whole 1024-bin warp chunks, ragged and unaligned rows, a second chunk
-    holding a few bins, a row shorter than the training window.  Targets also sit on
+    """Row lengths: whole 1024-bin warp chunks, multiples of 32 with a partial last chunk or
+    shorter than one chunk (the tensor-map path, zero-filled past the row), ragged and
+    unaligned rows, a second chunk holding a few bins, a row shorter than the training
+    window.  Targets also sit on
     lane and chunk boundaries, and two equal adjacent peaks test the index tie-break."""
     g = cuda_lib
     rng = np.random.default_rng(nr0)
