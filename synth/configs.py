@@ -99,11 +99,39 @@ class DSGrid:
 
 
 @dataclass(frozen=True)
+class DSGrid3:
+    """Dual-scale grid of the P = 3 motion model r = r0 + v t + a t^2/2 + b t^3/6: coarse
+    centres vc x ac x bc, fine offsets (k - Fv/2) vc.step/Fv, (q - Fa/2) ac.step/Fa,
+    (u - Fb/2) bc.step/Fb.  Cell c = (i na_c + l) nb_c + w, fine f = (k Fa + q) Fb + u."""
+    r0_begin: int
+    r0_count: int
+    vc: Axis
+    ac: Axis
+    bc: Axis
+    Fv: int
+    Fa: int
+    Fb: int
+
+    @property
+    def n_cells(self) -> int:
+        return self.vc.count * self.ac.count * self.bc.count
+
+    @property
+    def n_fine(self) -> int:
+        return self.Fv * self.Fa * self.Fb
+
+    @property
+    def n_hyp(self) -> int:
+        return self.r0_count * self.n_cells * self.n_fine
+
+
+@dataclass(frozen=True)
 class Target:
     r0_bins: float    # range at t = 0, in bins (may be fractional)
     v: float          # m/s
     a: float          # m/s^2
     amp: complex      # complex amplitude after pulse compression
+    b: float = 0.0    # m/s^3, acceleration rate (P = 3; the range gains b t^3 / 6)
 
 
 @dataclass(frozen=True)
@@ -124,6 +152,7 @@ class Scenario:
     plain: PlainGrid | None = None
     ds: DSGrid | None = None
     snr_db: List[float] = field(default_factory=list)
+    ds3: "DSGrid3 | None" = None
 
 
 def _snr_amp(rng: np.random.Generator, snr_db: float) -> complex:
@@ -239,6 +268,27 @@ def ds_adjoint_m1024(run: int = 0) -> Scenario:
                          float(pg.a.start + (k + oa) * pg.a.step), _snr_amp(rng, snr)))
         snrs.append(snr)
     return Scenario("ds_adjoint_m1024", radar, tg, seed, plain=pg, ds=ds, snr_db=snrs)
+
+
+def ds3_m512(run: int = 0) -> Scenario:
+    """P = 3 (acceleration rate) on the ds_m512 radar: 4 targets with v in [-70, 70] m/s,
+    a in [-9.5, 9.5] m/s^2, b in [-28, 28] m/s^3, SNR in [-10, 0] dB.  Coarse 8 v x 8 a x 4 b
+    cells (centres over [-75, 75] m/s, [-10, 10] m/s^2, [-32, 32] m/s^3), fine 64 dv x 8 da
+    x 4 db (0.293 m/s, 0.3125 m/s^2, 4 m/s^3): 4096 r0 x 256 cells x 2048 fine = 2.1e9
+    hypotheses; residual range migration of a cell 5.2 m <= dr / 2."""
+    radar = Radar(M=512, N=4096, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    seed = 1000 * 7 + run
+    rng = np.random.Generator(np.random.PCG64(seed))
+    margin = walk_margin_bins(radar, 80.0, 10.0) + 2
+    tg, snrs = [], []
+    for _ in range(4):
+        snr = float(rng.uniform(-10.0, 0.0))
+        tg.append(Target(float(rng.uniform(margin, radar.N - margin)), float(rng.uniform(-70.0, 70.0)),
+                         float(rng.uniform(-9.5, 9.5)), _snr_amp(rng, snr), float(rng.uniform(-28.0, 28.0))))
+        snrs.append(snr)
+    ds3 = DSGrid3(0, radar.N, Axis(-75.0 + 9.375, 18.75, 8), Axis(-10.0 + 1.25, 2.5, 8), Axis(-24.0, 16.0, 4),
+                  64, 8, 4)
+    return Scenario("ds3_m512", radar, tg, seed, snr_db=snrs, ds3=ds3)
 
 
 def kt_grid(radar: Radar, q_min: int, q_count: int, ac: Axis, Fa: int, L: int | None = None,

@@ -1,6 +1,7 @@
 """Seeded synthetic pulse-compressed echoes (paper Remark 1, eq. received signal_usual).
 
-For each target l with range history R_l(t) = r0_l dr + v_l t + a_l t^2 / 2:
+For each target l with range history R_l(t) = r0_l dr + v_l t + a_l t^2 / 2 (+ b_l t^3 / 6
+for an acceleration rate, P = 3):
 
     s[m][n] = sum_l A_l sinc(n - R_l(t_m)/dr) exp(-j 4 pi R_l(t_m) / lambda) + w[m][n]
 
@@ -51,7 +52,7 @@ def make_echo(radar: Radar, targets: Iterable[Target], seed: int, noise: bool = 
     t = np.arange(M, dtype=np.float64) / radar.prf_hz
     lam = radar.wavelength
     for tg in targets:
-        R = tg.r0_bins * radar.dr_m + tg.v * t + 0.5 * tg.a * t * t
+        R = tg.r0_bins * radar.dr_m + tg.v * t + 0.5 * tg.a * t * t + (tg.b / 6.0) * t * t * t
         x = R / radar.dr_m
         ph = tg.amp * _carrier(R, lam)
         if envelope == "asinc":
