@@ -335,6 +335,7 @@ def run_suite(args):
 
     out.update(measure_forms(0, 3, 1))
     out["keystone_m512"] = measure_kt(rows=0, steps=3, warmup=1)
+    out["p3_m512"] = measure_p3(3, 1)
     print(json.dumps({"suite": out}))
     return 0
 
@@ -467,6 +468,35 @@ def measure_kt(rows=0, steps=3, warmup=3):
     return res
 
 
+def measure_p3(steps=3, warmup=1, precision="bf16x3"):
+    """DS-GRFT with the acceleration rate (P = 3) on the ds3_m512 workload (M=512 x N=4096,
+    coarse 8 v x 8 a x 4 b, fine 64 x 8 x 4: 2.1e9 hypotheses), P written (8.6 GB, larger
+    than L2): CUDA events around `steps` calls after `warmup`."""
+    import torch
+    import paper_2403_06788_gb300 as g
+    import synth
+    dev = torch.device("cuda", 0)
+    g.load()
+    stream = torch.cuda.current_stream()
+    sc = synth.ds3_m512()
+    R, g3 = sc.radar, sc.ds3
+    echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
+    shape = (g3.vc.count * g3.Fv, g3.ac.count * g3.Fa, g3.bc.count * g3.Fb, g3.r0_count)
+    P = torch.empty(shape, device=dev)
+    ncell = g3.vc.count * g3.ac.count * g3.bc.count
+    run = lambda: g.dsgrft3_fine_dfm(R, echo, g3, 0, ncell, precision, None, P)
+    for _ in range(max(warmup, 1)):
+        run()
+    ms = _timed(run, steps, stream)
+    units = g3.n_hyp * R.M
+    res = {"workload": "DS-GRFT P=3 (acceleration rate), M=512 x N=4096, coarse 8 v x 8 a x 4 b, fine 64 x 8 x 4, "
+                       "4096 r0 = 2.1e9 hypotheses, P written", "precision": precision, "unit": UNIT,
+           "ms_per_call": ms, "value": units / (1e-3 * ms), "status": g.grft_sync_status()}
+    del P, echo
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_kt(args):
     print(json.dumps({"keystone": measure_kt(args.kt_rows, args.steps, args.warmup)}))
     return 0
@@ -575,6 +605,8 @@ def main():
                          "and gather forms (one JSON line; --cells N: the first N cells)")
     ap.add_argument("--other-precisions", type=int, default=1,
                     help="1: also time the step in the other contraction mode (fp16x1 beside bf16x3)")
+    ap.add_argument("--p3", action="store_true",
+                    help="time DS-GRFT with the acceleration rate (P = 3) on its 2.1e9-hypothesis grid (one JSON line)")
     ap.add_argument("--kt", action="store_true",
                     help="time the keystone branch (DS-KT-MFP map + detection) alone (one JSON line)")
     ap.add_argument("--kt-rows", type=int, default=0,
@@ -592,6 +624,9 @@ def main():
         return run_kt(args)
     if args.forms:
         return run_forms(args)
+    if args.p3:
+        print(json.dumps({"p3": measure_p3(args.steps, args.warmup, args.precision)}))
+        return 0
     if args.pd:
         return run_pd(args)
 

@@ -299,6 +299,33 @@ int dskt_fine_dfm_fft(const grft_radar *radar, const grft_c32 *Z, const grft_dsg
 int dskt_mfp(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid, grft_c32 *Y,
              float *P, void *stream);
 
+/* ---------------------------------------------------------------- P = 3 (acceleration rate)
+ *
+ * DS-GRFT with the third-order motion model r(t) = r0 + v t + a t^2 / 2 + b t^3 / 6 (Sec. II
+ * eq. slant range, c_3 = b / 6; Alg. 3 extended to P = 3).  Coarse centres vc x ac x bc, fine
+ * offsets (k - Fv/2) vc.step / Fv, (q - Fa/2) ac.step / Fa, (u - Fb/2) bc.step / Fb; cell
+ * c = (i ac.count + l) bc.count + w, fine f = (k Fa + q) Fb + u.  Bins are
+ * floor(d / dr + 0.5) with d = ((v t) + ((0.5 a)(t t))) + ((b / 6)((t t) t)) in FP64, each
+ * operation rounded once. */
+typedef struct {
+    int32_t r0_begin, r0_count;
+    grft_axis vc, ac, bc;
+    int32_t Fv, Fa, Fb;
+} grft_dsgrid3;
+
+/* The fused coarse gather + fine contraction of dsgrft_fine_dfm (Z = NULL) for a P = 3 grid,
+ * on the tensor cores (GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X1; GRFT_FP32 returns
+ * GRFT_EUNSUPPORTED):
+ *   Y(n0; c, f) = exp(j 4 pi n0 dr / lambda) sum_m s[m][n0 + rho_c(m)] w_c(m) D[m][f],
+ *   D[m][f] = exp(j 4 pi d(dv_k, da_q, db_u, t_m) / lambda).
+ * Output (Y and P, either nullable, not both): the v-slab of the layout
+ *   [(i - i0) Fv + k][l Fa + q][w Fb + u][n0 - r0_begin],  i0 = cell_begin / (ac.count bc.count);
+ * cells outside [cell_begin, cell_begin + cell_count) are left untouched.  Fv Fa Fb <= 2^20,
+ * cell_count <= 65535. */
+int dsgrft3_fine_dfm(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid3 *grid,
+                     int32_t cell_begin, int32_t cell_count, grft_precision precision, grft_c32 *Y, float *P,
+                     void *stream);
+
 /* Many CPIs (uneven M, N) in one persistent launch (graph-capturable after a first
  * uncaptured call of the same shape).  radar's M and N are ignored (per item); grid's
  * r0 fields are ignored (per item).  items is a HOST array of at most 256 entries; its

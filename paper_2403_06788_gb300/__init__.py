@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X1, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_LINEAR,
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
-__all__ = ["dsgrft_coarse_rm_fd_ex", "dsgrft_fine_dfm_fd", "dsgrft_fd", "dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
+__all__ = ["dsgrft3_fine_dfm", "dsgrft3", "dsgrft_coarse_rm_fd_ex", "dsgrft_fine_dfm_fd", "dsgrft_fd", "dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
            "load", "grft_version", "grft_sync_status", "grft_set_wait_limit", "grft_release_workspace",
            "grft_shutdown",
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
@@ -49,6 +49,11 @@ def _grid(g) -> _abi.grft_grid:
 def _dsgrid(g) -> _abi.grft_dsgrid:
     return _abi.grft_dsgrid(int(g.r0_begin), int(g.r0_count), _axis(g.vc), _axis(g.ac), int(g.Fv),
                             int(g.Fa))
+
+
+def _dsgrid3(g) -> _abi.grft_dsgrid3:
+    return _abi.grft_dsgrid3(int(g.r0_begin), int(g.r0_count), _axis(g.vc), _axis(g.ac), _axis(g.bc), int(g.Fv),
+                             int(g.Fa), int(g.Fb))
 
 
 def _cfar(c) -> _abi.grft_cfar:
@@ -209,6 +214,28 @@ def dsgrft_fine_dfm_fft(radar, echo, grid, cell_begin, cell_count, Y=None, P=Non
     check(load().dsgrft_fine_dfm_fft(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G),
                                      int(cell_begin), int(cell_count), _ptr(Y, torch.complex64, "Y"),
                                      _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft_fine_dfm_fft")
+
+
+def dsgrft3_fine_dfm(radar, echo, grid3, cell_begin, cell_count, precision, Y=None, P=None, stream=None):
+    """DS-GRFT with the acceleration rate (P = 3), fused gather + tensor-core contraction into
+    the v-slab [(i - i0) Fv + k][l Fa + q][w Fb + u][r0] starting at i0 = cell_begin / (na nb)."""
+    R, G = _radar(radar), _dsgrid3(grid3)
+    check(load().dsgrft3_fine_dfm(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G), int(cell_begin),
+                                  int(cell_count), _precision(precision), _ptr(Y, torch.complex64, "Y"),
+                                  _ptr(P, torch.float32, "P"), _stream(stream)), "dsgrft3_fine_dfm")
+
+
+def dsgrft3(radar, echo, grid3, precision="bf16x3", want_Y=False, want_P=True):
+    """P = 3 DS-GRFT over the whole grid; returns P [v_full][a_full][b_full][r0] (and Y)."""
+    shape = (int(grid3.vc.count) * int(grid3.Fv), int(grid3.ac.count) * int(grid3.Fa),
+             int(grid3.bc.count) * int(grid3.Fb), int(grid3.r0_count))
+    P = torch.empty(shape, dtype=torch.float32, device=echo.device) if want_P else None
+    Y = torch.empty(shape, dtype=torch.complex64, device=echo.device) if want_Y else None
+    ncell = int(grid3.vc.count) * int(grid3.ac.count) * int(grid3.bc.count)
+    dsgrft3_fine_dfm(radar, echo, grid3, 0, ncell, precision, Y, P)
+    if want_Y and want_P:
+        return P, Y
+    return Y if want_Y else P
 
 
 def dskt_keystone(radar, echo, Skt, stream=None):

@@ -40,6 +40,11 @@ class grft_dsgrid(C.Structure):
                 ("ac", grft_axis), ("Fv", C.c_int32), ("Fa", C.c_int32)]
 
 
+class grft_dsgrid3(C.Structure):
+    _fields_ = [("r0_begin", C.c_int32), ("r0_count", C.c_int32), ("vc", grft_axis),
+                ("ac", grft_axis), ("bc", grft_axis), ("Fv", C.c_int32), ("Fa", C.c_int32), ("Fb", C.c_int32)]
+
+
 class grft_cfar(C.Structure):
     _fields_ = [("guard", C.c_int32), ("train", C.c_int32), ("pfa", C.c_double),
                 ("fixed_thresh", C.c_float), ("mode", C.c_int32)]
@@ -84,6 +89,8 @@ SIGNATURES = {
                                      C.c_int, C.c_int, _P, _P, _P]),
     "dsgrft_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32,
                                       C.c_int32, _P, _P, _P]),
+    "dsgrft3_fine_dfm": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid3), C.c_int32, C.c_int32,
+                                   C.c_int, _P, _P, _P]),
     "dskt_keystone": (C.c_int, [C.POINTER(grft_radar), _P, _P, _P]),
     "dskt_coarse_rm": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32, _P, _P]),
     "dskt_fine_dfm_fft": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int32, C.c_int32,

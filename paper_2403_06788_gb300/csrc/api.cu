@@ -404,21 +404,18 @@ int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_d
     return launch_coarse_rm(c, R, (const float2 *)echo, *grid, cell_count, rho, w, (float2 *)Z);
 }
 
-int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo,
-                    const grft_dsgrid *grid, int32_t cell_begin, int32_t cell_count,
-                    grft_precision precision, grft_c32 *Y, float *P, void *stream) {
-    if (!radar_ok(radar) || (!Z && !echo) || (!Y && !P) || !dsgrid_ok(grid, radar) ||
-        cell_begin < 0 || cell_count < 0 ||
-        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count || cell_count > 65535)
-        return GRFT_EINVAL;
-    if (precision != GRFT_FP32 && precision != GRFT_BF16X3 && precision != GRFT_FP16X3 &&
-        precision != GRFT_FP16X1)
-        return GRFT_EINVAL;
+namespace {
+
+// The fine stage of dsgrft_fine_dfm (rate off) and dsgrft3_fine_dfm (P = 3, rate on): the
+// arguments are checked by the callers.
+int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo, const grft_dsgrid *grid,
+                  const Rate3 &rate, int32_t cell_begin, int32_t cell_count, grft_precision precision,
+                  grft_c32 *Y, float *P, void *stream) {
     Ctx c;
     int e = make_ctx(stream, c);
     if (e) return e;
     const RadarD R = radar_d(*radar);
-    const int F = grid->Fv * grid->Fa;
+    const int F = grid->Fv * grid->Fa * rate.Fb;
     const int Fpad = (F + 127) / 128 * 128;
     const int Mpad = (R.M + 31) / 32 * 32;
     const bool tc = precision != GRFT_FP32;
@@ -441,9 +438,9 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     float2 *w = (float2 *)(ws + rho_bytes);
     float2 *e0 = (float2 *)(ws + rho_bytes + w_bytes);
     unsigned char *dptr = ws + rho_bytes + w_bytes + e0_bytes;
-    if (!Z && (e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w))) return e;
+    if (!Z && (e = launch_coarse_tables(c, R, *grid, cell_begin, cell_count, rho, w, rate))) return e;
     if ((e = launch_range_phase(c, R, grid->r0_begin, grid->r0_count, e0))) return e;
-    if (!tc) {
+    if (!tc) {                       // P = 2 only (the callers refuse FP32 for P = 3)
         DsOut out;
         out.Y = (float2 *)Y;
         out.P = P;
@@ -463,7 +460,7 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
     const bool fp16 = precision == GRFT_FP16X3 || precision == GRFT_FP16X1;
     const int nprod = precision == GRFT_FP16X1 ? 1 : 3;
-    if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo))) return e;
+    if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo, rate))) return e;
     DsTcItem it;
     it.echo = (const float2 *)echo;
     it.Z = (const float2 *)Z;
@@ -476,8 +473,46 @@ int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *
     it.r0_count = grid->r0_count;
     it.cell_begin = cell_begin;
     it.cell_count = cell_count;
-    it.i0 = cell_begin / grid->ac.count;
-    return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, nprod, Zhi, Zlo, z_rows);
+    it.i0 = cell_begin / (grid->ac.count * rate.count);
+    return launch_ds_tc(c, &it, 1, *grid, rho, w, cell_begin, R.M, Bhi, Blo, Mpad, fp16, nprod, Zhi, Zlo, z_rows,
+                        rate);
+}
+
+bool precision_ok(grft_precision p) {
+    return p == GRFT_FP32 || p == GRFT_BF16X3 || p == GRFT_FP16X3 || p == GRFT_FP16X1;
+}
+
+}  // namespace
+
+int dsgrft_fine_dfm(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo,
+                    const grft_dsgrid *grid, int32_t cell_begin, int32_t cell_count,
+                    grft_precision precision, grft_c32 *Y, float *P, void *stream) {
+    if (!radar_ok(radar) || (!Z && !echo) || (!Y && !P) || !dsgrid_ok(grid, radar) ||
+        cell_begin < 0 || cell_count < 0 ||
+        (long)cell_begin + cell_count > (long)grid->vc.count * grid->ac.count || cell_count > 65535)
+        return GRFT_EINVAL;
+    if (!precision_ok(precision)) return GRFT_EINVAL;
+    return fine_dfm_impl(radar, Z, echo, grid, kNoRate, cell_begin, cell_count, precision, Y, P, stream);
+}
+
+int dsgrft3_fine_dfm(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid3 *grid3, int32_t cell_begin,
+                     int32_t cell_count, grft_precision precision, grft_c32 *Y, float *P, void *stream) {
+    if (!radar_ok(radar) || !echo || (!Y && !P) || !grid3 || !axis_ok(grid3->bc) || grid3->Fb <= 0)
+        return GRFT_EINVAL;
+    grft_dsgrid g;
+    g.r0_begin = grid3->r0_begin;
+    g.r0_count = grid3->r0_count;
+    g.vc = grid3->vc;
+    g.ac = grid3->ac;
+    g.Fv = grid3->Fv;
+    g.Fa = grid3->Fa;
+    if (!dsgrid_ok(&g, radar) || (long)g.Fv * g.Fa * grid3->Fb > (1L << 20) || cell_begin < 0 || cell_count < 0 ||
+        (long)cell_begin + cell_count > (long)g.vc.count * g.ac.count * grid3->bc.count || cell_count > 65535)
+        return GRFT_EINVAL;
+    if (!precision_ok(precision)) return GRFT_EINVAL;
+    if (precision == GRFT_FP32) return GRFT_EUNSUPPORTED;     // the tensor-core path only
+    const Rate3 rate{true, grid3->bc.start, grid3->bc.step, grid3->bc.count, grid3->Fb};
+    return fine_dfm_impl(radar, nullptr, echo, &g, rate, cell_begin, cell_count, precision, Y, P, stream);
 }
 
 int dsgrft_coarse_rm_fd_ex(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,

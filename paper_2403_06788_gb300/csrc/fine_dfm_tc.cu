@@ -88,6 +88,7 @@ struct TcBatch {
     int zld;                // row length of the split operand (elements) = 2 * Mpad
     int n_items, total_ctas, total_tiles;
     int tiles_n, F, Fv, Fa, na_c;
+    int Fb, nb_c;           // acceleration-rate axis (P = 3); 1, 1 for P = 2
     int fp16;
     int nprod;              // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only (no lo planes)
     uint32_t idesc;
@@ -590,6 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int r = q4 * 32 + lane;
         const int er = threadIdx.x - 64;         // 0..127 over the epilogue warps
         const int na_full = B.na_c * B.Fa;
+        const int nb_full = B.nb_c * B.Fb;
         bool aborted = false;
         int tcount = 0;
         for (int tile = cid; tile < B.total_tiles; tile += ncl, ++tcount) {
@@ -597,14 +599,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int nt, mt, cl;
             const TcItem &p = decode_unit<CL>(B, tile, rank, nt, mt, cl);
             const int c = p.cell0 + cl;
-            const int iv = c / B.na_c - p.i0, il = c % B.na_c;
+            const int iw = c % B.nb_c, c2 = c / B.nb_c;      // P = 3: c = (i na_c + l) nb_c + w
+            const int iv = c2 / B.na_c - p.i0, il = c2 % B.na_c;
             named_bar_sync(1, 128);                  // previous tile's offsets no longer read
             if (!aborted) {
                 const int f = nt * (TC_BN / 2) + er;
                 long off = -1;
-                if (f < B.F) {
-                    const int k = f / B.Fa, q = f % B.Fa;
-                    off = ((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * p.r0_count;
+                if (f < B.F) {                       // f = (k Fa + q) Fb + u
+                    const int u = f % B.Fb, f2 = f / B.Fb;
+                    const int k = f2 / B.Fa, q = f2 % B.Fa;
+                    off = (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (iw * B.Fb + u)) *
+                          p.r0_count;
                 }
                 s_rowoff[er] = off;
             }
@@ -911,8 +916,8 @@ void release_pipe(int dev) {
 int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, int nprod, uint16_t *const Zhi[2],
-                 uint16_t *const Zlo[2], long z_rows_cap) {
-    const int F = g.Fv * g.Fa;
+                 uint16_t *const Zlo[2], long z_rows_cap, const Rate3 &rate) {
+    const int F = g.Fv * g.Fa * rate.Fb;
     const int Fpad = (F + 127) / 128 * 128;
     TcBatch b;
     b.rho = rho;
@@ -925,6 +930,8 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     b.Fv = g.Fv;
     b.Fa = g.Fa;
     b.na_c = g.ac.count;
+    b.Fb = rate.Fb;
+    b.nb_c = rate.count;
     b.fp16 = fp16 ? 1 : 0;
     b.nprod = nprod;
     b.idesc = 0;                     // set per variant by launch_gemm

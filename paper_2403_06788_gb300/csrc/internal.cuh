@@ -21,6 +21,12 @@ __device__ __forceinline__ double displacement(double v, double a, double t) {
     return __dadd_rn(vt, __dmul_rn(ha, tt));
 }
 
+// P = 3: d + (b / 6) ((t t) t), the acceleration-rate term added last.
+__device__ __forceinline__ double displacement3(double v, double a, double b, double t) {
+    const double tt = __dmul_rn(t, t);
+    return __dadd_rn(displacement(v, a, t), __dmul_rn(__ddiv_rn(b, 6.0), __dmul_rn(tt, t)));
+}
+
 __device__ __forceinline__ int bin_shift(double d, double dr) {
     return (int)floor(__dadd_rn(__ddiv_rn(d, dr), 0.5));
 }
@@ -52,6 +58,17 @@ __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
 __device__ __forceinline__ void latch_error(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
+
+// The acceleration-rate axis of a P = 3 dual-scale grid (coarse centres start + w step, w <
+// count; Fb fine offsets (u - Fb/2) step / Fb).  A coarse cell index c of such a grid is
+// (i na_c + l) count + w and a fine index (k Fa + q) Fb + u.  on == false is P = 2 (count 1,
+// Fb 1): every formula reduces to the P = 2 one.
+struct Rate3 {
+    bool on;
+    double start, step;
+    int count, Fb;
+};
+constexpr Rate3 kNoRate{false, 0.0, 0.0, 1, 1};
 
 // --------------------------------------------------------------------------- host side
 struct RadarD {     // radar constants as the kernels use them
@@ -93,12 +110,12 @@ int launch_bins_phases(const Ctx &, const RadarD &, const double *v, const doubl
 int launch_plain_tables(const Ctx &, const RadarD &, const grft_grid &, long h0, int nh,
                         int32_t *rho, float2 *w);
 int launch_coarse_tables(const Ctx &, const RadarD &, const grft_dsgrid &, int cell_begin,
-                         int cell_count, int32_t *rho, float2 *w);
+                         int cell_count, int32_t *rho, float2 *w, const Rate3 &rate = kNoRate);
 int launch_range_phase(const Ctx &, const RadarD &, int r0_begin, int r0_count, float2 *e0);
 int launch_dechirp(const Ctx &, const RadarD &, const grft_dsgrid &, float2 *D);
 // Dechirp matrix in the K-major real-GEMM operand layout of the tensor-core kernel.
 int launch_dechirp_split(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Fpad,
-                         bool fp16, uint16_t *Bhi, uint16_t *Blo);
+                         bool fp16, uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
 
 int launch_plain(const Ctx &, const RadarD &, const float2 *echo, const grft_grid &, long h0,
                  int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,
@@ -163,7 +180,8 @@ constexpr int DS_TC_MAX_ITEMS = 64;    // CPIs per tensor-core launch (kernel-pa
 int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, int nprod, uint16_t *const Zhi[2],
-                 uint16_t *const Zlo[2], long z_rows_cap);   // nprod: 3 (split) or 1 (FP16 hi only)
+                 uint16_t *const Zlo[2], long z_rows_cap,    // nprod: 3 (split) or 1 (FP16 hi only)
+                 const Rate3 &rate = kNoRate);
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);

@@ -38,15 +38,17 @@ __global__ void k_plain_tables(RadarD R, double v0, double dv, double a0, double
 }
 
 // Coarse cells c = i * na_c + l: bins of the coarse trajectory and H_pre-DFM.
-__global__ void k_coarse_tables(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
+__global__ void k_coarse_tables(RadarD R, grft_dsgrid g, Rate3 rate, int cell_begin, int cell_count,
                                 int32_t *__restrict__ rho, float2 *__restrict__ w) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)cell_count * R.M) return;
     int c = cell_begin + (int)(idx / R.M), m = (int)(idx % R.M);
+    const int cw = c % rate.count;              // P = 3: (i na_c + l) nb_c + w
+    c /= rate.count;
     double vc = axis_value(g.vc.start, g.vc.step, c / g.ac.count);
     double ac = axis_value(g.ac.start, g.ac.step, c % g.ac.count);
     double t = slow_time(m, R.prf);
-    double d = displacement(vc, ac, t);
+    double d = rate.on ? displacement3(vc, ac, axis_value(rate.start, rate.step, cw), t) : displacement(vc, ac, t);
     rho[idx] = bin_shift(d, R.dr);
     w[idx] = range_phase(d, R.lambda);
 }
@@ -57,12 +59,16 @@ __global__ void k_range_phase(RadarD R, int r0_begin, int r0_count, float2 *__re
     e0[j] = range_phase(__dmul_rn((double)(r0_begin + j), R.dr), R.lambda);
 }
 
-__device__ __forceinline__ float2 dechirp_value(const RadarD &R, const grft_dsgrid &g, int m, int f) {
+__device__ __forceinline__ float2 dechirp_value(const RadarD &R, const grft_dsgrid &g, int m, int f,
+                                                const Rate3 &rate) {
+    const int u = f % rate.Fb;                  // P = 3: f = (k Fa + q) Fb + u
+    f /= rate.Fb;
     int k = f / g.Fa, q = f % g.Fa;
     double dv = fine_offset(g.vc.step, g.Fv, k);
     double da = fine_offset(g.ac.step, g.Fa, q);
     double t = slow_time(m, R.prf);
-    return range_phase(displacement(dv, da, t), R.lambda);
+    const double d = rate.on ? displacement3(dv, da, fine_offset(rate.step, rate.Fb, u), t) : displacement(dv, da, t);
+    return range_phase(d, R.lambda);
 }
 
 // D[m][f], f = k * Fa + q (H_DFM of the fine offsets, Def. 1).
@@ -71,7 +77,7 @@ __global__ void k_dechirp(RadarD R, grft_dsgrid g, float2 *__restrict__ D) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long)R.M * F) return;
     int m = (int)(i / F), f = (int)(i % F);
-    D[i] = dechirp_value(R, g, m, f);
+    D[i] = dechirp_value(R, g, m, f, Rate3{false, 0.0, 0.0, 1, 1});
 }
 
 __device__ __forceinline__ uint16_t to_bits(float x, bool fp16) {
@@ -89,13 +95,13 @@ __device__ __forceinline__ float from_bits(uint16_t b, bool fp16) {
 //   (ri, kri) = (0,0): Re D   (0,1): -Im D   (1,0): Im D   (1,1): Re D
 // split as hi = round(x), lo = round(x - hi) in BF16 or FP16.  Pulses m >= M and fine
 // hypotheses f >= F (padding up to Fpad) are zero.
-__global__ void k_dechirp_split(RadarD R, grft_dsgrid g, int Mpad, int Fpad, int fp16,
+__global__ void k_dechirp_split(RadarD R, grft_dsgrid g, Rate3 rate, int Mpad, int Fpad, int fp16,
                                 uint16_t *__restrict__ Bhi, uint16_t *__restrict__ Blo) {
-    int F = g.Fv * g.Fa;
+    int F = g.Fv * g.Fa * rate.Fb;
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;     // over Fpad * Mpad
     if (i >= (long)Fpad * Mpad) return;
     int f = (int)(i / Mpad), m = (int)(i % Mpad);
-    float2 d = (m < R.M && f < F) ? dechirp_value(R, g, m, f) : make_float2(0.f, 0.f);
+    float2 d = (m < R.M && f < F) ? dechirp_value(R, g, m, f, rate) : make_float2(0.f, 0.f);
     float vals[2][2] = {{d.x, -d.y}, {d.y, d.x}};
     long kk = (long)(m / 32) * 64 + (m % 32);
     for (int ri = 0; ri < 2; ++ri) {
@@ -135,11 +141,11 @@ int launch_plain_tables(const Ctx &c, const RadarD &R, const grft_grid &g, long 
 }
 
 int launch_coarse_tables(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_begin,
-                         int cell_count, int32_t *rho, float2 *w) {
+                         int cell_count, int32_t *rho, float2 *w, const Rate3 &rate) {
     long n = (long)cell_count * R.M;
     if (n == 0) return GRFT_OK;
     KernelTimer kt(c, GRFT_KERNEL_TABLES);
-    k_coarse_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, cell_begin, cell_count, rho, w);
+    k_coarse_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, rate, cell_begin, cell_count, rho, w);
     return check_launch();
 }
 
@@ -158,10 +164,10 @@ int launch_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, float2 *
 }
 
 int launch_dechirp_split(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int Mpad, int Fpad,
-                         bool fp16, uint16_t *Bhi, uint16_t *Blo) {
+                         bool fp16, uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate) {
     long n = (long)Fpad * Mpad;
     KernelTimer kt(c, GRFT_KERNEL_TABLES);
-    k_dechirp_split<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, Mpad, Fpad, fp16 ? 1 : 0, Bhi, Blo);
+    k_dechirp_split<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, rate, Mpad, Fpad, fp16 ? 1 : 0, Bhi, Blo);
     return check_launch();
 }
 

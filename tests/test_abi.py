@@ -63,8 +63,9 @@ def test_struct_offsets_compiled_by_the_host_compiler():
 #include <stddef.h>
 #include "dsgrft.h"
 int main(void){
- printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(grft_det), offsetof(grft_det,p), offsetof(grft_det,r0_m),
-   sizeof(grft_dsgrid), offsetof(grft_dsgrid,Fv), sizeof(grft_batch_item), offsetof(grft_cfar,fixed_thresh));
+ printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(grft_det), offsetof(grft_det,p), offsetof(grft_det,r0_m),
+   sizeof(grft_dsgrid), offsetof(grft_dsgrid,Fv), sizeof(grft_batch_item), offsetof(grft_cfar,fixed_thresh),
+   sizeof(grft_dsgrid3), offsetof(grft_dsgrid3,bc), offsetof(grft_dsgrid3,Fb));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -75,7 +76,8 @@ int main(void){
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(_abi.grft_det), _abi.grft_det.p.offset, _abi.grft_det.r0_m.offset,
                     ctypes.sizeof(_abi.grft_dsgrid), _abi.grft_dsgrid.Fv.offset,
-                    ctypes.sizeof(_abi.grft_batch_item), _abi.grft_cfar.fixed_thresh.offset]
+                    ctypes.sizeof(_abi.grft_batch_item), _abi.grft_cfar.fixed_thresh.offset,
+                    ctypes.sizeof(_abi.grft_dsgrid3), _abi.grft_dsgrid3.bc.offset, _abi.grft_dsgrid3.Fb.offset]
 
 
 def test_kernel_class_ids_match_header():
