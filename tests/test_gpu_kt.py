@@ -204,3 +204,39 @@ def test_kt_rejects_unsupported(cuda_lib):
         g.dskt_fine_dfm_fft(R, Z, dataclasses.replace(ok, Fv=32), 0, 3, None,
                             torch.empty((96, 2, R.N), device="cuda"))
     assert g.grft_sync_status() == 0
+
+
+_CHUNK_CODE = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2403_06788_gb300 as g, synth
+sc = synth.dskt_m64()
+R, ds = sc.radar, sc.ds
+s = synth.make_echo(R, sc.targets, sc.seed)
+P = g.dsktmfp(R, torch.from_numpy(s).cuda(), ds)
+assert g.grft_sync_status() == 0
+np.save(sys.argv[1], P.cpu().numpy())
+"""
+
+
+def test_dskt_mfp_chunks_over_folding_factors(cuda_lib, tmp_path):
+    """A budget of two folding-factor rows (4 chunks for q in [-3, 3]) gives the same map,
+    bit for bit, as one chunk."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sc = synth.dskt_m64()
+    row_bytes = sc.ds.ac.count * sc.radar.M * sc.ds.r0_count * 8
+    outs = []
+    for name, budget in (("one", None), ("four", 2 * row_bytes + 64)):
+        env = dict(os.environ)
+        env.pop("DSGRFT_SPLIT_BUDGET_BYTES", None)
+        if budget:
+            env["DSGRFT_SPLIT_BUDGET_BYTES"] = str(budget)
+        out = str(tmp_path / (name + ".npy"))
+        r = subprocess.run([sys.executable, "-c", _CHUNK_CODE % root, out], env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
