@@ -240,3 +240,31 @@ def test_dskt_mfp_chunks_over_folding_factors(cuda_lib, tmp_path):
         assert r.returncode == 0, r.stderr[-2000:]
         outs.append(np.load(out))
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_kt_edges_max_range_min_pulses_and_empty(cuda_lib):
+    """N = 8192 (the largest range length) with M = 16 (the fewest pulses): keystone and
+    coarse stage on every output; the fine stage with M = 16 zero-padded into a 64-point
+    transform; an empty cell range writes nothing."""
+    g = cuda_lib
+    R = Radar(M=16, N=8192, fc_hz=1.0e9, prf_hz=500.0, dr_m=15.0)
+    s = synth.make_echo(R, [Target(5000.3, 150.0, 4.0, complex(2.0, -1.0))], 44)
+    Skt = _keystone(g, R, s)
+    ykt = oracle.keystone(R, s)
+    assert rel_peak_err(Skt, ykt[:, _slots(g, R.N)]) <= TOL_FP32
+    ds = synth.kt_grid(R, -1, 3, Axis(-5.0, 10.0, 2), 2, L=64, r0_begin=4990, r0_count=33)
+    Z = torch.empty((ds.n_cells, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dskt_coarse_rm(R, torch.from_numpy(Skt).cuda(), ds, 0, ds.n_cells, Z)
+    assert g.grft_sync_status() == 0
+    Zo = oracle.kt_coarse_rm(R, ykt, ds, 0, ds.n_cells)
+    assert rel_peak_err(Z.cpu().numpy(), Zo) <= TOL_FP32
+    nv, na = ds.vc.count * ds.Fv, ds.ac.count * ds.Fa
+    Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dskt_fine_dfm_fft(R, Z, ds, 0, ds.n_cells, Y, None)
+    assert g.grft_sync_status() == 0
+    Yo = oracle.dskt_map(R, s, ds, ykt=ykt)
+    assert rel_peak_err(Y.cpu().numpy(), Yo) <= TOL_FP32
+    sentinel = torch.full_like(Z, complex(7.0, 7.0))
+    g.dskt_coarse_rm(R, torch.from_numpy(Skt).cuda(), ds, 2, 0, sentinel)
+    torch.cuda.synchronize()
+    assert torch.all(sentinel == complex(7.0, 7.0))

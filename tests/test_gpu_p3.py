@@ -2,7 +2,7 @@
 against the FP64 numpy oracle (oracle/p3.py): every output of a small case with ragged
 tiles on every axis, the trivial b axis equal to the P = 2 path bit for bit, a cell
 sub-range written into its v-slab only, sampled rows and target focus on the
-2.1e9-hypothesis ds3_m512 grid, and the rejection of FP32."""
+2.1e9-hypothesis ds3_m512 grid, an empty cell range, and the rejection of FP32."""
 import dataclasses
 
 import numpy as np
@@ -129,3 +129,13 @@ def test_p3_rejects_fp32(cuda_lib):
     with pytest.raises(g.GrftError):
         g.dsgrft3(R, torch.from_numpy(s).cuda(), g3, precision="fp32")
     assert g.grft_sync_status() == 0
+
+
+def test_p3_empty_cell_range_writes_nothing(cuda_lib):
+    g = cuda_lib
+    R, g3, s = _small()
+    shape = (g3.vc.count * g3.Fv, g3.ac.count * g3.Fa, g3.bc.count * g3.Fb, g3.r0_count)
+    P = torch.full(shape, 3.0, device="cuda")
+    g.dsgrft3_fine_dfm(R, torch.from_numpy(s).cuda(), g3, 5, 0, "bf16x3", None, P)
+    torch.cuda.synchronize()
+    assert g.grft_sync_status() == 0 and torch.all(P == 3.0)
