@@ -1,7 +1,8 @@
-// Radix-2 transforms of power-of-two length over complex FP32 data in shared memory, done
-// by a whole CTA of NT threads (every thread calls; each stage ends in __syncthreads).
-// `cols` transforms of the same length, stride `ld` apart, run together: one barrier per
-// stage for all of them.
+// Transforms of power-of-two length over complex FP32 data in shared memory, done by a
+// whole CTA of NT threads (every thread calls; each pass ends in __syncthreads): radix-4
+// passes of two radix-2 stages each, plus one radix-2 stage when log2 n is odd.  `cols`
+// transforms of the same length, stride `ld` apart, run together: one barrier per pass for
+// all of them.
 #pragma once
 
 #include "internal.cuh"
