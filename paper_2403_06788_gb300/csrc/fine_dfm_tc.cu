@@ -14,10 +14,11 @@
 //
 // k_coarse_split (kernel a, the mGIFT of Alg. 1 in the time domain): one CTA per (cell,
 //   128-bin tile).  It gathers every bin's samples at n0 + rho_c(m) from the L2-resident
-//   echo, multiplies by the coarse phase w_c(m), splits hi/lo and writes the K-major
-//   operand Zs[cell][bin][k'] (two 16-bit planes) in whole-sector runs; the TMA loads of
-//   kernel b apply the 128-byte swizzle.  Done once per (cell, bin) instead of once per
-//   fine-hypothesis tile.
+//   echo (one contiguous run of bins per pulse and warp), multiplies by the coarse phase
+//   w_c(m), splits hi/lo, transposes through a warp-private shared tile and writes the
+//   K-major operand Zs[cell][bin][k'] (two 16-bit planes) as whole 128-byte lines; the TMA
+//   loads of kernel b apply the 128-byte swizzle.  Done once per (cell, bin) instead of once
+//   per fine-hypothesis tile.
 // k_ds_tc (kernel b): one persistent CTA per SM, 192 threads:
 //   warp 0      TMA producer: Zs tile (A, 128 x 64) and dechirp tile (B, 256 x 64), hi and
 //               lo planes, 128-byte swizzle, into a 2-stage ring (96 KB per stage)
@@ -59,8 +60,9 @@ constexpr size_t tc_smem_bytes(int BN, int ST, int BK, int NP) {
     return (size_t)ST * ((NP == 3 ? 2 : 1) * ((size_t)TC_BM * BK * 2 + (size_t)BN * BK * 2)) + 1024;
 }
 
-constexpr int SP_THREADS = 512;             // 16 warps x 8 range bins = one 128-bin tile
+constexpr int SP_THREADS = 128;             // 4 warps x 32 range bins = one 128-bin tile
 constexpr int SP_TAB_MAX = 2048;            // pulses whose bins and phases are staged in shared memory
+constexpr int SP_TR_WORDS = (SP_THREADS / 32) * 2 * 32 * 8;   // uint4 words of the warp tiles (32 KB)
 
 constexpr int TC_MAX_ITEMS = DS_TC_MAX_ITEMS;        // CPIs per launch (kernel-parameter table)
 constexpr int TC_ROUNDS = 1;                         // rounds beyond what the buffer forces (1: none)
@@ -276,33 +278,35 @@ __device__ __forceinline__ float2 ld_global_nc_hint(const float2 *src, uint64_t 
     return v;
 }
 
-__global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_constant__ TcBatch B,
-                                                                uint16_t *__restrict__ Zhi,
-                                                                uint16_t *__restrict__ Zlo) {
-    // One CTA per (item, cell, 128-bin tile).  Lane l of warp w owns bin r = 8w + l/4 and
-    // the 8-pulse group g = l%4 of every 32-pulse stage: its gathers are 8-bin runs (whole
-    // sectors) and its stores complete 64-byte runs of the K-major output rows
-    // (k' = (m/32)*64 + (re|im)*32 + m%32, hi and lo planes).  The cell's bins and phases
-    // are staged in shared memory; the next stage's samples are requested before the
-    // current stage is converted.
-    __shared__ int s_rho[SP_TAB_MAX];
-    __shared__ float2 s_w[SP_TAB_MAX];
+__global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_constant__ TcBatch B,
+                                                             uint16_t *__restrict__ Zhi,
+                                                             uint16_t *__restrict__ Zlo, int tab_cap) {
+    // One CTA per (item, cell, 128-bin tile), four warps; warp w owns the 32 bins 32w + lane of
+    // the tile and every pulse, taken in sub-steps of 8 pulses.  A lane's gathers for one pulse
+    // are consecutive bins of the echo row (the warp reads one 256-byte run per pulse).  The
+    // converted values pass through a warp-private shared tile [plane][32 rows][8 chunks of
+    // 16 bytes] (chunk index XOR row % 8: conflict-free on both sides) and leave, once the four
+    // sub-steps of a 32-pulse stage are in, as whole 128-byte lines of the K-major operand rows
+    // (k' = (m/32)*64 + (re|im)*32 + m%32).  The cell's bins and phases are staged in shared
+    // memory; the next sub-step's samples are requested before the current one is converted.
+    extern __shared__ uint4 sp_smem[];          // [warps][2 planes][32][8], then w[tab_cap], rho[tab_cap]
     __shared__ int s_rng[2];                    // least and greatest bin shift of the cell
+    float2 *s_w = reinterpret_cast<float2 *>(sp_smem + SP_TR_WORDS);
+    int *s_rho = reinterpret_cast<int *>(s_w + tab_cap);
     const TcItem &p = B.it[find_item_cta(B, blockIdx.x)];
     const int local = blockIdx.x - p.cta0;
     const int mt = local % p.tiles_m;
     const int cl = local / p.tiles_m;
     const int c = p.cell0 + cl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = warp * 8 + (lane >> 2);
-    const int g = lane & 3;
     const bool fp16 = B.fp16 != 0;
-    const int j = mt * TC_BM + r;
+    const int j0 = mt * TC_BM;
+    const int j = j0 + warp * 32 + lane;
     const bool jok = j < p.r0_count;
     const long tab = (long)(c - B.tab_cell0) * B.Mtab;
     const long ztab = (long)(c - B.tab_cell0) * p.M;     // cell offset inside Z (M pulses per cell)
     const int nbase = p.r0_begin + j;
-    const bool tab_smem = !p.Z && p.M <= SP_TAB_MAX;
+    const bool tab_smem = !p.Z && p.M <= tab_cap;
     if (tab_smem) {
         if (tid == 0) {
             s_rng[0] = 0x7fffffff;
@@ -327,46 +331,60 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
     }
     const int *rho_t = tab_smem ? s_rho : B.rho + tab;
     const float2 *w_t = tab_smem ? s_w : B.w + tab;
-    const size_t row = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j;
-    uint16_t *zh = Zhi + row * (size_t)B.zld + g * 8;
-    uint16_t *zl = Zlo + row * (size_t)B.zld + g * 8;
-
+    uint4 *tr = sp_smem + warp * 512;            // this warp's tile: hi plane, then lo plane
+    const size_t row0 = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j0 + warp * 32;
     const uint64_t pol_z = l2_policy_evict_first();
     const bool with_lo = B.nprod == 3;          // block-uniform
-    auto split_store = [&](int kt, const float (&re)[8], const float (&im)[8]) {
+    const int S = 4 * p.KT;                     // sub-steps of 8 pulses (even)
+
+    // Convert sub-step s (pulses 8s..8s+7 of this lane's bin; phase already applied), place
+    // it in the warp tile, and after the fourth sub-step of a stage write the stage's lines.
+    auto put = [&](int s, const float (&re)[8], const float (&im)[8]) {
+        const int g = s & 3, kt = s >> 2, sw = lane & 7;
         uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
             split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
         }
-        const int o = kt * TC_BK;
-        st_global_v4_hint(zh + o, rh[0], rh[1], rh[2], rh[3], pol_z);
-        st_global_v4_hint(zh + o + 32, ih[0], ih[1], ih[2], ih[3], pol_z);
+        tr[lane * 8 + (g ^ sw)] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        tr[lane * 8 + ((4 + g) ^ sw)] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
         if (with_lo) {
-            st_global_v4_hint(zl + o, rl[0], rl[1], rl[2], rl[3], pol_z);
-            st_global_v4_hint(zl + o + 32, il[0], il[1], il[2], il[3], pol_z);
+            tr[256 + lane * 8 + (g ^ sw)] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            tr[256 + lane * 8 + ((4 + g) ^ sw)] = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+        if (g == 3) {
+            __syncwarp();
+            for (int pl = 0; pl < (with_lo ? 2 : 1); ++pl) {
+                uint16_t *Z = pl ? Zlo : Zhi;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int idx = q * 32 + lane, row = idx >> 3, ch = idx & 7;
+                    const uint4 x = tr[pl * 256 + row * 8 + (ch ^ (row & 7))];
+                    st_global_v4_hint(Z + (row0 + row) * (size_t)B.zld + kt * TC_BK + ch * 8, x.x, x.y, x.z, x.w,
+                                      pol_z);
+                }
+            }
+            __syncwarp();
         }
     };
 
     // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
     // of the tile is inside the r0 range and every gathered bin is inside the echo, so the
     // loop carries no bound checks.
-    const int j0 = mt * TC_BM;
     if (tab_smem && (p.M % 32) == 0 && j0 + TC_BM <= p.r0_count &&
         p.r0_begin + j0 + s_rng[0] >= 0 && p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
         const float2 *src = p.echo + nbase;
         const long N = p.N;
-        const int KT = p.KT;
         const uint64_t pol_e = l2_policy_evict_last();
-        auto ld = [&](int kt, float2 (&v)[8]) {
-            const int m0 = kt * 32 + g * 8;
+        auto ld = [&](int s, float2 (&v)[8]) {
+            const int m0 = s * 8;
             const float2 *rowp = src + (long)m0 * N;
 #pragma unroll
             for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
         };
-        auto cv = [&](int kt, const float2 (&v)[8]) {
-            const int m0 = kt * 32 + g * 8;
+        auto cv = [&](int s, const float2 (&v)[8]) {
+            const int m0 = s * 8;
             float re[8], im[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -374,24 +392,24 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
                 re[i] = x.x;
                 im[i] = x.y;
             }
-            split_store(kt, re, im);
+            put(s, re, im);
         };
         float2 va[8], vb[8];
         ld(0, va);
-        for (int kt = 0; kt < KT; kt += 2) {    // the two buffers alternate
-            if (kt + 1 < KT) ld(kt + 1, vb);
-            cv(kt, va);
-            if (kt + 1 >= KT) break;
-            if (kt + 2 < KT) ld(kt + 2, va);
-            cv(kt + 1, vb);
+        for (int s = 0; s < S; s += 2) {        // the two buffers alternate
+            ld(s + 1, vb);
+            cv(s, va);
+            if (s + 2 < S) ld(s + 2, va);
+            cv(s + 1, vb);
         }
         return;
     }
 
-    auto load8 = [&](int kt, float2 (&v)[8]) {
+    // General path (edge tiles, materialised Z, partial pulse groups, tables in global memory)
+    auto load8 = [&](int s, float2 (&v)[8]) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int m = kt * 32 + g * 8 + i;
+            const int m = s * 8 + i;
             float2 x = make_float2(0.f, 0.f);
             if (m < p.M && jok) {
                 if (p.Z) {
@@ -404,23 +422,25 @@ __global__ void __launch_bounds__(SP_THREADS, 2) k_coarse_split(const __grid_con
             v[i] = x;
         }
     };
-    auto store8 = [&](int kt, const float2 (&v)[8]) {
+    auto cv8 = [&](int s, const float2 (&v)[8]) {
         float re[8], im[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int m = kt * 32 + g * 8 + i;
+            const int m = s * 8 + i;
             float2 x = v[i];
             if (!p.Z && m < p.M) x = cmul(x, w_t[m]);
             re[i] = x.x;
             im[i] = x.y;
         }
-        split_store(kt, re, im);
+        put(s, re, im);
     };
-    // general path (edge tiles, materialised Z, partial pulse groups): one stage at a time
-    for (int kt = 0; kt < p.KT; ++kt) {
-        float2 v[8];
-        load8(kt, v);
-        store8(kt, v);
+    float2 va[8], vb[8];
+    load8(0, va);
+    for (int s = 0; s < S; s += 2) {
+        load8(s + 1, vb);
+        cv8(s, va);
+        if (s + 2 < S) load8(s + 2, va);
+        cv8(s + 1, vb);
     }
 }
 
@@ -857,8 +877,17 @@ struct Round {
 };
 
 int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
+    // shared memory: the warp tiles, then the bins and phases of a cell (largest M of the
+    // round, up to SP_TAB_MAX; larger items read their tables from global memory)
+    static bool attr[64] = {false};
+    int cap = 0;
+    for (int i = 0; i < b.n_items; ++i) cap = b.it[i].M > cap ? b.it[i].M : cap;
+    if (cap > SP_TAB_MAX) cap = SP_TAB_MAX;
+    const size_t most = SP_TR_WORDS * sizeof(uint4) + (size_t)SP_TAB_MAX * (sizeof(float2) + sizeof(int));
+    const size_t bytes = SP_TR_WORDS * sizeof(uint4) + (size_t)cap * (sizeof(float2) + sizeof(int));
+    if (c.device >= 64 || !set_smem_attr((const void *)k_coarse_split, most, c.device, attr)) return GRFT_ECUDA;
     KernelTimer kt(c, GRFT_KERNEL_SPLIT);
-    k_coarse_split<<<b.total_ctas, SP_THREADS, 0, c.stream>>>(b, Zhi, Zlo);
+    k_coarse_split<<<b.total_ctas, SP_THREADS, bytes, c.stream>>>(b, Zhi, Zlo, cap);
     return check_launch();
 }
 
