@@ -6,12 +6,12 @@
 // positive band f_k = k f_s / N): the band-limited circular advance of each range profile
 // by delta bins.  Two kernels, both one persistent CTA per row at a time
 // with the N samples in shared memory:
-//   k_range_fft  forward radix-2 decimation in frequency of each pulse row; the spectrum is
-//                stored in bit-reversed order (nothing is permuted);
+//   k_range_fft  forward decimation in frequency of each pulse row; the spectrum is stored
+//                in bit-reversed order (nothing is permuted);
 //   k_rm_fd      per (cell, pulse): the spectrum times the ramp exp(j 2 pi k frac(delta) / N)
 //                (two small per-row tables: a coarse and a fine factor, plus exp(-j pi f)),
-//                inverse radix-2 decimation in time from the bit-reversed order to natural
-//                order, then the integer part of delta as an index offset when the range
+//                inverse decimation in time from the bit-reversed order to natural order,
+//                then the integer part of delta as an index offset when the range
 //                window [r0_begin, r0_begin + r0_count) is written (times w_c and 1/N).
 // Twiddles (one table per stage span) are built once per CTA with sincospif; the
 // transforms are those of fft_smem.cuh.
@@ -23,26 +23,26 @@ namespace {
 
 constexpr int FD_THREADS = 512;
 
-__global__ __launch_bounds__(FD_THREADS) void k_range_fft(const float2 *__restrict__ echo, int M, int N,
+__global__ __launch_bounds__(FD_THREADS, 2) void k_range_fft(const float2 *__restrict__ echo, int M, int N,
                                                         int logN, float2 *__restrict__ S) {
     extern __shared__ float2 fd_smem[];
-    float2 *x = fd_smem, *tw = fd_smem + N;
+    float2 *x = fd_smem, *tw = fd_smem + fft_padded(N);      // x padded (fft_smem.cuh)
     build_twiddles<FD_THREADS>(tw, N);
     for (int m = blockIdx.x; m < M; m += gridDim.x) {
         __syncthreads();
-        for (int n = threadIdx.x; n < N; n += FD_THREADS) x[n] = __ldg(echo + (long)m * N + n);
+        for (int n = threadIdx.x; n < N; n += FD_THREADS) x[fpad(n)] = __ldg(echo + (long)m * N + n);
         __syncthreads();
-        fft_dif_fwd<FD_THREADS>(x, 1, N, tw, logN);
-        for (int p = threadIdx.x; p < N; p += FD_THREADS) S[(long)m * N + p] = x[p];   // bit-reversed order
+        fft_dif_fwd<FD_THREADS, 3>(x, 1, fft_padded(N), tw, logN);
+        for (int p = threadIdx.x; p < N; p += FD_THREADS) S[(long)m * N + p] = x[fpad(p)];   // bit-reversed order
     }
 }
 
-__global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
+__global__ __launch_bounds__(FD_THREADS, 2) void k_rm_fd(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
                                                     int logN, int positive, const float2 *__restrict__ S,
                                                     const float2 *__restrict__ w_c, float2 *__restrict__ Z) {
     extern __shared__ float2 fd_smem[];
     const int N = R.N;
-    float2 *x = fd_smem, *tw = fd_smem + N;
+    float2 *x = fd_smem, *tw = fd_smem + fft_padded(N);      // x padded (fft_smem.cuh)
     __shared__ float2 s_hi[128], s_lo[64];     // ramp factors exp(j 2 pi u f / N), u = 64 u_hi + u_lo
     __shared__ long s_I;                        // integer advance of the row
     __shared__ float s_f;                       // fractional advance of the row
@@ -83,24 +83,24 @@ __global__ __launch_bounds__(FD_THREADS) void k_rm_fd(RadarD R, grft_dsgrid g, i
             const int k = (int)brev_bits((unsigned)p, logN);        // natural frequency of slot p
             const int u = positive ? k : (k < N / 2 ? k + N / 2 : k - N / 2);   // positive: k; else signed k + N/2
             const float2 ramp = cmul(c0, cmul(s_hi[u >> 6], s_lo[u & 63]));
-            x[p] = cmul(__ldg(Sm + p), ramp);
+            x[fpad(p)] = cmul(__ldg(Sm + p), ramp);
         }
         __syncthreads();
-        fft_dit_inv<FD_THREADS>(x, 1, N, tw, logN);
+        fft_dit_inv<FD_THREADS>(x, 1, fft_padded(N), tw, logN);
         const float2 wm = w_c[(long)cl * R.M + m];
         const float2 sc = make_float2(wm.x * inv_n, wm.y * inv_n);
         float2 *zrow = Z + row * g.r0_count;
         for (int j = threadIdx.x; j < g.r0_count; j += FD_THREADS) {
             long n = ((long)g.r0_begin + j + I) % N;
             if (n < 0) n += N;
-            zrow[j] = cmul(x[n], sc);
+            zrow[j] = cmul(x[fpad((int)n)], sc);
         }
     }
 }
 
 }  // namespace
 
-size_t fd_smem_bytes(int N) { return 2 * (size_t)N * sizeof(float2); }
+size_t fd_smem_bytes(int N) { return ((size_t)fft_padded(N) + N) * sizeof(float2); }
 
 int launch_range_fft(const Ctx &c, const RadarD &R, const float2 *echo, float2 *S) {
     int logN = 0;

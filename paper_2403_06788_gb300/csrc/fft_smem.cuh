@@ -1,8 +1,13 @@
-// Transforms of power-of-two length over complex FP32 data in shared memory, done by a
-// whole CTA of NT threads (every thread calls; each pass ends in __syncthreads): radix-4
-// passes of two radix-2 stages each, plus one radix-2 stage when log2 n is odd.  `cols`
-// transforms of the same length, stride `ld` apart, run together: one barrier per pass for
-// all of them.
+// Transforms of power-of-two length over complex FP32 data in shared memory, done by a whole
+// CTA of NT threads (every thread calls).  The radix-2 stages are taken MAXNS (4, or 3 to
+// halve the registers) at a time: a thread loads the 2^MAXNS elements that those stages
+// combine, runs the stages in registers and stores them back, so a length-2^L transform
+// costs ceil(L / MAXNS) passes, each ending in one __syncthreads.  `cols` transforms of the
+// same length, `ld` elements apart, run together.
+//
+// Layout: element e of a column sits at column offset fpad(e) = e + e/16 (one unused slot
+// after every 16), so that in the first pass, where a thread reads 2^MAXNS consecutive
+// elements, the lanes of a half-warp fall on distinct banks; `ld` >= fft_padded(n).
 #pragma once
 
 #include "internal.cuh"
@@ -15,9 +20,12 @@ __device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y
 
 __device__ __forceinline__ unsigned brev_bits(unsigned x, int bits) { return bits ? __brev(x) >> (32 - bits) : 0u; }
 
+__host__ __device__ __forceinline__ int fpad(int e) { return e + (e >> 4); }
+__host__ __device__ constexpr int fft_padded(int n) { return n + (n >> 4); }
+
 // Twiddles laid out per stage span: the butterflies of span h read tw[h + r] =
-// exp(+j pi r / h), r < h, so consecutive butterflies read consecutive words (no bank
-// conflicts, unlike one table read at stride n / 2h).  n entries serve every length <= n.
+// exp(+j pi r / h), r < h, so consecutive butterflies read consecutive words.  n entries
+// serve every length <= n.  (Unpadded.)
 template <int NT>
 __device__ __forceinline__ void build_twiddles(float2 *tw, int n) {
     for (int t = threadIdx.x; t < n; t += NT) {
@@ -32,88 +40,80 @@ __device__ __forceinline__ void build_twiddles(float2 *tw, int n) {
     }
 }
 
-// Forward decimation in frequency, in place: natural order in, bit-reversed order out
-// (exponent -).  Radix-2 stage of span h = 2^lh: butterfly b pairs i = (b >> lh) 2h +
-// (b & (h - 1)) with i + h, then multiplies the difference by conj(tw[h + r]).  Two
-// consecutive stages (spans h, h/2) run as one radix-4 pass over the quad
-// i, i + h/2, i + h, i + 3h/2 (one barrier per pass); a leading radix-2 stage when log2 n
-// is odd.
-template <int NT>
-__device__ __forceinline__ void fft_dif_fwd(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    const int half = 1 << (logn - 1);
-    int lh = logn - 1;
-    if (logn & 1) {                             // radix-2 stage of span n/2
-        const int h = 1 << lh;
-        for (int t = threadIdx.x; t < cols * half; t += NT) {
-            const int col = t >> (logn - 1), b = t & (half - 1);
-            float2 *xc = x + (long)col * ld;
-            const float2 u = xc[b], v = xc[b + h];
-            xc[b] = cadd2(u, v);
-            xc[b + h] = cmul(csub2(u, v), conj2(tw[h + b]));
+// One pass of NS (<= 4) radix-2 stages with spans h0, 2 h0, .., h0 2^(NS-1), h0 = 2^s0.
+// Group g of a column holds the elements i0 + h0 q, q < 2^NS, with r0 = g mod h0 and
+// i0 = (g / h0) 2^NS h0 + r0; the butterfly of span h = h0 2^u pairs q and q + 2^u (bit u
+// of q clear) and takes the twiddle of r = r0 + h0 (q mod 2^u).
+//   DIF (forward, exponent -): stages in decreasing span; (a, b) -> (a + b, (a - b) conj(w)).
+//   DIT (inverse, exponent +): stages in increasing span; b w, then (a + b w, a - b w).
+template <int NT, int NS, bool DIF>
+__device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const float2 *tw, int logn, int s0) {
+    constexpr int G = 1 << NS;
+    const int h0 = 1 << s0;
+    const int lper = logn - NS;                 // log2 of the groups per column
+    for (int t = threadIdx.x; t < (cols << lper); t += NT) {
+        const int col = t >> lper, g = t & ((1 << lper) - 1);
+        float2 *xc = x + (long)col * ld;
+        const int r0 = g & (h0 - 1);
+        const int i0 = ((g >> s0) << (s0 + NS)) + r0;
+        float2 v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) v[q] = xc[fpad(i0 + (q << s0))];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int u = DIF ? NS - 1 - k : k;
+            const int h = h0 << u;
+            float2 w[G / 2];
+#pragma unroll
+            for (int a = 0; a < (1 << u); ++a) w[a] = tw[h + r0 + (a << s0)];
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                if (q & (1 << u)) continue;
+                const float2 a = v[q], b = v[q + (1 << u)];
+                const float2 wq = w[q & ((1 << u) - 1)];
+                if (DIF) {
+                    v[q] = cadd2(a, b);
+                    v[q + (1 << u)] = cmul(csub2(a, b), conj2(wq));
+                } else {
+                    const float2 y = cmul(b, wq);
+                    v[q] = cadd2(a, y);
+                    v[q + (1 << u)] = csub2(a, y);
+                }
+            }
         }
-        __syncthreads();
-        --lh;
-    }
-    if (logn < 2) return;
-    const int quarter = 1 << (logn - 2);
-    for (; lh >= 1; lh -= 2) {                  // spans h = 2^lh and h/2
-        const int h = 1 << lh, g = h >> 1;
-        for (int t = threadIdx.x; t < cols * quarter; t += NT) {
-            const int col = t >> (logn - 2), b = t & (quarter - 1);
-            float2 *xc = x + (long)col * ld;
-            const int r = b & (g - 1), i = ((b >> (lh - 1)) << (lh + 1)) + r;
-            const float2 x0 = xc[i], x1 = xc[i + g], x2 = xc[i + h], x3 = xc[i + h + g];
-            const float2 a0 = cadd2(x0, x2), a2 = cmul(csub2(x0, x2), conj2(tw[h + r]));
-            const float2 a1 = cadd2(x1, x3), a3 = cmul(csub2(x1, x3), conj2(tw[h + r + g]));
-            const float2 wg = conj2(tw[g + r]);
-            xc[i] = cadd2(a0, a1);
-            xc[i + g] = cmul(csub2(a0, a1), wg);
-            xc[i + h] = cadd2(a2, a3);
-            xc[i + h + g] = cmul(csub2(a2, a3), wg);
-        }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < G; ++q) xc[fpad(i0 + (q << s0))] = v[q];
     }
 }
 
-// Inverse decimation in time, in place: bit-reversed order in, natural order out
-// (exponent +, unscaled).  Radix-2 stage of span h: x[i + h] is multiplied by tw[h + r]
-// before the butterfly.  Stages h, 2h run as one radix-4 pass over i, i + h, i + 2h, i + 3h;
-// a trailing radix-2 stage when log2 n is odd.
-template <int NT>
+template <int NT, bool DIF, int MAXNS>
+__device__ __forceinline__ void fft_pass_any(float2 *x, int cols, int ld, const float2 *tw, int logn, int s0) {
+    switch (logn - s0 < MAXNS ? logn - s0 : MAXNS) {
+        case 4: if constexpr (MAXNS >= 4) fft_pass<NT, 4, DIF>(x, cols, ld, tw, logn, s0); break;
+        case 3: fft_pass<NT, 3, DIF>(x, cols, ld, tw, logn, s0); break;
+        case 2: fft_pass<NT, 2, DIF>(x, cols, ld, tw, logn, s0); break;
+        default: fft_pass<NT, 1, DIF>(x, cols, ld, tw, logn, s0); break;
+    }
+    __syncthreads();
+}
+
+// Forward decimation in frequency, in place: natural order in, bit-reversed order out
+// (exponent -).  Passes of up to MAXNS (3 or 4) stages from the largest spans down (MAXNS 3
+// halves the registers a thread holds).
+template <int NT, int MAXNS = 4>
+__device__ __forceinline__ void fft_dif_fwd(float2 *x, int cols, int ld, const float2 *tw, int logn) {
+    static_assert(MAXNS == 3 || MAXNS == 4, "stages per pass");
+    if (logn < 1) return;
+    for (int s0 = ((logn - 1) / MAXNS) * MAXNS; s0 >= 0; s0 -= MAXNS)
+        fft_pass_any<NT, true, MAXNS>(x, cols, ld, tw, logn, s0);
+}
+
+// Inverse decimation in time, in place: bit-reversed order in, natural order out (exponent
+// +, unscaled).  Passes of up to MAXNS stages from span 1 up.
+template <int NT, int MAXNS = 4>
 __device__ __forceinline__ void fft_dit_inv(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    const int half = 1 << (logn - 1);
-    int lh = 0;
-    if (logn >= 2) {
-        const int quarter = 1 << (logn - 2);
-        for (; lh + 1 < logn; lh += 2) {        // spans h = 2^lh and 2h
-            const int h = 1 << lh, h2 = h << 1;
-            for (int t = threadIdx.x; t < cols * quarter; t += NT) {
-                const int col = t >> (logn - 2), b = t & (quarter - 1);
-                float2 *xc = x + (long)col * ld;
-                const int r = b & (h - 1), i = ((b >> lh) << (lh + 2)) + r;
-                const float2 wh = tw[h + r];
-                const float2 x0 = xc[i], x1 = cmul(xc[i + h], wh), x2 = xc[i + h2], x3 = cmul(xc[i + h2 + h], wh);
-                const float2 a0 = cadd2(x0, x1), a1 = csub2(x0, x1), a2 = cadd2(x2, x3), a3 = csub2(x2, x3);
-                const float2 b2 = cmul(a2, tw[h2 + r]), b3 = cmul(a3, tw[h2 + r + h]);
-                xc[i] = cadd2(a0, b2);
-                xc[i + h2] = csub2(a0, b2);
-                xc[i + h] = cadd2(a1, b3);
-                xc[i + h2 + h] = csub2(a1, b3);
-            }
-            __syncthreads();
-        }
-    }
-    if (lh < logn) {                            // radix-2 stage of span n/2
-        const int h = 1 << lh;
-        for (int t = threadIdx.x; t < cols * half; t += NT) {
-            const int col = t >> (logn - 1), b = t & (half - 1);
-            float2 *xc = x + (long)col * ld;
-            const float2 u = xc[b], v = cmul(xc[b + h], tw[h + b]);
-            xc[b] = cadd2(u, v);
-            xc[b + h] = csub2(u, v);
-        }
-        __syncthreads();
-    }
+    static_assert(MAXNS == 3 || MAXNS == 4, "stages per pass");
+    for (int s0 = 0; s0 < logn; s0 += MAXNS) fft_pass_any<NT, false, MAXNS>(x, cols, ld, tw, logn, s0);
 }
 
 }  // namespace grft

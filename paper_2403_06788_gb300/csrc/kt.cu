@@ -61,14 +61,14 @@ __device__ __forceinline__ float2 kt_chirp(int x, int logM, float2 eps) {
     return make_float2(c, s);
 }
 
-__global__ __launch_bounds__(KT_THREADS) void k_keystone(const float2 *__restrict__ S, int M, int N, int logM,
+__global__ __launch_bounds__(KT_THREADS, 2) void k_keystone(const float2 *__restrict__ S, int M, int N, int logM,
                                                        int logN, int cols, double lam_2ndr,
                                                        float2 *__restrict__ Skt) {
     extern __shared__ float2 kt_smem[];
-    const int P = 2 * M, logP = logM + 1;
-    float2 *b0 = kt_smem;                       // [cols][P]: Doppler spectrum, then the chirp kernel
-    float2 *b1 = kt_smem + (long)cols * P;      // [cols][P]: chirped spectrum, then the product
-    float2 *tw = kt_smem + 2L * cols * P;       // [P]
+    const int P = 2 * M, logP = logM + 1, Pp = fft_padded(P);   // columns padded (fft_smem.cuh)
+    float2 *b0 = kt_smem;                       // [cols][Pp]: Doppler spectrum, then the chirp kernel
+    float2 *b1 = kt_smem + (long)cols * Pp;     // [cols][Pp]: chirped spectrum, then the product
+    float2 *tw = kt_smem + 2L * cols * Pp;      // [P]
     __shared__ float2 s_eps[4];                 // eps of each column as an FP32 pair (hi, lo)
     build_twiddles<KT_THREADS>(tw, P);
     const float scale = 1.0f / (float)((long)M * P);          // exact: a power of two
@@ -83,47 +83,50 @@ __global__ __launch_bounds__(KT_THREADS) void k_keystone(const float2 *__restric
         }
         for (int t = threadIdx.x; t < cols * M; t += KT_THREADS) {
             const int col = t % cols, m = t / cols;
-            b0[(long)col * P + m] = __ldg(S + (long)m * N + p0 + col);
+            b0[(long)col * Pp + fpad(m)] = __ldg(S + (long)m * N + p0 + col);
         }
         __syncthreads();
-        fft_dif_fwd<KT_THREADS>(b0, cols, P, tw, logM);       // Y[l] at b0[bitrev_M(l mod M)]
+        fft_dif_fwd<KT_THREADS, 3>(b0, cols, Pp, tw, logM);      // Y[l] at b0[bitrev_M(l mod M)]
         for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) {
             const int col = t >> logP, i = t & (P - 1);
             float2 v = make_float2(0.f, 0.f);
             if (i < M) {
                 const int l = i - M / 2;
                 const int at = (int)brev_bits((unsigned)(l & (M - 1)), logM);
-                v = cmul(b0[(long)col * P + at], kt_chirp(l, logM, s_eps[col]));
+                v = cmul(b0[(long)col * Pp + fpad(at)], kt_chirp(l, logM, s_eps[col]));
             }
-            b1[t] = v;
+            b1[(long)col * Pp + fpad(i)] = v;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) {
             const int col = t >> logP, e = t & (P - 1);
             float2 g = make_float2(0.f, 0.f);                  // e = M: never used by the convolution
             if (e != M) g = conj2(kt_chirp((e < M ? e : e - P) + M / 2, logM, s_eps[col]));
-            b0[t] = g;
+            b0[(long)col * Pp + fpad(e)] = g;
         }
         __syncthreads();
-        fft_dif_fwd<KT_THREADS>(kt_smem, 2 * cols, P, tw, logP);   // kernel and sequence together
-        for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) b1[t] = cmul(b0[t], b1[t]);
+        fft_dif_fwd<KT_THREADS, 3>(kt_smem, 2 * cols, Pp, tw, logP);  // kernel and sequence together
+        for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) {
+            const long o = (long)(t >> logP) * Pp + fpad(t & (P - 1));
+            b1[o] = cmul(b0[o], b1[o]);
+        }
         __syncthreads();
-        fft_dit_inv<KT_THREADS>(b1, cols, P, tw, logP);
+        fft_dit_inv<KT_THREADS, 3>(b1, cols, Pp, tw, logP);
         for (int t = threadIdx.x; t < cols * M; t += KT_THREADS) {
             const int col = t % cols, m = t / cols;
-            const float2 v = cmul(b1[(long)col * P + m], kt_chirp(m, logM, s_eps[col]));
+            const float2 v = cmul(b1[(long)col * Pp + fpad(m)], kt_chirp(m, logM, s_eps[col]));
             Skt[(long)m * N + p0 + col] = make_float2(v.x * scale, v.y * scale);
         }
     }
 }
 
-__global__ __launch_bounds__(KT_THREADS) void k_rm_kt(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
+__global__ __launch_bounds__(KT_THREADS, 2) void k_rm_kt(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
                                                     int logN, double lam_2ndr, const float2 *__restrict__ Skt,
                                                     float2 *__restrict__ Z) {
     extern __shared__ float2 kt_smem[];
     const int N = R.N;
-    float2 *x = kt_smem, *tw = kt_smem + N;
-    float *E = (float *)(kt_smem + 2L * N);    // E[p] = k_s eps_k / N
+    float2 *x = kt_smem, *tw = kt_smem + fft_padded(N);     // x padded (fft_smem.cuh)
+    float *E = (float *)(tw + N);               // E[p] = k_s eps_k / N
     __shared__ long s_I;                        // integer advance of the row
     __shared__ float s_f, s_d1;                 // fractional advance, delta1
     __shared__ float2 s_w;                      // H_pre-DFM of the row
@@ -163,16 +166,16 @@ __global__ __launch_bounds__(KT_THREADS) void k_rm_kt(RadarD R, grft_dsgrid g, i
             const float phi = fmaf(E[p], d1, (float)ks * f * inv_n);
             float sn, cs;
             sincospif(2.0f * phi, &sn, &cs);
-            x[p] = cmul(__ldg(Sm + p), make_float2(cs, sn));
+            x[fpad(p)] = cmul(__ldg(Sm + p), make_float2(cs, sn));
         }
         __syncthreads();
-        fft_dit_inv<KT_THREADS>(x, 1, N, tw, logN);
+        fft_dit_inv<KT_THREADS>(x, 1, fft_padded(N), tw, logN);
         const float2 sc = make_float2(s_w.x * inv_n, s_w.y * inv_n);
         float2 *zrow = Z + row * g.r0_count;
         for (int j = threadIdx.x; j < g.r0_count; j += KT_THREADS) {
             long n = ((long)g.r0_begin + j + I) % N;
             if (n < 0) n += N;
-            zrow[j] = cmul(x[n], sc);
+            zrow[j] = cmul(x[fpad((int)n)], sc);
         }
     }
 }
@@ -187,9 +190,11 @@ int ilog2_exact(int n) {
 
 int kt_columns(int M) { return M <= 1024 ? 4 : 2; }
 
-size_t kt_smem_bytes(int M) { return (size_t)(2 * kt_columns(M) + 1) * 2 * M * sizeof(float2); }
+size_t kt_smem_bytes(int M) {
+    return ((size_t)2 * kt_columns(M) * fft_padded(2 * M) + 2 * (size_t)M) * sizeof(float2);
+}
 
-size_t rm_kt_smem_bytes(int N) { return (size_t)N * 2 * sizeof(float2) + (size_t)N * sizeof(float); }
+size_t rm_kt_smem_bytes(int N) { return ((size_t)fft_padded(N) + N) * sizeof(float2) + (size_t)N * sizeof(float); }
 
 static int kt_set_attributes(const Ctx &c) {
     static bool done[64] = {false};

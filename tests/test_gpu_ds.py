@@ -115,6 +115,19 @@ def test_ds_fine_grid_padding_and_single_cell(cuda_lib):
         assert rel_peak_err(Y.cpu().numpy(), oracle.dsgrft_full(R, s, ds)) <= TOL[prec]
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x1"])
+def test_ds_long_cpi_tables_from_global_memory(cuda_lib, precision):
+    """M = 2100 pulses: more than the operand-split kernel stages in shared memory (2048), so it
+    reads the cell's bins and phases from global memory; 66 pulse stages, the last partial."""
+    g = cuda_lib
+    R, ds, s = _small_case(M=2100, N=400, r0b=5, r0c=260, Fv=4, Fa=2, nvc=2, nac=1, seed=6)
+    es = torch.from_numpy(s).cuda()
+    Y = g.dsgrft(R, es, ds, precision=precision, want_Y=True, want_P=False)
+    assert g.grft_sync_status() == 0
+    err = rel_peak_err(Y.cpu().numpy(), oracle.dsgrft_full(R, s, ds))
+    assert err <= TOL[precision] and err <= (1e-4 if precision == "bf16x3" else 5e-4), err
+
+
 def test_ds_full_ds_m512_sampled(cuda_lib):
     """ds_m512 at full size (2^30 hypotheses) in the launch configuration the benchmark times,
     compared with the oracle on sampled rows (every r0 of 24 (v, a) rows, incl. targets)."""
