@@ -44,6 +44,7 @@ __global__ __launch_bounds__(FD_THREADS, 2) void k_rm_fd(RadarD R, grft_dsgrid g
     const int N = R.N;
     float2 *x = fd_smem, *tw = fd_smem + fft_padded(N);      // x padded (fft_smem.cuh)
     __shared__ float2 s_hi[128], s_lo[64];     // ramp factors exp(j 2 pi u f / N), u = 64 u_hi + u_lo
+    const int lhi = logN > 6 ? logN - 6 : 0;    // bits of u_hi
     __shared__ long s_I;                        // integer advance of the row
     __shared__ float s_f;                       // fractional advance of the row
     build_twiddles<FD_THREADS>(tw, N);
@@ -66,9 +67,10 @@ __global__ __launch_bounds__(FD_THREADS, 2) void k_rm_fd(RadarD R, grft_dsgrid g
         const float f = s_f;
         for (int u = threadIdx.x; u < 128 + 64; u += FD_THREADS) {
             float sn, cs;
-            if (u < 128) {
+            if (u < 128) {                      // stored at the bit-reversed position (see below)
+                if (u >= (1 << lhi)) continue;
                 sincospif(2.0f * (float)(64 * u) * f / (float)N, &sn, &cs);
-                s_hi[u] = make_float2(cs, sn);
+                s_hi[brev_bits((unsigned)u, lhi)] = make_float2(cs, sn);
             } else {
                 sincospif(2.0f * (float)(u - 128) * f / (float)N, &sn, &cs);
                 s_lo[u - 128] = make_float2(cs, sn);
@@ -82,7 +84,10 @@ __global__ __launch_bounds__(FD_THREADS, 2) void k_rm_fd(RadarD R, grft_dsgrid g
         for (int p = threadIdx.x; p < N; p += FD_THREADS) {
             const int k = (int)brev_bits((unsigned)p, logN);        // natural frequency of slot p
             const int u = positive ? k : (k < N / 2 ? k + N / 2 : k - N / 2);   // positive: k; else signed k + N/2
-            const float2 ramp = cmul(c0, cmul(s_hi[u >> 6], s_lo[u & 63]));
+            // u >> 6 is the bit reversal of the low lhi bits of p (up to the top bit the
+            // baseband offset flips), so the table slot brev(u >> 6) is consecutive over a
+            // warp's slots: conflict-free; u & 63 is the same for the whole warp (broadcast)
+            const float2 ramp = cmul(c0, cmul(s_hi[brev_bits((unsigned)(u >> 6), lhi)], s_lo[u & 63]));
             x[fpad(p)] = cmul(__ldg(Sm + p), ramp);
         }
         __syncthreads();
@@ -91,9 +96,8 @@ __global__ __launch_bounds__(FD_THREADS, 2) void k_rm_fd(RadarD R, grft_dsgrid g
         const float2 sc = make_float2(wm.x * inv_n, wm.y * inv_n);
         float2 *zrow = Z + row * g.r0_count;
         for (int j = threadIdx.x; j < g.r0_count; j += FD_THREADS) {
-            long n = ((long)g.r0_begin + j + I) % N;
-            if (n < 0) n += N;
-            zrow[j] = cmul(x[fpad((int)n)], sc);
+            const int n = (int)(((long)g.r0_begin + j + I) & (N - 1));   // mod N (a power of two)
+            zrow[j] = cmul(x[fpad(n)], sc);
         }
     }
 }

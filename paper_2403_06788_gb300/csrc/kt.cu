@@ -173,9 +173,8 @@ __global__ __launch_bounds__(KT_THREADS, 2) void k_rm_kt(RadarD R, grft_dsgrid g
         const float2 sc = make_float2(s_w.x * inv_n, s_w.y * inv_n);
         float2 *zrow = Z + row * g.r0_count;
         for (int j = threadIdx.x; j < g.r0_count; j += KT_THREADS) {
-            long n = ((long)g.r0_begin + j + I) % N;
-            if (n < 0) n += N;
-            zrow[j] = cmul(x[fpad((int)n)], sc);
+            const int n = (int)(((long)g.r0_begin + j + I) & (N - 1));   // mod N (a power of two)
+            zrow[j] = cmul(x[fpad(n)], sc);
         }
     }
 }
