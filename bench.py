@@ -124,22 +124,23 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(pw)}
 
 
-def _cpu_oracle_sample(sc, s, target_s: float, warm_rows: int = 8):
-    """Time the FP64 oracle on (cell, fine) rows of the DS grid, every r0 and pulse."""
+def _cpu_oracle_sample(sc, s, target_s: float, warm_rows: int = 8, threads: int = 0):
+    """Time the FP64 oracle on (cell, fine) rows of the DS grid, every r0 and pulse, on
+    `threads` host threads (0: all)."""
     import oracle
     ds = sc.ds
-    nthreads = oracle.num_threads()
+    nthreads = threads if threads > 0 else oracle.num_threads()
     rng = np.random.default_rng(0)
     def rows(n):
         return rng.integers(0, ds.n_cells, n), rng.integers(0, ds.n_fine, n)
     c, f = rows(max(warm_rows, nthreads))
     t0 = time.perf_counter()
-    oracle.dsgrft_rows(sc.radar, s, ds, c, f)
+    oracle.dsgrft_rows(sc.radar, s, ds, c, f, nthreads=threads)
     rate = c.size / (time.perf_counter() - t0)
     n = int(max(nthreads, min(200000, rate * target_s)))
     c, f = rows(n)
     t0 = time.perf_counter()
-    oracle.dsgrft_rows(sc.radar, s, ds, c, f)
+    oracle.dsgrft_rows(sc.radar, s, ds, c, f, nthreads=threads)
     dt = time.perf_counter() - t0
     units = n * ds.r0_count * sc.radar.M
     return units / dt, nthreads, n, dt
@@ -814,8 +815,11 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, cores, n, dt = _cpu_oracle_sample(sc, s, target_s=args.cpu_seconds)
+        v1, _, n1, dt1 = _cpu_oracle_sample(sc, s, target_s=args.cpu_seconds / 3, warm_rows=2, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} (cell, fine) rows of the same DS grid x 4096 r0 x 512 pulses ({dt:.1f} s)"}
+               "sample": f"{n} (cell, fine) rows of the same DS grid x 4096 r0 x 512 pulses ({dt:.1f} s)",
+               "value_1core": v1,
+               "sample_1core": f"{n1} rows on one host thread ({dt1:.1f} s)"}
 
     if rank != 0:
         if world > 1:

@@ -75,21 +75,28 @@ static inline cplx echo_at(const float *s, const orc_radar *R, int m, long n) {
     return z;
 }
 
+/* Thread count of a call: nthreads > 0 as given, else the process default (the OpenMP
+ * maximum seen before any call set a count), so that a one-thread call does not pin the
+ * later ones. */
+static int default_threads(void) {
+#ifdef _OPENMP
+    static int d = 0;
+    if (d == 0) d = omp_get_max_threads();
+    return d;
+#else
+    return 1;
+#endif
+}
+
 static void set_threads(int nthreads) {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads > 0 ? nthreads : default_threads());
 #else
     (void)nthreads;
 #endif
 }
 
-int orc_num_threads(void) {
-#ifdef _OPENMP
-    return omp_get_max_threads();
-#else
-    return 1;
-#endif
-}
+int orc_num_threads(void) { return default_threads(); }
 
 /* Bin shifts and phases for explicit (v, a) pairs: rho[h][m], w[h][m] = exp(j4pi d/lambda). */
 int orc_bins_phases(const orc_radar *R, const double *v, const double *a, int nh, int32_t *rho,
