@@ -909,7 +909,7 @@ int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
 
 int launch_round_gemm(const Ctx &c, const Round &rd, int Mpad, int Fpad, const uint16_t *Bhi,
                       const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
-    if (variant < 0) {   // autotune: time the tile shapes on this round, keep the fastest
+    if (variant < 0) {   // autotune: time the tile shapes on this round of cells, keep the fastest
         variant = tune_variant(c, rd.b, [&](int v) {
             return launch_gemm_variant(v, c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Fpad);
         });
