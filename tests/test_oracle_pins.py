@@ -342,6 +342,26 @@ def test_ds_equals_grft_wherever_coarse_and_full_bins_agree():
     assert same >= 10
 
 
+def test_ds_at_zero_fine_offset_is_grft_at_the_cell_centre():
+    """Fine offset k = Fv/2, q = Fa/2 is zero (half-open fine grid), so DS-GRFT there sums
+    the same bins and phases as plain GRFT at the coarse centre (v_c, a_c): the two oracles
+    must agree for every cell and every r0 (the exact form of DS reducing to GRFT on the
+    coarse grid)."""
+    sc = synth.plain_m64()
+    R = dataclasses.replace(sc.radar, M=48, N=160)
+    s = synth.make_echo(R, [Target(70.0, 150.0, -8.0, complex(2.0, 1.0))], 22)
+    ds = DSGrid(3, 150, Axis(-90.0, 75.0, 4), Axis(-15.0, 30.0, 2), 6, 4)
+    cells = np.arange(ds.n_cells)
+    fine = np.full(ds.n_cells, (ds.Fv // 2) * ds.Fa + ds.Fa // 2)
+    Yds = oracle.dsgrft_rows(R, s, ds, cells, fine)
+    centres = PlainGrid(ds.r0_begin, ds.r0_count, ds.vc, ds.ac)
+    Ypl = oracle.grft_plain_rows(R, s, centres, cells // ds.ac.count, cells % ds.ac.count)
+    np.testing.assert_allclose(Yds, Ypl, rtol=0, atol=1e-9 * np.abs(Ypl).max())
+    # and the DS-GRFT output differs from the centre's elsewhere (the fine phase is applied)
+    other = oracle.dsgrft_rows(R, s, ds, cells, np.zeros_like(fine))
+    assert np.abs(other - Ypl).max() > 1e-3 * np.abs(Ypl).max()
+
+
 # ---------------------------------------------------------------- P9: sinc target closed form
 def test_sinc_target_closed_form_at_truth():
     """Noiseless sinc target: at its true (n0, v, a) the gathered samples are
