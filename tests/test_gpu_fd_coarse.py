@@ -40,6 +40,22 @@ def test_fd_coarse_stage_every_output_small(cuda_lib):
     assert rel_peak_err(Zs.cpu().numpy(), Zo[3:5]) <= TOL_FP32
 
 
+@pytest.mark.parametrize("N", [128, 512, 1024, 2048])
+def test_fd_coarse_stage_every_output_all_pass_shapes(cuda_lib, N):
+    """Range lengths whose log2 leaves 3, 1, 2 and 3 stages for the last pass of the
+    shared-memory transforms (passes of up to four radix-2 stages), both bands."""
+    g = cuda_lib
+    R = Radar(M=24, N=N, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
+    ds = DSGrid(3, N - 9, Axis(-150.0, 100.0, 3), Axis(-10.0, 20.0, 1), 2, 1)
+    s = synth.make_echo(R, [Target(0.45 * N, -60.0, 4.0, complex(2.0, -1.0))], 40 + N % 97)
+    for band in ("baseband", "positive"):
+        Z = torch.zeros((ds.n_cells, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+        g.dsgrft_coarse_rm_fd_ex(R, torch.from_numpy(s).cuda(), ds, 0, ds.n_cells, band, Z)
+        assert g.grft_sync_status() == 0
+        Zo = oracle.coarse_rm_fd(R, s, ds, 0, ds.n_cells, band=band)
+        assert rel_peak_err(Z.cpu().numpy(), Zo) <= TOL_FP32, band
+
+
 @pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16x3", TOL_SPLIT)])
 def test_fd_then_fine_stage_matches_oracle_rows(cuda_lib, precision, tol):
     g = cuda_lib

@@ -73,6 +73,22 @@ def test_kt_coarse_stage_every_output(cuda_lib):
     assert rel_peak_err(Zs.cpu().numpy(), Zo[9:12]) <= TOL_FP32
 
 
+@pytest.mark.parametrize("N", [128, 1024])
+def test_kt_coarse_stage_every_output_all_pass_shapes(cuda_lib, N):
+    """Range lengths whose log2 leaves 3 and 2 stages for the last pass of the inverse
+    transform (passes of up to four radix-2 stages)."""
+    g = cuda_lib
+    R = Radar(M=32, N=N, fc_hz=1.0e9, prf_hz=500.0, dr_m=15.0)
+    ds = synth.kt_grid(R, -2, 3, Axis(-15.0, 10.0, 2), 2, r0_begin=5, r0_count=N - 11)
+    ykt = synth.make_noise((R.M, R.N), 43 + N % 89).astype(np.complex128)
+    Skt = torch.from_numpy(np.ascontiguousarray(ykt[:, _slots(g, R.N)].astype(np.complex64))).cuda()
+    Z = torch.empty((ds.n_cells, R.M, ds.r0_count), dtype=torch.complex64, device="cuda")
+    g.dskt_coarse_rm(R, Skt, ds, 0, ds.n_cells, Z)
+    assert g.grft_sync_status() == 0
+    Zo = oracle.kt_coarse_rm(R, ykt.astype(np.complex64), ds, 0, ds.n_cells)
+    assert rel_peak_err(Z.cpu().numpy(), Zo) <= TOL_FP32
+
+
 @pytest.mark.parametrize("L", [64, 128])
 def test_kt_fine_stage_every_output(cuda_lib, L):
     g = cuda_lib
