@@ -36,7 +36,7 @@ FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
 # the autotuner picks here) on the first 16 coarse cells (276.9 MB + 231.0 MB), scaled by
 # 16 to one launch of this workload (all 256 cells in one launch).  Reset to None whenever
 # that kernel changes.
-DRAM_TRAFFIC_PER_LAUNCH = 16 * (276.930048e6 + 231.043072e6)
+DRAM_TRAFFIC_PER_LAUNCH = 16 * (276.915712e6 + 230.874368e6)
 
 
 def _peaks():
