@@ -32,6 +32,7 @@ namespace grft {
 namespace {
 
 constexpr int KT_THREADS = 512;
+constexpr int KT_RPI = 2;                      // rows per iteration of k_rm_kt (N <= 4096)
 
 // eps = fbar - 1 of slot p in FP64.
 __device__ __forceinline__ double kt_eps(int p, int logN, int N, double lam_2ndr) {
@@ -121,27 +122,26 @@ __global__ __launch_bounds__(KT_THREADS, 2) void k_keystone(const float2 *__rest
 }
 
 __global__ __launch_bounds__(KT_THREADS, 2) void k_rm_kt(RadarD R, grft_dsgrid g, int cell_begin, int cell_count,
-                                                    int logN, double lam_2ndr, const float2 *__restrict__ Skt,
-                                                    float2 *__restrict__ Z) {
+                                                    int logN, double lam_2ndr, int rpi,
+                                                    const float2 *__restrict__ Skt, float2 *__restrict__ Z) {
+    // rpi (1 or KT_RPI) rows per iteration, their transforms run together (as in k_rm_fd)
     extern __shared__ float2 kt_smem[];
-    const int N = R.N;
-    float2 *x = kt_smem, *tw = kt_smem + fft_padded(N);     // x padded (fft_smem.cuh)
-    float *E = (float *)(tw + N);               // E[p] = k_s eps_k / N
-    __shared__ long s_I;                        // integer advance of the row
-    __shared__ float s_f, s_d1;                 // fractional advance, delta1
-    __shared__ float2 s_w;                      // H_pre-DFM of the row
+    const int N = R.N, Np = fft_padded(N);
+    float2 *x = kt_smem, *tw = kt_smem + (long)rpi * Np;     // rpi padded rows (fft_smem.cuh), twiddles
+    __shared__ long s_I[KT_RPI];                // integer advance of each row
+    __shared__ float s_f[KT_RPI], s_d1[KT_RPI]; // fractional advance, delta1
+    __shared__ float2 s_w[KT_RPI];              // H_pre-DFM of each row
+    __shared__ int s_m[KT_RPI];                 // pulse of each row
     build_twiddles<KT_THREADS>(tw, N);
-    for (int p = threadIdx.x; p < N; p += KT_THREADS) {
-        const int k = (int)brev_bits((unsigned)p, logN);
-        const int ks = k < N / 2 ? k : k - N;
-        E[p] = (float)__dmul_rn(__dmul_rn((double)ks, kt_eps(p, logN, N, lam_2ndr)), 1.0 / N);
-    }
     const long rows = (long)cell_count * R.M;
     const float inv_n = 1.0f / (float)N;        // exact: N a power of two
-    for (long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int cl = (int)(row / R.M), m = (int)(row - (long)cl * R.M);
-        __syncthreads();                        // previous row's reads of x and the row scalars are done
-        if (threadIdx.x == 0) {
+    const float l2n = (float)lam_2ndr;          // f_k / f_c per unit of k_s
+    for (long row0 = (long)blockIdx.x * rpi; row0 < rows; row0 += (long)gridDim.x * rpi) {
+        const int nr = (int)(rows - row0 < rpi ? rows - row0 : rpi);
+        __syncthreads();                        // the previous rows' reads of x and the row scalars are done
+        if (threadIdx.x < nr) {                 // one thread per row, FP64
+            const long row = row0 + threadIdx.x;
+            const int cl = (int)(row / R.M), m = (int)(row - (long)cl * R.M);
             const int c = cell_begin + cl;
             const double vq = axis_value(g.vc.start, g.vc.step, c / g.ac.count);
             const double ac = axis_value(g.ac.start, g.ac.step, c % g.ac.count);
@@ -150,31 +150,39 @@ __global__ __launch_bounds__(KT_THREADS, 2) void k_rm_kt(RadarD R, grft_dsgrid g
             const double q2 = displacement(0.0, ac, t);                    // c_2,c t^2
             const double D = __dsub_rn(d1, __ddiv_rn(q2, R.dr));
             const double fl = floor(D);
-            s_I = (long)fl;
-            s_f = (float)__dsub_rn(D, fl);
-            s_d1 = (float)d1;
-            s_w = range_phase(q2, R.lambda);
+            s_I[threadIdx.x] = (long)fl;
+            s_f[threadIdx.x] = (float)__dsub_rn(D, fl);
+            s_d1[threadIdx.x] = (float)d1;
+            s_w[threadIdx.x] = range_phase(q2, R.lambda);
+            s_m[threadIdx.x] = m;
         }
         __syncthreads();
-        const long I = s_I;
-        const float f = s_f, d1 = s_d1;
-        const float2 *Sm = Skt + (long)m * N;
-        for (int p = threadIdx.x; p < N; p += KT_THREADS) {
+        for (int tt = threadIdx.x; tt < (nr << logN); tt += KT_THREADS) {
+            const int r = tt >> logN, p = tt & (N - 1);
             const int k = (int)brev_bits((unsigned)p, logN);
             const int ks = k < N / 2 ? k : k - N;
+            // E_k = k_s eps_k / N with eps_k = fbar - 1 = -u / (1 + u), u = f_k / f_c (|u| < 1e-2):
+            // FP32 here; its relative error enters the phase as E_k delta1 (well under 1e-6 turns)
+            const float u = (float)ks * l2n;
+            const float E = (float)ks * __fdividef(-u, 1.0f + u) * inv_n;
             // turns of the ramp: k_s f / N (|.| <= 1/2) + the dispersive E_k delta1 (small)
-            const float phi = fmaf(E[p], d1, (float)ks * f * inv_n);
+            const float phi = fmaf(E, s_d1[r], (float)ks * s_f[r] * inv_n);
             float sn, cs;
             sincospif(2.0f * phi, &sn, &cs);
-            x[fpad(p)] = cmul(__ldg(Sm + p), make_float2(cs, sn));
+            x[(long)r * Np + fpad(p)] = cmul(__ldg(Skt + (long)s_m[r] * N + p), make_float2(cs, sn));
         }
         __syncthreads();
-        fft_dit_inv<KT_THREADS>(x, 1, fft_padded(N), tw, logN);
-        const float2 sc = make_float2(s_w.x * inv_n, s_w.y * inv_n);
-        float2 *zrow = Z + row * g.r0_count;
-        for (int j = threadIdx.x; j < g.r0_count; j += KT_THREADS) {
-            const int n = (int)(((long)g.r0_begin + j + I) & (N - 1));   // mod N (a power of two)
-            zrow[j] = cmul(x[fpad(n)], sc);
+        fft_dit_inv<KT_THREADS>(x, nr, Np, tw, logN);
+        for (int r = 0; r < nr; ++r) {
+            const long row = row0 + r;
+            const float2 sc = make_float2(s_w[r].x * inv_n, s_w[r].y * inv_n);
+            const long I = s_I[r];
+            const float2 *xr = x + (long)r * Np;
+            float2 *zrow = Z + row * g.r0_count;
+            for (int j = threadIdx.x; j < g.r0_count; j += KT_THREADS) {
+                const int n = (int)(((long)g.r0_begin + j + I) & (N - 1));   // mod N (a power of two)
+                zrow[j] = cmul(xr[fpad(n)], sc);
+            }
         }
     }
 }
@@ -193,7 +201,9 @@ size_t kt_smem_bytes(int M) {
     return ((size_t)2 * kt_columns(M) * fft_padded(2 * M) + 2 * (size_t)M) * sizeof(float2);
 }
 
-size_t rm_kt_smem_bytes(int N) { return ((size_t)fft_padded(N) + N) * sizeof(float2) + (size_t)N * sizeof(float); }
+// rpi padded rows and the twiddles
+size_t rm_kt_smem_bytes(int N, int rpi) { return ((size_t)rpi * fft_padded(N) + N) * sizeof(float2); }
+static int kt_rows_per_iter(int N) { return N <= 4096 ? KT_RPI : 1; }
 
 static int kt_set_attributes(const Ctx &c) {
     static bool done[64] = {false};
@@ -202,7 +212,7 @@ static int kt_set_attributes(const Ctx &c) {
         if (cudaFuncSetAttribute(k_keystone, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kt_smem_bytes(2048)) != cudaSuccess ||
             cudaFuncSetAttribute(k_rm_kt, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)rm_kt_smem_bytes(8192)) != cudaSuccess)
+                                 (int)rm_kt_smem_bytes(8192, 1)) != cudaSuccess)   // >= (4096, KT_RPI)
             return GRFT_ECUDA;
         done[c.device] = true;
     }
@@ -230,11 +240,14 @@ int launch_rm_kt(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int cell_b
     if (e) return e;
     const long rows = (long)cell_count * R.M;
     if (rows == 0) return GRFT_OK;
+    const int rpi = kt_rows_per_iter(R.N);
+    const long iters = (rows + rpi - 1) / rpi;
     const long cap = 2L * c.num_sms * 4;
-    const int grid = (int)(rows < cap ? rows : cap);
+    const int grid = (int)(iters < cap ? iters : cap);
     KernelTimer kt(c, GRFT_KERNEL_COARSE_RM);
-    k_rm_kt<<<grid, KT_THREADS, rm_kt_smem_bytes(R.N), c.stream>>>(R, g, cell_begin, cell_count, ilog2_exact(R.N),
-                                                                    lam_over_2ndr(R), Skt, Z);
+    k_rm_kt<<<grid, KT_THREADS, rm_kt_smem_bytes(R.N, rpi), c.stream>>>(R, g, cell_begin, cell_count,
+                                                                         ilog2_exact(R.N), lam_over_2ndr(R), rpi,
+                                                                         Skt, Z);
     return check_launch();
 }
 
