@@ -157,8 +157,9 @@ def run_reference(args):
     for _ in range(args.warmup):
         _cpu_oracle_sample(sc, s, target_s=1.0)
     vals, cores, nrows, tot = [], 0, 0, 0.0
+    step_s = min(args.ref_step_s, args.ref_total_s / max(1, args.steps))   # the whole run stays bounded
     for _ in range(args.steps):
-        v, cores, n, dt = _cpu_oracle_sample(sc, s, target_s=args.ref_step_s)
+        v, cores, n, dt = _cpu_oracle_sample(sc, s, target_s=step_s)
         vals.append(v)
         nrows += n
         tot += dt
@@ -583,13 +584,14 @@ def run_pd(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)   # about 0.5 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp16x1", "fp32"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--ref-total-s", type=float, default=120.0)
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline and accuracy check")
     ap.add_argument("--cells", type=int, default=0,
