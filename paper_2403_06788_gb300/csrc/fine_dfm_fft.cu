@@ -238,25 +238,40 @@ __global__ __launch_bounds__(GF_THREADS, STAGE ? 2 : 1) void k_gft_fft(
         // bin f = f1 + P f2 of this warp's range bin at 17 f2 + 560 f1 + warp
         if (jok) {
             const int base = 17 * f2 + warp;
-            const bool all = Fv == L;           // every bin kept (the keystone grid)
+            if (Fv == L) {                      // every bin kept (the keystone grid): no index test
+                if (out.Y) {
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                const int f1 = bitrev(i, ilog2(P));
-                int k = f1 + P * f2 + Fv / 2;   // kept index: f = (k - Fv/2) mod L
-                if (k >= L) k -= L;
-                if (all || k < Fv) {
-                    const int a = base + 560 * f1;
-                    if (out.Y)
-                        ((float2 *)gf_stage)[a] = cmul(ej, y[i]);
-                    else
-                        gf_stage[a] = y[i].x * y[i].x + y[i].y * y[i].y;
+                    for (int i = 0; i < P; ++i)
+                        ((float2 *)gf_stage)[base + 560 * bitrev(i, ilog2(P))] = cmul(ej, y[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < P; ++i)
+                        gf_stage[base + 560 * bitrev(i, ilog2(P))] = y[i].x * y[i].x + y[i].y * y[i].y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const int f1 = bitrev(i, ilog2(P));
+                    int k = f1 + P * f2 + Fv / 2;   // kept index: f = (k - Fv/2) mod L
+                    if (k >= L) k -= L;
+                    if (k < Fv) {
+                        const int a = base + 560 * f1;
+                        if (out.Y)
+                            ((float2 *)gf_stage)[a] = cmul(ej, y[i]);
+                        else
+                            gf_stage[a] = y[i].x * y[i].x + y[i].y * y[i].y;
+                    }
                 }
             }
         }
         __syncthreads();
         // write-out: thread (k0 = tid / 16, jj = tid % 16) stores bins k = k0, k0 + 32, ...
-        // of range bin j0 + jj: 16 consecutive threads write 64 contiguous bytes
+        // of range bin j0 + jj: 16 consecutive threads write 64 contiguous bytes.  The staged
+        // bin f = f1 + P f2 (f2 < 32) sits at 17 f2 + 560 f1 + jj; the loop steps f by KSTEP = 32,
+        // a multiple of P, so f1 = f mod P is fixed and f2 steps by 32 / P (mod 32).
         {
+            static_assert((GF_THREADS / GF_WARPS) % P == 0 && L / P == 32, "write-out steps whole f2 rows");
+            constexpr int F2STEP = (GF_THREADS / GF_WARPS) / P;
             const int jj = threadIdx.x & (GF_WARPS - 1), k0 = threadIdx.x / GF_WARPS;
             const int jo = j0 + jj;
             if (jo < r0_count) {
@@ -265,17 +280,20 @@ __global__ __launch_bounds__(GF_THREADS, STAGE ? 2 : 1) void k_gft_fft(
                 long o = ((long)(iv * Fv + k0) * na_full + (il * Fa + q)) * r0_count + jo;
                 int f = k0 - Fv / 2;
                 if (f < 0) f += L;
-                for (int k = k0; k < Fv; k += KSTEP, o += ostep) {
-                    const int a = 17 * (f / P) + 560 * (f % P) + jj;
-                    if (out.Y) {
-                        const float2 v = ((const float2 *)gf_stage)[a];
+                const int afix = 560 * (f % P) + jj;
+                int f2 = f / P;
+                if (out.Y) {
+                    for (int k = k0; k < Fv; k += KSTEP, o += ostep) {
+                        const float2 v = ((const float2 *)gf_stage)[afix + 17 * f2];
                         out.Y[o] = v;
                         if (out.P) out.P[o] = v.x * v.x + v.y * v.y;   // |e0 y|^2 = |y|^2 (|e0| = 1)
-                    } else {
-                        out.P[o] = gf_stage[a];
+                        f2 = (f2 + F2STEP) & 31;
                     }
-                    f += KSTEP;
-                    if (f >= L) f -= L;
+                } else {
+                    for (int k = k0; k < Fv; k += KSTEP, o += ostep) {
+                        out.P[o] = gf_stage[afix + 17 * f2];
+                        f2 = (f2 + F2STEP) & 31;
+                    }
                 }
             }
         }

@@ -47,6 +47,7 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     __shared__ alignas(16) float2 s_w[PL_MCHUNK][PL_H];     // w
     __shared__ alignas(16) float2 s_jw[PL_MCHUNK][PL_H];    // j w = (-w.im, w.re)
     __shared__ int s_same[PL_MCHUNK];            // every hypothesis of the group shifts like the first
+    __shared__ int s_rng[2];                     // least and greatest shift of the chunk
 
     const int h0 = blockIdx.y * PL_H;
     const int nhl = min(PL_H, nh - h0);
@@ -54,6 +55,7 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     // every load and store instruction of the warp is one contiguous 256-byte run)
     const int j0 = blockIdx.x * PL_TILE + (threadIdx.x >> 5) * (32 * PL_J) + (threadIdx.x & 31);
     const int n0 = r0_begin + j0;
+    const int n0_tile = r0_begin + blockIdx.x * PL_TILE;   // first bin of the CTA's tile
 
     uint64_t acc[PL_H][PL_J];                  // (re, im) pairs for the paired FMA
 #pragma unroll
@@ -73,21 +75,42 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
             s_w[mm][h] = wv;
             s_jw[mm][h] = make_float2(-wv.y, wv.x);
         }
-        __syncthreads();
-        if (threadIdx.x < PL_MCHUNK) {
-            int same = 1;
-#pragma unroll
-            for (int h = 1; h < PL_H; ++h) same &= s_rho[threadIdx.x][h] == s_rho[threadIdx.x][0];
-            s_same[threadIdx.x] = same;
+        if (threadIdx.x == 0) {
+            s_rng[0] = INT_MAX;
+            s_rng[1] = INT_MIN;
         }
         __syncthreads();
-        auto load_row = [&](int mm, int r, float2 (&v)[PL_J]) {
-            const float2 *row = echo + (long)(mc + mm) * N;
-            const int base = n0 + r;
+        if (threadIdx.x < PL_MCHUNK) {          // PL_MCHUNK <= PL_THREADS: one thread per pulse
+            int same = 1, lo = s_rho[threadIdx.x][0], hi = lo;
 #pragma unroll
-            for (int j = 0; j < PL_J; ++j) {
-                const int n = base + 32 * j;
-                v[j] = ((unsigned)n < (unsigned)N) ? __ldg(row + n) : make_float2(0.f, 0.f);
+            for (int h = 1; h < PL_H; ++h) {
+                const int r = s_rho[threadIdx.x][h];
+                same &= r == s_rho[threadIdx.x][0];
+                lo = min(lo, r);
+                hi = max(hi, r);
+            }
+            s_same[threadIdx.x] = same;
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&s_rng[0], lo);
+                atomicMax(&s_rng[1], hi);
+            }
+        }
+        __syncthreads();
+        // block-uniform: every gather of the tile's bins at every shift of the chunk is inside
+        // the echo (the unused table slots hold shift 0, which only widens the range)
+        const bool inside = n0_tile + s_rng[0] >= 0 && n0_tile + PL_TILE - 1 + s_rng[1] < N;
+        auto load_row = [&](int mm, int r, float2 (&v)[PL_J]) {
+            const float2 *row = echo + (long)(mc + mm) * N + (n0 + r);
+            if (inside) {
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j) v[j] = __ldg(row + 32 * j);
+            } else {
+                const int base = n0 + r;
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j)
+                    v[j] = ((unsigned)(base + 32 * j) < (unsigned)N) ? __ldg(row + 32 * j) : make_float2(0.f, 0.f);
             }
         };
         // Accumulate pulse mm whose samples (at the first hypothesis' shift) are in sv.
@@ -140,22 +163,20 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
                 }
             }
         };
-        // two pulses of look-ahead, two buffers that alternate: the samples of pulses
-        // mm+1 and mm+2 are in flight while pulse mm is accumulated
-        float2 pa[PL_J], pb[PL_J];
-        load_row(0, s_rho[0][0], pa);
-        if (mn > 1) load_row(1, s_rho[1][0], pb);
-        for (int mm = 0; mm < mn; mm += 2) {
-            float2 sv[PL_J];
-#pragma unroll
-            for (int j = 0; j < PL_J; ++j) sv[j] = pa[j];
-            if (mm + 2 < mn) load_row(mm + 2, s_rho[mm + 2][0], pa);
-            pulse(mm, sv);
+        // two pulses of look-ahead over three buffers in rotation: the samples of pulses mm+1
+        // and mm+2 are in flight while pulse mm is accumulated, and no buffer is copied
+        float2 b0[PL_J], b1[PL_J], b2[PL_J];
+        load_row(0, s_rho[0][0], b0);
+        if (mn > 1) load_row(1, s_rho[1][0], b1);
+        for (int mm = 0; mm < mn; mm += 3) {
+            if (mm + 2 < mn) load_row(mm + 2, s_rho[mm + 2][0], b2);
+            pulse(mm, b0);
             if (mm + 1 >= mn) break;
-#pragma unroll
-            for (int j = 0; j < PL_J; ++j) sv[j] = pb[j];
-            if (mm + 3 < mn) load_row(mm + 3, s_rho[mm + 3][0], pb);
-            pulse(mm + 1, sv);
+            if (mm + 3 < mn) load_row(mm + 3, s_rho[mm + 3][0], b0);
+            pulse(mm + 1, b1);
+            if (mm + 2 >= mn) break;
+            if (mm + 4 < mn) load_row(mm + 4, s_rho[mm + 4][0], b1);
+            pulse(mm + 2, b2);
         }
     }
 
