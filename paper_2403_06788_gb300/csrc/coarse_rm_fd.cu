@@ -33,7 +33,7 @@ __global__ __launch_bounds__(FD_THREADS, 2) void k_range_fft(const float2 *__res
         __syncthreads();
         for (int n = threadIdx.x; n < N; n += FD_THREADS) x[fpad(n)] = __ldg(echo + (long)m * N + n);
         __syncthreads();
-        fft_dif_fwd<FD_THREADS, 3>(x, 1, fft_padded(N), tw, logN);
+        fft_dif_fwd<FD_THREADS>(x, 1, fft_padded(N), tw, logN);
         for (int p = threadIdx.x; p < N; p += FD_THREADS) S[(long)m * N + p] = x[fpad(p)];   // bit-reversed order
     }
 }

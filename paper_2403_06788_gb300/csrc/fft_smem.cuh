@@ -40,32 +40,40 @@ __device__ __forceinline__ void build_twiddles(float2 *tw, int n) {
     }
 }
 
-// One pass of NS (<= 4) radix-2 stages with spans h0, 2 h0, .., h0 2^(NS-1), h0 = 2^s0.
+// One pass of NS (<= 4) radix-2 stages with spans h0, 2 h0, .., h0 2^(NS-1), h0 = 2^S0.
 // Group g of a column holds the elements i0 + h0 q, q < 2^NS, with r0 = g mod h0 and
 // i0 = (g / h0) 2^NS h0 + r0; the butterfly of span h = h0 2^u pairs q and q + 2^u (bit u
 // of q clear) and takes the twiddle of r = r0 + h0 (q mod 2^u).
 //   DIF (forward, exponent -): stages in decreasing span; (a, b) -> (a + b, (a - b) conj(w)).
 //   DIT (inverse, exponent +): stages in increasing span; b w, then (a + b w, a - b w).
-template <int NT, int NS, bool DIF>
-__device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const float2 *tw, int logn, int s0) {
+// S0 is a compile-time constant (0, 4, 8 or 12), so element q of a group sits at a base
+// plus an immediate offset, and so does twiddle a of a stage (tw[h + r0 + a h0]):
+//   h0 = 1: i0 = 2^NS g is a multiple of 2^NS <= 16 apart from no offset, so fpad(i0 + q) =
+//           fpad(i0) + q for q < 2^NS (i0 mod 16 + q < 16);
+//   h0 >= 16: q h0 is a multiple of 16, so fpad(i0 + q h0) = fpad(i0) + q (h0 + h0 / 16).
+template <int NT, int NS, int S0, bool DIF>
+__device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const float2 *tw, int logn) {
     constexpr int G = 1 << NS;
-    const int h0 = 1 << s0;
+    constexpr int h0 = 1 << S0;
+    constexpr int step = h0 == 1 ? 1 : h0 + h0 / 16;   // padded distance of consecutive q
+    static_assert(h0 == 1 || h0 % 16 == 0, "passes start at span 1 or a multiple of 16");
     const int lper = logn - NS;                 // log2 of the groups per column
     for (int t = threadIdx.x; t < (cols << lper); t += NT) {
         const int col = t >> lper, g = t & ((1 << lper) - 1);
-        float2 *xc = x + (long)col * ld;
         const int r0 = g & (h0 - 1);
-        const int i0 = ((g >> s0) << (s0 + NS)) + r0;
+        const int i0 = ((g >> S0) << (S0 + NS)) + r0;
+        float2 *xg = x + (long)col * ld + fpad(i0);
         float2 v[G];
 #pragma unroll
-        for (int q = 0; q < G; ++q) v[q] = xc[fpad(i0 + (q << s0))];
+        for (int q = 0; q < G; ++q) v[q] = xg[q * step];
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
             const int u = DIF ? NS - 1 - k : k;
             const int h = h0 << u;
+            const float2 *twg = tw + h + r0;
             float2 w[G / 2];
 #pragma unroll
-            for (int a = 0; a < (1 << u); ++a) w[a] = tw[h + r0 + (a << s0)];
+            for (int a = 0; a < (1 << u); ++a) w[a] = twg[a * h0];
 #pragma unroll
             for (int q = 0; q < G; ++q) {
                 if (q & (1 << u)) continue;
@@ -82,38 +90,49 @@ __device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const floa
             }
         }
 #pragma unroll
-        for (int q = 0; q < G; ++q) xc[fpad(i0 + (q << s0))] = v[q];
+        for (int q = 0; q < G; ++q) xg[q * step] = v[q];
     }
 }
 
-template <int NT, bool DIF, int MAXNS>
-__device__ __forceinline__ void fft_pass_any(float2 *x, int cols, int ld, const float2 *tw, int logn, int s0) {
-    switch (logn - s0 < MAXNS ? logn - s0 : MAXNS) {
-        case 4: if constexpr (MAXNS >= 4) fft_pass<NT, 4, DIF>(x, cols, ld, tw, logn, s0); break;
-        case 3: fft_pass<NT, 3, DIF>(x, cols, ld, tw, logn, s0); break;
-        case 2: fft_pass<NT, 2, DIF>(x, cols, ld, tw, logn, s0); break;
-        default: fft_pass<NT, 1, DIF>(x, cols, ld, tw, logn, s0); break;
+// The pass starting at stage S0: NS = min(MAXNS, logn - S0) stages, then the CTA barrier.
+template <int NT, bool DIF, int MAXNS, int S0>
+__device__ __forceinline__ void fft_pass_at(float2 *x, int cols, int ld, const float2 *tw, int logn) {
+    const int ns = logn - S0 < MAXNS ? logn - S0 : MAXNS;
+    if (ns >= 4) {
+        if constexpr (MAXNS >= 4) fft_pass<NT, 4, S0, DIF>(x, cols, ld, tw, logn);
+    } else if (ns == 3) {
+        fft_pass<NT, 3, S0, DIF>(x, cols, ld, tw, logn);
+    } else if (ns == 2) {
+        fft_pass<NT, 2, S0, DIF>(x, cols, ld, tw, logn);
+    } else {
+        fft_pass<NT, 1, S0, DIF>(x, cols, ld, tw, logn);
     }
     __syncthreads();
 }
 
 // Forward decimation in frequency, in place: natural order in, bit-reversed order out
-// (exponent -).  Passes of up to MAXNS (3 or 4) stages from the largest spans down (MAXNS 3
-// halves the registers a thread holds).
+// (exponent -).  Passes of up to four stages (pass starts 0, 4, 8, 12) from the largest
+// spans down; lengths up to 2^13.
 template <int NT, int MAXNS = 4>
 __device__ __forceinline__ void fft_dif_fwd(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    static_assert(MAXNS == 3 || MAXNS == 4, "stages per pass");
+    static_assert(MAXNS == 4, "pass starts must be multiples of 4");
     if (logn < 1) return;
-    for (int s0 = ((logn - 1) / MAXNS) * MAXNS; s0 >= 0; s0 -= MAXNS)
-        fft_pass_any<NT, true, MAXNS>(x, cols, ld, tw, logn, s0);
+    if (logn > 12) fft_pass_at<NT, true, MAXNS, 12>(x, cols, ld, tw, logn);
+    if (logn > 8) fft_pass_at<NT, true, MAXNS, 8>(x, cols, ld, tw, logn);
+    if (logn > 4) fft_pass_at<NT, true, MAXNS, 4>(x, cols, ld, tw, logn);
+    fft_pass_at<NT, true, MAXNS, 0>(x, cols, ld, tw, logn);
 }
 
 // Inverse decimation in time, in place: bit-reversed order in, natural order out (exponent
-// +, unscaled).  Passes of up to MAXNS stages from span 1 up.
+// +, unscaled).  Passes of up to MAXNS stages from span 1 up; lengths up to 2^13.
 template <int NT, int MAXNS = 4>
 __device__ __forceinline__ void fft_dit_inv(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    static_assert(MAXNS == 3 || MAXNS == 4, "stages per pass");
-    for (int s0 = 0; s0 < logn; s0 += MAXNS) fft_pass_any<NT, false, MAXNS>(x, cols, ld, tw, logn, s0);
+    static_assert(MAXNS == 4, "pass starts must be multiples of 4");
+    if (logn < 1) return;
+    fft_pass_at<NT, false, MAXNS, 0>(x, cols, ld, tw, logn);
+    if (logn > 4) fft_pass_at<NT, false, MAXNS, 4>(x, cols, ld, tw, logn);
+    if (logn > 8) fft_pass_at<NT, false, MAXNS, 8>(x, cols, ld, tw, logn);
+    if (logn > 12) fft_pass_at<NT, false, MAXNS, 12>(x, cols, ld, tw, logn);
 }
 
 }  // namespace grft

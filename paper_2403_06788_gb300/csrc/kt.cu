@@ -87,7 +87,7 @@ __global__ __launch_bounds__(KT_THREADS, 2) void k_keystone(const float2 *__rest
             b0[(long)col * Pp + fpad(m)] = __ldg(S + (long)m * N + p0 + col);
         }
         __syncthreads();
-        fft_dif_fwd<KT_THREADS, 3>(b0, cols, Pp, tw, logM);      // Y[l] at b0[bitrev_M(l mod M)]
+        fft_dif_fwd<KT_THREADS>(b0, cols, Pp, tw, logM);      // Y[l] at b0[bitrev_M(l mod M)]
         for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) {
             const int col = t >> logP, i = t & (P - 1);
             float2 v = make_float2(0.f, 0.f);
@@ -106,13 +106,13 @@ __global__ __launch_bounds__(KT_THREADS, 2) void k_keystone(const float2 *__rest
             b0[(long)col * Pp + fpad(e)] = g;
         }
         __syncthreads();
-        fft_dif_fwd<KT_THREADS, 3>(kt_smem, 2 * cols, Pp, tw, logP);  // kernel and sequence together
+        fft_dif_fwd<KT_THREADS>(kt_smem, 2 * cols, Pp, tw, logP);  // kernel and sequence together
         for (int t = threadIdx.x; t < cols * P; t += KT_THREADS) {
             const long o = (long)(t >> logP) * Pp + fpad(t & (P - 1));
             b1[o] = cmul(b0[o], b1[o]);
         }
         __syncthreads();
-        fft_dit_inv<KT_THREADS, 3>(b1, cols, Pp, tw, logP);
+        fft_dit_inv<KT_THREADS>(b1, cols, Pp, tw, logP);
         for (int t = threadIdx.x; t < cols * M; t += KT_THREADS) {
             const int col = t % cols, m = t / cols;
             const float2 v = cmul(b1[(long)col * Pp + fpad(m)], kt_chirp(m, logM, s_eps[col]));
