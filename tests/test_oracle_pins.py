@@ -362,20 +362,6 @@ def test_ds_at_zero_fine_offset_is_grft_at_the_cell_centre():
     assert np.abs(other - Ypl).max() > 1e-3 * np.abs(Ypl).max()
 
 
-def test_oracle_thread_count_of_a_call_does_not_persist():
-    """A one-thread call gives the same rows as an all-thread call and leaves the default
-    thread count of later calls unchanged (the CPU baseline times both in one process)."""
-    sc = synth.ds_m512()
-    s = synth.make_echo(sc.radar, sc.targets, sc.seed)
-    cells, fine = np.arange(4) * 37, np.arange(4) * 101
-    default = oracle.num_threads()
-    Ya = oracle.dsgrft_rows(sc.radar, s, sc.ds, cells, fine)
-    Y1 = oracle.dsgrft_rows(sc.radar, s, sc.ds, cells, fine, nthreads=1)
-    assert oracle.num_threads() == default
-    Yb = oracle.dsgrft_rows(sc.radar, s, sc.ds, cells, fine)
-    assert np.array_equal(Ya, Y1) and np.array_equal(Ya, Yb)
-
-
 # ---------------------------------------------------------------- P9: sinc target closed form
 def test_sinc_target_closed_form_at_truth():
     """Noiseless sinc target: at its true (n0, v, a) the gathered samples are
