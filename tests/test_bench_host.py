@@ -38,3 +38,21 @@ def test_oracle_thread_count_of_a_call_does_not_persist():
     assert oracle.num_threads() == default
     Yb = oracle.dsgrft_rows(sc.radar, s, sc.ds, cells, fine)
     assert np.array_equal(Ya, Y1) and np.array_equal(Ya, Yb)
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """bench.py --impl reference: one JSON line with the contract's keys, the oracle timed on
+    the host (a tiny sample here)."""
+    import argparse
+    import json
+    args = argparse.Namespace(gpus=1, steps=1, warmup=1, ref_step_s=0.2, ref_total_s=0.2)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
