@@ -48,8 +48,8 @@ __device__ __forceinline__ void build_twiddles(float2 *tw, int n) {
 //   DIT (inverse, exponent +): stages in increasing span; b w, then (a + b w, a - b w).
 // S0 is a compile-time constant (0, 4, 8 or 12), so element q of a group sits at a base
 // plus an immediate offset, and so does twiddle a of a stage (tw[h + r0 + a h0]):
-//   h0 = 1: i0 = 2^NS g is a multiple of 2^NS <= 16 apart from no offset, so fpad(i0 + q) =
-//           fpad(i0) + q for q < 2^NS (i0 mod 16 + q < 16);
+//   h0 = 1: i0 = 2^NS g is a multiple of 2^NS (at most 16), so i0 mod 16 + q < 16 and
+//           fpad(i0 + q) = fpad(i0) + q for q < 2^NS;
 //   h0 >= 16: q h0 is a multiple of 16, so fpad(i0 + q h0) = fpad(i0) + q (h0 + h0 / 16).
 template <int NT, int NS, int S0, bool DIF>
 __device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const float2 *tw, int logn) {
