@@ -1,12 +1,12 @@
-// Transforms of power-of-two length over complex FP32 data in shared memory, done by a whole
-// CTA of NT threads (every thread calls).  The radix-2 stages are taken MAXNS (4, or 3 to
-// halve the registers) at a time: a thread loads the 2^MAXNS elements that those stages
-// combine, runs the stages in registers and stores them back, so a length-2^L transform
-// costs ceil(L / MAXNS) passes, each ending in one __syncthreads.  `cols` transforms of the
-// same length, `ld` elements apart, run together.
+// Transforms of power-of-two length (up to 2^13) over complex FP32 data in shared memory,
+// done by a whole CTA of NT threads (every thread calls).  The radix-2 stages are taken four
+// at a time: a thread loads the 16 elements that those stages combine, runs the stages in
+// registers and stores them back, so a length-2^L transform costs ceil(L / 4) passes, each
+// ending in one __syncthreads.  `cols` transforms of the same length, `ld` elements apart,
+// run together.
 //
 // Layout: element e of a column sits at column offset fpad(e) = e + e/16 (one unused slot
-// after every 16), so that in the first pass, where a thread reads 2^MAXNS consecutive
+// after every 16), so that in the first pass, where a thread reads up to 16 consecutive
 // elements, the lanes of a half-warp fall on distinct banks; `ld` >= fft_padded(n).
 #pragma once
 
@@ -94,12 +94,12 @@ __device__ __forceinline__ void fft_pass(float2 *x, int cols, int ld, const floa
     }
 }
 
-// The pass starting at stage S0: NS = min(MAXNS, logn - S0) stages, then the CTA barrier.
-template <int NT, bool DIF, int MAXNS, int S0>
+// The pass starting at stage S0: NS = min(4, logn - S0) stages, then the CTA barrier.
+template <int NT, bool DIF, int S0>
 __device__ __forceinline__ void fft_pass_at(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    const int ns = logn - S0 < MAXNS ? logn - S0 : MAXNS;
-    if (ns >= 4) {
-        if constexpr (MAXNS >= 4) fft_pass<NT, 4, S0, DIF>(x, cols, ld, tw, logn);
+    const int ns = logn - S0 < 4 ? logn - S0 : 4;
+    if (ns == 4) {
+        fft_pass<NT, 4, S0, DIF>(x, cols, ld, tw, logn);
     } else if (ns == 3) {
         fft_pass<NT, 3, S0, DIF>(x, cols, ld, tw, logn);
     } else if (ns == 2) {
@@ -113,26 +113,24 @@ __device__ __forceinline__ void fft_pass_at(float2 *x, int cols, int ld, const f
 // Forward decimation in frequency, in place: natural order in, bit-reversed order out
 // (exponent -).  Passes of up to four stages (pass starts 0, 4, 8, 12) from the largest
 // spans down; lengths up to 2^13.
-template <int NT, int MAXNS = 4>
+template <int NT>
 __device__ __forceinline__ void fft_dif_fwd(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    static_assert(MAXNS == 4, "pass starts must be multiples of 4");
     if (logn < 1) return;
-    if (logn > 12) fft_pass_at<NT, true, MAXNS, 12>(x, cols, ld, tw, logn);
-    if (logn > 8) fft_pass_at<NT, true, MAXNS, 8>(x, cols, ld, tw, logn);
-    if (logn > 4) fft_pass_at<NT, true, MAXNS, 4>(x, cols, ld, tw, logn);
-    fft_pass_at<NT, true, MAXNS, 0>(x, cols, ld, tw, logn);
+    if (logn > 12) fft_pass_at<NT, true, 12>(x, cols, ld, tw, logn);
+    if (logn > 8) fft_pass_at<NT, true, 8>(x, cols, ld, tw, logn);
+    if (logn > 4) fft_pass_at<NT, true, 4>(x, cols, ld, tw, logn);
+    fft_pass_at<NT, true, 0>(x, cols, ld, tw, logn);
 }
 
 // Inverse decimation in time, in place: bit-reversed order in, natural order out (exponent
-// +, unscaled).  Passes of up to MAXNS stages from span 1 up; lengths up to 2^13.
-template <int NT, int MAXNS = 4>
+// +, unscaled).  Passes of up to four stages from span 1 up; lengths up to 2^13.
+template <int NT>
 __device__ __forceinline__ void fft_dit_inv(float2 *x, int cols, int ld, const float2 *tw, int logn) {
-    static_assert(MAXNS == 4, "pass starts must be multiples of 4");
     if (logn < 1) return;
-    fft_pass_at<NT, false, MAXNS, 0>(x, cols, ld, tw, logn);
-    if (logn > 4) fft_pass_at<NT, false, MAXNS, 4>(x, cols, ld, tw, logn);
-    if (logn > 8) fft_pass_at<NT, false, MAXNS, 8>(x, cols, ld, tw, logn);
-    if (logn > 12) fft_pass_at<NT, false, MAXNS, 12>(x, cols, ld, tw, logn);
+    fft_pass_at<NT, false, 0>(x, cols, ld, tw, logn);
+    if (logn > 4) fft_pass_at<NT, false, 4>(x, cols, ld, tw, logn);
+    if (logn > 8) fft_pass_at<NT, false, 8>(x, cols, ld, tw, logn);
+    if (logn > 12) fft_pass_at<NT, false, 12>(x, cols, ld, tw, logn);
 }
 
 }  // namespace grft
