@@ -9,6 +9,8 @@
 //   [Re Zc | Im Zc] (rows n0)  x  [[Re D, Im D], [-Im D, Re D]]  =  [Re Y~ | Im Y~]
 // and each real operand x is split as hi = round16(x), lo = round16(x - hi) (BF16 or FP16),
 // accumulating hi*hi + hi*lo + lo*hi in FP32 (three tcgen05.mma per K step).  The
+// two-product FP16 mode (NP = 2) splits the gathered operand only and rounds the dechirp
+// once: hi*hi + lo*hi, two tcgen05.mma per K step, no lo plane of the dechirp loaded.  The
 // single-product FP16 mode (NP = 1) keeps only hi*hi: one tcgen05.mma per K step, no lo
 // planes loaded or written.
 //
@@ -56,8 +58,11 @@ constexpr uint64_t TC_DRAIN_LIMIT = 4000000000ull;   // bounded drain on the unw
 // BN real columns per tile (BN/2 fine hypotheses) and ST pipeline stages.
 // ... and BK real k per stage: 64 (128-byte swizzle rows) or 32 (64-byte swizzle rows, so
 // twice the stages fit the same shared memory).
+// Planes (hi, lo) of the gathered operand A and of the dechirp operand B per product count.
+constexpr int tc_planes_a(int NP) { return NP >= 2 ? 2 : 1; }
+constexpr int tc_planes_b(int NP) { return NP == 3 ? 2 : 1; }
 constexpr size_t tc_smem_bytes(int BN, int ST, int BK, int NP) {
-    return (size_t)ST * ((NP == 3 ? 2 : 1) * ((size_t)TC_BM * BK * 2 + (size_t)BN * BK * 2)) + 1024;
+    return (size_t)ST * (tc_planes_a(NP) * (size_t)TC_BM * BK * 2 + tc_planes_b(NP) * (size_t)BN * BK * 2) + 1024;
 }
 
 constexpr int SP_THREADS = 128;             // 4 warps x 32 range bins = one 128-bin tile
@@ -92,7 +97,7 @@ struct TcBatch {
     int tiles_n, F, Fv, Fa, na_c;
     int Fb, nb_c;           // acceleration-rate axis (P = 3); 1, 1 for P = 2
     int fp16;
-    int nprod;              // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only (no lo planes)
+    int nprod;              // 3: hi*hi + hi*lo + lo*hi; 2: hi*hi + lo*hi; 1: hi*hi only
     uint32_t idesc;
     int *status;
     uint64_t wait_limit;
@@ -112,20 +117,14 @@ __device__ __forceinline__ int find_item_tile(const TcBatch &b, int idx) {
     return i;
 }
 
-// Coordinates of a work unit: with CL = 1 one tile (item, cell, bin tile mt, hypothesis
-// tile nt); with CL = 2 a pair of bin tiles (2 mg, 2 mg + 1) sharing hypothesis tile nt,
-// CTA `rank` of the cluster taking bin tile 2 mg + rank (a tile past the item's last bin
-// tile computes on whatever rows it loads and stores nothing).
-template <int CL>
-__device__ __forceinline__ const TcItem &decode_unit(const TcBatch &b, int unit, int rank, int &nt, int &mt,
-                                                     int &cl) {
+// Coordinates of a work unit: one tile (item, cell, bin tile mt, hypothesis tile nt).
+__device__ __forceinline__ const TcItem &decode_unit(const TcBatch &b, int unit, int &nt, int &mt, int &cl) {
     const TcItem &p = b.it[find_item_tile(b, unit)];
     const int local = unit - p.tile0;
     nt = local % b.tiles_n;
     const int rest = local / b.tiles_n;
-    const int groups = (p.tiles_m + CL - 1) / CL;
-    mt = (rest % groups) * CL + rank;
-    cl = rest / groups;
+    mt = rest % p.tiles_m;
+    cl = rest / p.tiles_m;
     return p;
 }
 
@@ -159,38 +158,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
-}
-
-// Commit to the same mbarrier in every CTA of cta_mask (cluster of two: both consumers of
-// a multicast stage signal both producers).
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(cta_mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of every CTA of the cluster.
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// 2-D tiled TMA load delivered to the same shared-memory offset (and completing the same
-// mbarrier offset) in every CTA of cta_mask.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
-                                               uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
-        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() {
@@ -334,7 +301,7 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
     uint4 *tr = sp_smem + warp * 512;            // this warp's tile: hi plane, then lo plane
     const size_t row0 = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j0 + warp * 32;
     const uint64_t pol_z = l2_policy_evict_first();
-    const bool with_lo = B.nprod == 3;          // block-uniform
+    const bool with_lo = B.nprod >= 2;          // block-uniform
     const int S = 4 * p.KT;                     // sub-steps of 8 pulses (even)
 
     // Convert sub-step s (pulses 8s..8s+7 of this lane's bin; phase already applied), place
@@ -445,7 +412,7 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
 }
 
 // =========================================================================== kernel b
-template <int BN, int ST, int CL, int BK, int NP>
+template <int BN, int ST, int BK, int NP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ds_tc(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
             const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
@@ -454,16 +421,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr int TC_STAGES = ST;
     constexpr uint32_t TC_A_BYTES = TC_BM * BK * 2;    // per plane
     constexpr uint32_t TC_B_BYTES = BN * BK * 2;       // per plane
-    constexpr uint32_t NPL = NP == 3 ? 2 : 1;          // planes per operand (hi, lo)
-    constexpr uint32_t TC_STAGE_BYTES = NPL * (TC_A_BYTES + TC_B_BYTES);
-    constexpr uint32_t TC_B_OFF = NPL * TC_A_BYTES;    // B planes follow the A planes
+    constexpr uint32_t TC_STAGE_BYTES = tc_planes_a(NP) * TC_A_BYTES + tc_planes_b(NP) * TC_B_BYTES;
+    constexpr uint32_t TC_B_OFF = tc_planes_a(NP) * TC_A_BYTES;   // B planes follow the A planes
     constexpr int KSUB = 64 / BK;                      // stages per 32-pulse group
     constexpr uint32_t TC_TMEM_COLS = 2 * BN;          // two accumulators
     static_assert(BN % 32 == 0 && BN <= 256 && TC_TMEM_COLS >= 32, "tile");
-    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
-    static_assert(NP == 3 || NP == 1, "three products (split) or one (FP16)");
-    constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
-    constexpr uint32_t TC_B_PART = TC_B_BYTES / CL;    // rows of B this CTA fetches (per plane)
+    static_assert(NP >= 1 && NP <= 3, "three, two or one products per K step");
     extern __shared__ unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
@@ -474,8 +437,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
-    const int cid = (int)blockIdx.x / CL, ncl = (int)gridDim.x / CL;   // cluster index, count
+    const int cid = (int)blockIdx.x, ncl = (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&mapAhi);
@@ -484,7 +446,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tma_prefetch_desc(&mapBlo);
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);             // every CTA of the cluster reads each stage's B
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tmem_full[b], 1);
@@ -503,7 +465,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
     }
     __syncthreads();
-    if (CL > 1) cluster_sync_all();              // peers' barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem_base = tmem_holder;
     const uint64_t lim = B.wait_limit;
@@ -515,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int last_it = -1;
             for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl) {
                 int nt, mt, cl;
-                const TcItem &p = decode_unit<CL>(B, tile, rank, nt, mt, cl);
+                const TcItem &p = decode_unit(B, tile, nt, mt, cl);
                 const int arow = (int)(p.zrow0 + (long)cl * p.r0_pad + mt * TC_BM);
                 for (int kt = 0; kt < p.KT * KSUB; ++kt, ++it) {
                     const int s = it % TC_STAGES;
@@ -527,19 +488,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     unsigned char *st = smem + s * TC_STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
                     tma_load_2d(st, &mapAhi, kt * BK, arow, &full[s]);
-                    if (NP == 3) tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * BK, arow, &full[s]);
-                    if (CL == 1) {
-                        tma_load_2d(st + TC_B_OFF, &mapBhi, kt * BK, nt * TC_BN, &full[s]);
-                        if (NP == 3)
-                            tma_load_2d(st + TC_B_OFF + TC_B_BYTES, &mapBlo, kt * BK, nt * TC_BN, &full[s]);
-                    } else {   // this CTA's share of the B rows, delivered to every CTA of the cluster
-                        const int brow = nt * TC_BN + rank * (TC_BN / CL);
-                        tma_load_2d_mc(st + TC_B_OFF + rank * TC_B_PART, &mapBhi, kt * BK, brow, &full[s],
-                                       CL_MASK);
-                        if (NP == 3)
-                            tma_load_2d_mc(st + TC_B_OFF + TC_B_BYTES + rank * TC_B_PART, &mapBlo, kt * BK, brow,
-                                           &full[s], CL_MASK);
-                    }
+                    if (NP >= 2) tma_load_2d(st + TC_A_BYTES, &mapAlo, kt * BK, arow, &full[s]);
+                    tma_load_2d(st + TC_B_OFF, &mapBhi, kt * BK, nt * TC_BN, &full[s]);
+                    if (NP == 3) tma_load_2d(st + TC_B_OFF + TC_B_BYTES, &mapBlo, kt * BK, nt * TC_BN, &full[s]);
                     last_it = it;
                 }
             }
@@ -581,16 +532,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint32_t off = kk * 32;   // 16 elements x 2 bytes inside the swizzle row
                         umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_hi + off), B.idesc,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
-                        if (NP == 3) {
+                        if (NP == 3)
                             umma_f16(d_tmem, umma_desc<BK>(a_hi + off), umma_desc<BK>(b_lo + off), B.idesc, 1u);
+                        if (NP >= 2)
                             umma_f16(d_tmem, umma_desc<BK>(a_lo + off), umma_desc<BK>(b_hi + off), B.idesc, 1u);
-                        }
                     }
                     issued_any = true;
-                    if (CL == 1)
-                        umma_commit(&empty[s]);
-                    else
-                        umma_commit_mc(&empty[s], CL_MASK);   // the stage's B is shared
+                    umma_commit(&empty[s]);
                 }
                 if (!ok) break;
                 umma_commit(&tmem_full[b]);
@@ -617,7 +565,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int tile = cid; tile < B.total_tiles; tile += ncl, ++tcount) {
             const int b = tcount & 1;
             int nt, mt, cl;
-            const TcItem &p = decode_unit<CL>(B, tile, rank, nt, mt, cl);
+            const TcItem &p = decode_unit(B, tile, nt, mt, cl);
             const int c = p.cell0 + cl;
             const int iw = c % B.nb_c, c2 = c / B.nb_c;      // P = 3: c = (i na_c + l) nb_c + w
             const int iv = c2 / B.na_c - p.i0, il = c2 % B.na_c;
@@ -677,7 +625,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      "r"(TC_TMEM_COLS)
                      : "memory");
     }
-    if (CL > 1) cluster_sync_all();              // no peer still signals or writes into this CTA
 }
 
 bool set_smem_attr(const void *fn, size_t bytes, int device, bool *done) {
@@ -704,7 +651,7 @@ namespace {
 // DSGRFT_AUTOTUNE=0 disables timing (the default variant is used); DSGRFT_TILE_VARIANT=v
 // forces variant v.  Variants give
 // bit-identical results: only the N tiling changes, not the order of the K accumulation.
-constexpr int TC_VARIANTS = 5;     // (BN, stages, CTAs per cluster, BK): see launch_gemm_variant
+constexpr int TC_VARIANTS = 3;     // (BN, stages, BK): see launch_gemm_variant
 using TuneKey = std::tuple<int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
@@ -802,14 +749,13 @@ int tune_variant(const Ctx &c, const TcBatch &, Run run) {
     return best;
 }
 
-template <int BN, int ST, int CL, int BK, int NP>
+template <int BN, int ST, int BK, int NP>
 int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
     static bool attr[64] = {false};
-    static int max_clusters[64] = {0};
     const size_t smem = tc_smem_bytes(BN, ST, BK, NP);
     static_assert(tc_smem_bytes(BN, ST, BK, NP) <= 227 * 1024, "shared memory");
-    if (!set_smem_attr((const void *)k_ds_tc<BN, ST, CL, BK, NP>, smem, c.device, attr)) return GRFT_ECUDA;
+    if (!set_smem_attr((const void *)k_ds_tc<BN, ST, BK, NP>, smem, c.device, attr)) return GRFT_ECUDA;
     const uint64_t kdim = 2ull * Mpad;
     const CUtensorMapSwizzle sw = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     CUtensorMap mzh, mzl, mbh, mbl;
@@ -817,71 +763,50 @@ int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
                        TC_BM, sw) ||
         !encode_tma_2d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, kdim, (uint64_t)zrows, kdim * 2, BK,
                        TC_BM, sw) ||
-        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2, BK,
-                       BN / CL, sw) ||
-        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2, BK,
-                       BN / CL, sw))
+        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, kdim, 2ull * Fpad, kdim * 2, BK, BN,
+                       sw) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, kdim, 2ull * Fpad, kdim * 2, BK, BN,
+                       sw))
         return GRFT_ECUDA;
     TcBatch bb = b;
     bb.tiles_n = 2 * Fpad / BN;
     long units = 0;
     for (int i = 0; i < bb.n_items; ++i) {
         bb.it[i].tile0 = (int)units;
-        units += (long)bb.it[i].ncell * ((bb.it[i].tiles_m + CL - 1) / CL) * bb.tiles_n;
+        units += (long)bb.it[i].ncell * bb.it[i].tiles_m * bb.tiles_n;
     }
     if (units > 0x7fffffffL) return GRFT_EINVAL;
     bb.total_tiles = (int)units;
     const uint32_t fmt = bb.fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
     bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
                ((uint32_t)(TC_BM >> 4) << 24);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute la[1];
-    cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = c.stream;
-    int slots = c.num_sms;                    // persistent CTAs (CL = 1) or clusters (CL = 2)
-    if (CL > 1) {
-        la[0].id = cudaLaunchAttributeClusterDimension;
-        la[0].val.clusterDim.x = CL;
-        la[0].val.clusterDim.y = 1;
-        la[0].val.clusterDim.z = 1;
-        cfg.attrs = la;
-        cfg.numAttrs = 1;
-        if (c.device >= 64) return GRFT_EUNSUPPORTED;
-        if (max_clusters[c.device] <= 0) {
-            cfg.gridDim = dim3(CL * (c.num_sms / CL));
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k_ds_tc<BN, ST, CL, BK, NP>, &cfg) != cudaSuccess || n <= 0)
-                return GRFT_ECUDA;
-            max_clusters[c.device] = n;
-        }
-        slots = max_clusters[c.device];
-    }
-    const int groups = bb.total_tiles < slots ? bb.total_tiles : slots;
-    cfg.gridDim = dim3(CL * groups);
+    const int slots = c.num_sms;              // one persistent CTA per SM
+    const int grid = bb.total_tiles < slots ? bb.total_tiles : slots;
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
-    if (cudaLaunchKernelEx(&cfg, k_ds_tc<BN, ST, CL, BK, NP>, mzh, mzl, mbh, mbl, bb) != cudaSuccess)
-        return GRFT_ECUDA;
+    k_ds_tc<BN, ST, BK, NP><<<grid, TC_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
     return check_launch();
 }
 
 int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo,
                         long zrows, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    if (b.nprod == 2) {   // lo plane of A only: 64 KB (BK 64) or 32 KB (BK 32) per stage of 256 columns
+        switch (variant) {
+            case 1: return launch_gemm<128, 4, 64, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 2: return launch_gemm<256, 6, 32, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            default: return launch_gemm<256, 3, 64, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        }
+    }
     if (b.nprod == 1) {   // no lo planes: twice the stages in the same shared memory
         switch (variant) {
-            case 1: return launch_gemm<128, 6, 1, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            case 2: return launch_gemm<256, 4, 2, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            case 3: return launch_gemm<256, 8, 1, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            case 4: return launch_gemm<256, 8, 2, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            default: return launch_gemm<256, 4, 1, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 1: return launch_gemm<128, 6, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 2: return launch_gemm<256, 8, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            default: return launch_gemm<256, 4, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
         }
     }
     switch (variant) {
-        case 1: return launch_gemm<128, 3, 1, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 2: return launch_gemm<256, 2, 2, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 3: return launch_gemm<256, 4, 1, 32, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        case 4: return launch_gemm<256, 4, 2, 32, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-        default: return launch_gemm<256, 2, 1, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 1: return launch_gemm<128, 3, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        case 2: return launch_gemm<256, 4, 32, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+        default: return launch_gemm<256, 2, 64, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
     }
 }
 
@@ -995,8 +920,8 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
         while (rmax < tm) rmax <<= 1;
         if (items[i].cell_count > 0) total_rows += (long)items[i].cell_count * tm * TC_BM;
     }
-    // precision bucket: 0 split BF16, 1 split FP16, 3 single-product FP16
-    const TuneKey key(Mpad, Fpad, rmax, (fp16 ? 1 : 0) + (nprod == 1 ? 2 : 0));
+    // precision bucket: 0 split BF16, 1 split FP16, 3 single-product FP16, 5 two-product FP16
+    const TuneKey key(Mpad, Fpad, rmax, (fp16 ? 1 : 0) + (nprod == 1 ? 2 : 0) + (nprod == 2 ? 4 : 0));
     int variant = tune_lookup(key);
     if (variant < 0 && !tune_enabled()) variant = 0;
     if (const char *fv = getenv("DSGRFT_TILE_VARIANT")) {   // explicit choice (tests, experiments)

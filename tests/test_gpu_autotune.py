@@ -1,9 +1,8 @@
 """GPU: the tile-shape autotuner of the tensor-core contraction.  Every variant (BN 256 or
-128 columns, 64 or 32 k per stage with 2 to 4 stages, single CTAs or CTA pairs that
-multicast the dechirp tile) gives bit-identical outputs (only the tiling differs, not the K accumulation order),
-also when the pairs end in an unpaired bin tile; the first call of a shape bucket records
-its choice in the JSON-lines cache named by DSGRFT_TUNE_CACHE, and a later process reuses
-it."""
+128 columns, 64 or 32 k per stage with 2 to 8 stages) gives bit-identical outputs (only the
+tiling differs, not the K accumulation order), with whole and ragged bin tiles; the first
+call of a shape bucket records its choice in the JSON-lines cache named by
+DSGRFT_TUNE_CACHE, and a later process reuses it."""
 import json
 import os
 import subprocess
@@ -39,13 +38,13 @@ def _run(tmp, name, r0_count=900, precision="bf16x3", **env):
     return np.load(out)
 
 
-@pytest.mark.parametrize("r0_count,precision", [(900, "bf16x3"), (800, "bf16x3"), (900, "fp16x1")])
+@pytest.mark.parametrize("r0_count,precision", [(900, "bf16x3"), (800, "bf16x3"), (900, "fp16x2"), (900, "fp16x1")])
 def test_tile_variants_are_bit_identical(cuda_lib, tmp_path, r0_count, precision):
-    # 8 bin tiles; 7 (the last pair unpaired); the single-product variants (twice the stages)
+    # 8 bin tiles (the last one ragged); 7; the single-product variants (twice the stages)
     import numpy as np
     y0 = _run(str(tmp_path), "v0", r0_count, precision, DSGRFT_TILE_VARIANT=0)
     assert np.isfinite(y0).all() and np.abs(y0).max() > 0
-    for v in range(1, 5):
+    for v in range(1, 3):
         yv = _run(str(tmp_path), "v%d" % v, r0_count, precision, DSGRFT_TILE_VARIANT=v)
         assert np.array_equal(y0, yv), v
 
@@ -55,7 +54,7 @@ def test_autotune_records_and_reuses_choice(cuda_lib, tmp_path):
     cache = os.path.join(str(tmp_path), "tune.jsonl")
     ya = _run(str(tmp_path), "a", DSGRFT_TUNE_CACHE=cache, DSGRFT_AUTOTUNE=1)
     lines = [json.loads(l) for l in open(cache)]
-    assert len(lines) == 1 and lines[0]["variant"] in range(5)
+    assert len(lines) == 1 and lines[0]["variant"] in range(3)
     assert lines[0]["Mpad"] == 320 and lines[0]["Fpad"] == 256
     yb = _run(str(tmp_path), "b", DSGRFT_TUNE_CACHE=cache, DSGRFT_AUTOTUNE=1)
     assert len(open(cache).readlines()) == 1          # the second process found the entry
