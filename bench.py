@@ -32,11 +32,11 @@ METRIC = "DS-GRFT vs plain GRFT hypothesis·pulse MACs/s, 1 GB300, ≤2e-3 rel p
 UNIT = "hyp*pulse/s"
 WORKLOAD = "DS-GRFT, M=512 x N=4096 complex64, 4096 r0 x (32x64) v x (8x16) a = 2^30 hypotheses"
 FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_ds_tc<256,4,2,32> (the tile shape
-# the autotuner picks here) on the first 16 coarse cells (276.9 MB + 231.0 MB), scaled by
-# 16 to one launch of this workload (all 256 cells in one launch).  Reset to None whenever
-# that kernel changes.
-DRAM_TRAFFIC_PER_LAUNCH = 16 * (276.915712e6 + 230.874368e6)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
+# coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
+# per precision.  None until a capture of the current kernel exists.
+DRAM_TRAFFIC_PER_LAUNCH = {}
+PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
 
 
 def _peaks():
@@ -587,7 +587,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)   # about 0.5 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp16x1", "fp32"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp16x2", "fp16x1", "fp32"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
@@ -606,8 +606,9 @@ def main():
     ap.add_argument("--forms", action="store_true",
                     help="time the FFT-form fine stage and the frequency-domain coarse stage against the dense "
                          "and gather forms (one JSON line; --cells N: the first N cells)")
-    ap.add_argument("--other-precisions", type=int, default=1,
-                    help="1: also time the step in the other contraction mode (fp16x1 beside bf16x3)")
+    ap.add_argument("--other-precisions", default="bf16x3,fp16x2,fp16x1,fp32",
+                    help="also time the step in these contraction modes (comma list; the headline's is "
+                         "skipped; empty: none)")
     ap.add_argument("--p3", action="store_true",
                     help="time DS-GRFT with the acceleration rate (P = 3) on its 2.1e9-hypothesis grid (one JSON line)")
     ap.add_argument("--kt", action="store_true",
@@ -709,15 +710,18 @@ def main():
     det_host = torch.empty_like(det_out, device="cpu").pin_memory()
     n_host = torch.empty(1, dtype=torch.int32).pin_memory()
     e2e_steps = args.e2e_steps if args.e2e_steps > 0 else max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e2e_tot = 0.0
     for i in range(e2e_steps):
+        flush.fill_(i & 255)                 # L2 flushed as in the device-timed steps (not timed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         echo.copy_(echo_host, non_blocking=True)
         step()
         det_host.copy_(det_out, non_blocking=True)
         n_host.copy_(n_out, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
+        e2e_tot += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_tot / e2e_steps, dev)
 
     # ---------------------------------------------------------------- plain GRFT, same hypotheses
     plain_ms = None
@@ -736,6 +740,22 @@ def main():
         b_ev.record(stream)
         torch.cuda.synchronize()
         plain_ms = a_ev.elapsed_time(b_ev) / args.plain_steps
+    # plain GRFT's error at this size: Y of the whole grid (the timed calls write P only)
+    # against the oracle on sampled (v, a) rows, every r0 bin (targets' rows included)
+    plain_err = None
+    if args.plain_steps > 0 and rank == 0 and not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(2)
+        pv = list(rng.integers(0, nv, 6)) + [int(round((t.v - pg.v.start) / pg.v.step)) for t in sc.targets[:2]]
+        pa = list(rng.integers(0, na, 6)) + [int(round((t.a - pg.a.start) / pg.a.step)) for t in sc.targets[:2]]
+        pv, pa = np.clip(pv, 0, nv - 1), np.clip(pa, 0, na - 1)
+        Ypl = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device=dev)
+        g.grft_plain(R, echo, pg_slab, Ypl, None)
+        Yg = Ypl[torch.as_tensor(pv, device=dev), torch.as_tensor(pa, device=dev)].cpu().numpy()
+        del Ypl
+        torch.cuda.empty_cache()
+        Ypo = oracle.grft_plain_rows(R, s, pg_slab, [int(x) for x in pv], [int(x) for x in pa])
+        plain_err = float(np.abs(Yg - Ypo).max() / np.abs(Ypo).max())
 
     # ---------------------------------------------------------------- standalone coarse RM gather
     # (kernel a materialising Z = s[m][n0 + rho_c(m)] w_c(m) for every cell: HBM-write bound)
@@ -776,18 +796,21 @@ def main():
         acc = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
 
     # ---------------------------------------------------------------- the other contraction modes
-    # (same step, same workload): fp16x1 = one FP16 product per MAC, not the split form of the
-    # headline; its value, contraction time and sampled error are reported beside it
+    # (same step, same workload): bf16x3 / fp16x3 = hi/lo split of both operands, three
+    # products per MAC; fp16x2 = hi/lo split of the gathered operand, the dechirp rounded once,
+    # two products; fp16x1 = one FP16 product per MAC (not a split form); fp32 = the SIMT
+    # contraction.  Each mode's value, contraction time, roofline and sampled error.
     others = {}
-    if world == 1 and args.other_precisions:
-        for op in [p for p in ("fp16x1", "bf16x3") if p != args.precision][:1]:
+    modes = [m for m in str(args.other_precisions).split(",") if m and m != args.precision]
+    if world == 1:
+        for op in modes:
             def step_o():
                 g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, op, None, P)
                 g.detect_peaks(P, cfar, args.topk, axes=pg, dr_m=R.dr_m, out=det_out, n_out=n_out)
-            for _ in range(args.warmup):
+            for _ in range(args.warmup if op != "fp32" else 1):
                 step_o()
             torch.cuda.synchronize()
-            k2 = max(3, args.steps // 2)
+            k2 = max(3, args.steps // 2) if op != "fp32" else 3
             evo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k2)]
             g.grft_timing(True)
             for i in range(k2):
@@ -805,13 +828,17 @@ def main():
                 g.dsgrft_fine_dfm(R, None, echo, ds, 0, ncell, op, Y, None)
                 Yg = Y[torch.as_tensor(vf, device=dev), torch.as_tensor(af, device=dev)].cpu().numpy()
                 del Y
+                torch.cuda.empty_cache()
                 err_o = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
-            c_s = 1e-3 * mco / max(nco, 1)
-            alg_o = FLOP_PER_HYP_PULSE * units / max(nco / k2, 1)
-            peak_o = _peaks()[0].get("bf16_tflops", 1956.7)
-            others[op] = {"products_per_mac": 1 if op == "fp16x1" else 3, "value": units / (1e-3 * ms_o),
-                          "ms_per_step": ms_o, "contract_ms": 1e3 * c_s,
-                          "roofline_frac": alg_o / c_s / 1e12 / peak_o, "max_rel_peak_err": err_o, "steps": k2}
+            ent = {"products_per_mac": PRODUCTS_PER_MAC[op], "value": units / (1e-3 * ms_o),
+                   "ms_per_step": ms_o, "max_rel_peak_err": err_o, "steps": k2}
+            if nco > 0:                      # tensor-core modes: the contraction kernel's own events
+                c_s = 1e-3 * mco / nco
+                alg_o = FLOP_PER_HYP_PULSE * units / (nco / k2)
+                peak_o = _peaks()[0].get("bf16_tflops", 1930.4)
+                ent.update({"contract_ms": 1e3 * c_s, "roofline_frac": alg_o / c_s / 1e12 / peak_o,
+                            "tensor_pipe_frac": alg_o * PRODUCTS_PER_MAC[op] / c_s / 1e12 / peak_o})
+            others[op] = ent
 
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
@@ -840,7 +867,7 @@ def main():
         launches_per_step = 1
     alg_flops = FLOP_PER_HYP_PULSE * units / launches_per_step
     achieved = alg_flops / gemm_avg_s / 1e12
-    exec_factor = 3 if args.precision in ("bf16x3", "fp16x3") else 1   # products per MAC executed
+    exec_factor = PRODUCTS_PER_MAC[args.precision]   # products per MAC executed
     # the timed region is a fraction of a second of back-to-back steps: the burst figure
     # (cuBLAS timed alone) is the denominator, not the seconds-long power-capped loop
     peak = peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained"))
@@ -885,8 +912,8 @@ def main():
                      "peak_source": f"{src} {'bf16_tflops (burst)' if args.precision != 'fp32' else 'FP32 FFMA from SM count and max clock'}",
                      "algorithmic_flop_per_launch": alg_flops, "executed_flop_per_launch": alg_flops * exec_factor,
                      "tensor_pipe_frac": alg_flops * exec_factor / gemm_avg_s / 1e12 / peak,
-                     "traffic": (DRAM_TRAFFIC_PER_LAUNCH if (launches_per_step == 1 and args.cells == 0
-                                                             and args.precision != "fp32") else None),
+                     "traffic": (DRAM_TRAFFIC_PER_LAUNCH.get(args.precision)
+                                 if (launches_per_step == 1 and args.cells == 0) else None),
                      "ms": 1e3 * gemm_avg_s,
                      "launches_per_step": launches_per_step},
         "stages_ms": dict({"dsgrft_fine_dfm call": sum(gemm_ms) / len(gemm_ms),
@@ -894,7 +921,10 @@ def main():
                           **{f"{k} kernel": (v[1] / args.steps) for k, v in ktime.items() if v[0] > 0}),
         "plain_grft": None if plain_ms is None else {
             "value": plain_units / (1e-3 * plain_ms), "ms_per_step": plain_ms,
-            "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units)},
+            "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units),
+            "max_rel_peak_err": plain_err,
+            "note": "both forms execute 8 flop per hypothesis-pulse here (time-domain gather): the speedup is "
+                    "tensor cores against FP32 SIMT, not an operation-count reduction"},
         "kernels": kernel_rooflines,
         "max_rel_peak_err": acc,
         "other_precisions": others or None,

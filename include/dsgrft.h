@@ -80,9 +80,11 @@ typedef enum {
     GRFT_FP32 = 0,   /* FP32 SIMT contraction (FFMA) */
     GRFT_BF16X3 = 1, /* tcgen05 tensor cores, hi/lo-split BF16 operands, 3 products, FP32 accumulate */
     GRFT_FP16X3 = 2, /* tcgen05 tensor cores, hi/lo-split FP16 operands, 3 products, FP32 accumulate */
-    GRFT_FP16X1 = 3  /* tcgen05 tensor cores, FP16 operands (one rounding each), 1 product, FP32
+    GRFT_FP16X1 = 3, /* tcgen05 tensor cores, FP16 operands (one rounding each), 1 product, FP32
                         accumulate: not the split form; within the 2e-3-of-peak bound of the split
                         path on the benchmark workloads (measured errors in the tests) */
+    GRFT_FP16X2 = 4  /* tcgen05 tensor cores, FP16, hi/lo split of the gathered echo operand and the
+                        dechirp rounded once, 2 products (hi*hi + lo*hi), FP32 accumulate */
 } grft_precision;
 
 typedef enum { GRFT_GATHER_NEAREST = 0, GRFT_GATHER_LINEAR = 1 } grft_gather;
@@ -314,7 +316,7 @@ typedef struct {
 } grft_dsgrid3;
 
 /* The fused coarse gather + fine contraction of dsgrft_fine_dfm (Z = NULL) for a P = 3 grid,
- * on the tensor cores (GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X1; GRFT_FP32 returns
+ * on the tensor cores (GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X2, GRFT_FP16X1; GRFT_FP32 returns
  * GRFT_EUNSUPPORTED):
  *   Y(n0; c, f) = exp(j 4 pi n0 dr / lambda) sum_m s[m][n0 + rho_c(m)] w_c(m) D[m][f],
  *   D[m][f] = exp(j 4 pi d(dv_k, da_q, db_u, t_m) / lambda).

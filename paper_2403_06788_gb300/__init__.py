@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X1, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_LINEAR,
+from ._abi import (DET_BYTES, GRFT_BF16X3, GRFT_FP16X1, GRFT_FP16X2, GRFT_FP16X3, GRFT_FP32, GRFT_GATHER_LINEAR,
                    GRFT_GATHER_NEAREST, PRECISIONS, GrftError, check, load)
 
 __all__ = ["dsgrft3_fine_dfm", "dsgrft3", "dsgrft_coarse_rm_fd_ex", "dsgrft_fine_dfm_fd", "dsgrft_fd", "dskt_keystone", "spectral_slots", "dskt_coarse_rm", "dskt_fine_dfm_fft", "dskt_mfp", "dsktmfp",
@@ -25,7 +25,7 @@ __all__ = ["dsgrft3_fine_dfm", "dsgrft3", "dsgrft_coarse_rm_fd_ex", "dsgrft_fine
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "dsgrft_coarse_rm_fd", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
-           "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_FP16X1", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
+           "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_FP16X1", "GRFT_FP16X2", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
 
 DET_DTYPE = np.dtype([("idx", "<i8"), ("n0", "<i4"), ("vi", "<i4"), ("ai", "<i4"), ("p", "<f4"),
                       ("r0_m", "<f8"), ("v", "<f8"), ("a", "<f8")])

@@ -13,10 +13,11 @@ _lib = None
 
 GRFT_OK, GRFT_EINVAL, GRFT_ENOMEM, GRFT_ECUDA, GRFT_ETIMEOUT, GRFT_EUNSUPPORTED, GRFT_EOVERFLOW = (
     0, -1, -2, -3, -4, -5, -6)
-GRFT_FP32, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X1 = 0, 1, 2, 3
+GRFT_FP32, GRFT_BF16X3, GRFT_FP16X3, GRFT_FP16X1, GRFT_FP16X2 = 0, 1, 2, 3, 4
 GRFT_GATHER_NEAREST, GRFT_GATHER_LINEAR = 0, 1
 BANDS = {"baseband": 0, "positive": 1}
-PRECISIONS = {"fp32": GRFT_FP32, "bf16x3": GRFT_BF16X3, "fp16x3": GRFT_FP16X3, "fp16x1": GRFT_FP16X1}
+PRECISIONS = {"fp32": GRFT_FP32, "bf16x3": GRFT_BF16X3, "fp16x3": GRFT_FP16X3, "fp16x1": GRFT_FP16X1,
+              "fp16x2": GRFT_FP16X2}
 KERNELS = {"tables": 0, "plain": 1, "coarse_rm": 2, "split": 3, "contract": 4, "contract_fp32": 5,
            "cfar": 6, "topk": 7, "adjoint": 8, "contract_fft": 9, "keystone": 10}
 

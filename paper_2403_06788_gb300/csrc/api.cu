@@ -458,8 +458,8 @@ int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *ec
     unsigned char *zp = dptr + 2 * d_bytes;
     uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
-    const bool fp16 = precision == GRFT_FP16X3 || precision == GRFT_FP16X1;
-    const int nprod = precision == GRFT_FP16X1 ? 1 : 3;
+    const bool fp16 = precision_fp16(precision);
+    const int nprod = precision_nprod(precision);
     if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo, rate))) return e;
     DsTcItem it;
     it.echo = (const float2 *)echo;
@@ -479,7 +479,7 @@ int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *ec
 }
 
 bool precision_ok(grft_precision p) {
-    return p == GRFT_FP32 || p == GRFT_BF16X3 || p == GRFT_FP16X3 || p == GRFT_FP16X1;
+    return p == GRFT_FP32 || p == GRFT_BF16X3 || p == GRFT_FP16X3 || p == GRFT_FP16X1 || p == GRFT_FP16X2;
 }
 
 }  // namespace
@@ -732,7 +732,9 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
                             const grft_batch_item *items, int32_t n_items, grft_precision precision,
                             void *stream) {
     if (!radar || !grid || !items || n_items <= 0 || n_items > 256) return GRFT_EINVAL;
-    if (precision != GRFT_BF16X3 && precision != GRFT_FP16X3 && precision != GRFT_FP16X1) return GRFT_EINVAL;
+    if (precision != GRFT_BF16X3 && precision != GRFT_FP16X3 && precision != GRFT_FP16X1 &&
+        precision != GRFT_FP16X2)
+        return GRFT_EINVAL;
     int Mmax = 0, Nmax = 0;
     long rpad_max = 0;
     for (int i = 0; i < n_items; ++i) {
@@ -781,8 +783,8 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     unsigned char *zp = dptr + 2 * d_bytes;
     uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
-    const bool fp16 = precision == GRFT_FP16X3 || precision == GRFT_FP16X1;
-    const int nprod = precision == GRFT_FP16X1 ? 1 : 3;
+    const bool fp16 = precision_fp16(precision);
+    const int nprod = precision_nprod(precision);
     if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
     if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;
     if ((e = launch_dechirp_split(c, R, g, Mpad, Fpad, fp16, Bhi, Blo))) return e;

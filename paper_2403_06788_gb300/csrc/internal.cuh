@@ -170,6 +170,12 @@ struct DsTcItem {
     int cell_begin, cell_count, i0;
 };
 int ds_tc_r0_pad(int r0_count);
+// Operand format and products per real MAC of a tensor-core precision (3: hi*hi + hi*lo +
+// lo*hi; 2: hi*hi + lo*hi with the dechirp rounded once; 1: hi*hi).
+inline bool precision_fp16(grft_precision p) {
+    return p == GRFT_FP16X3 || p == GRFT_FP16X1 || p == GRFT_FP16X2;
+}
+inline int precision_nprod(grft_precision p) { return p == GRFT_FP16X1 ? 1 : (p == GRFT_FP16X2 ? 2 : 3); }
 // Split coarse-RM pre-pass + tensor-core contraction for a list of items, in rounds whose
 // split operand (at most z_rows_cap rows of 2*Mpad 16-bit values per plane) fits one
 // buffer.  Tables rho/w are indexed [cell - tab_cell0][Mtab]; B planes are [2 Fpad][2 Mpad].
@@ -180,7 +186,7 @@ constexpr int DS_TC_MAX_ITEMS = 64;    // CPIs per tensor-core launch (kernel-pa
 int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsgrid &g,
                  const int32_t *rho, const float2 *w, int tab_cell0, int Mtab, const uint16_t *Bhi,
                  const uint16_t *Blo, int Mpad, bool fp16, int nprod, uint16_t *const Zhi[2],
-                 uint16_t *const Zlo[2], long z_rows_cap,    // nprod: 3 (split) or 1 (FP16 hi only)
+                 uint16_t *const Zlo[2], long z_rows_cap,    // nprod: 3, 2 or 1 products per real MAC
                  const Rate3 &rate = kNoRate);
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,

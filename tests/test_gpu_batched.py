@@ -59,7 +59,7 @@ SHAPES = [(100, 500, 0, 500), (256, 1200, 37, 1000), (333, 777, 100, 300), (64, 
           (1024, 2048, 512, 1024)]
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3", "fp16x1"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3", "fp16x2", "fp16x1"])
 def test_batched_equals_standalone_and_oracle(cuda_lib, precision):
     g = cuda_lib
     grid = _grid()

@@ -38,7 +38,7 @@ def test_precision_config_slab_bf16x3_and_fp16x3(cuda_lib):
     cell, fine = ds_rows_of_canonical(ds, np.array(vloc) + i_row * ds.Fv, np.array(af))
     Yo = oracle.dsgrft_rows(R, s, ds, cell, fine)
     errs = {}
-    for prec in ("bf16x3", "fp16x3", "fp16x1"):
+    for prec in ("bf16x3", "fp16x3", "fp16x2", "fp16x1"):
         Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device="cuda")
         g.dsgrft_fine_dfm(R, None, echo, ds, cb, cc, prec, Y, None)
         assert g.grft_sync_status() == 0

@@ -1,5 +1,6 @@
 """GPU parity of the DS-GRFT path (coarse RM gather, fine DFM contraction in FP32 SIMT and
-on the tensor cores in split BF16/FP16) against the FP64 oracle, through the C ABI."""
+on the tensor cores in split BF16/FP16, two-product split FP16 and single-product FP16)
+against the FP64 oracle, through the C ABI."""
 import dataclasses
 
 import numpy as np
@@ -13,7 +14,7 @@ from tests.helpers import TOL_FP32, TOL_SPLIT, rel_peak_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": TOL_FP32, "bf16x3": TOL_SPLIT, "fp16x3": TOL_SPLIT, "fp16x1": TOL_SPLIT}
+TOL = {"fp32": TOL_FP32, "bf16x3": TOL_SPLIT, "fp16x3": TOL_SPLIT, "fp16x2": TOL_SPLIT, "fp16x1": TOL_SPLIT}
 
 
 def _small_case(M=100, N=700, r0b=17, r0c=300, Fv=16, Fa=16, nvc=3, nac=2, seed=3):
@@ -26,7 +27,7 @@ def _small_case(M=100, N=700, r0b=17, r0c=300, Fv=16, Fa=16, nvc=3, nac=2, seed=
     return R, ds, s
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16x3", "fp16x1"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16x3", "fp16x2", "fp16x1"])
 def test_ds_fused_small_every_output(cuda_lib, precision):
     g = cuda_lib
     R, ds, s = _small_case()
@@ -40,8 +41,9 @@ def test_ds_fused_small_every_output(cuda_lib, precision):
     if precision in ("bf16x3", "fp16x3"):
         # the split path is far better than its 2e-3 bound; guard against silent regressions
         assert err <= 1e-4, err
-    if precision == "fp16x1":
-        # one FP16 rounding per operand: about 2^-12 per term, well inside the 2e-3 bound
+    if precision in ("fp16x2", "fp16x1"):
+        # one FP16 rounding of the dechirp (and, for fp16x1, of the echo operand): about
+        # 2^-12 per term, well inside the 2e-3 bound
         assert err <= 5e-4, err
 
 
@@ -110,12 +112,12 @@ def test_ds_fine_grid_padding_and_single_cell(cuda_lib):
     g = cuda_lib
     R, ds, s = _small_case(M=33, Fv=5, Fa=3, nvc=1, nac=1, r0c=129)
     es = torch.from_numpy(s).cuda()
-    for prec in ("fp32", "bf16x3", "fp16x3", "fp16x1"):
+    for prec in ("fp32", "bf16x3", "fp16x3", "fp16x2", "fp16x1"):
         Y = g.dsgrft(R, es, ds, precision=prec, want_Y=True, want_P=False)
         assert rel_peak_err(Y.cpu().numpy(), oracle.dsgrft_full(R, s, ds)) <= TOL[prec]
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp16x1"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x2", "fp16x1"])
 def test_ds_long_cpi_tables_from_global_memory(cuda_lib, precision):
     """M = 2100 pulses: more than the operand-split kernel stages in shared memory (2048), so it
     reads the cell's bins and phases from global memory; 66 pulse stages, the last partial."""
@@ -147,7 +149,7 @@ def test_ds_full_ds_m512_sampled(cuda_lib):
     from oracle.wrap import ds_rows_of_canonical
     cell, fine = ds_rows_of_canonical(ds, vf, af)
     Yo = oracle.dsgrft_rows(R, s, ds, cell, fine)
-    for prec in ("bf16x3", "fp32", "fp16x1"):
+    for prec in ("bf16x3", "fp16x2", "fp32", "fp16x1"):
         Y = g.dsgrft(R, es, ds, precision=prec, want_Y=True, want_P=False)
         assert g.grft_sync_status() == 0
         Yg = Y[torch.as_tensor(vf, device="cuda"), torch.as_tensor(af, device="cuda")].cpu().numpy()
