@@ -7,7 +7,7 @@ fine 64 x 16): FP64 tables, fused coarse-RM gather + fine-DFM tensor-core contra
 hypotheses is timed beside it (the DS speedup), and the FP64 oracle is timed on a bounded
 sample on the host cores.  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision bf16x3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp16x2]
 """
 from __future__ import annotations
 
@@ -37,6 +37,8 @@ FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
 # per precision.  None until a capture of the current kernel exists.
 DRAM_TRAFFIC_PER_LAUNCH = {}
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
+# arithmetic type of the contraction's operands (accumulation is FP32 in every mode)
+DTYPE = {"bf16x3": "bf16", "fp16x3": "f16", "fp16x2": "f16", "fp16x1": "f16", "fp32": "f32"}
 
 
 def _peaks():
@@ -223,11 +225,41 @@ def _timed(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def _contract_roofline(g, units, fn, steps, stream):
+    """Run fn `steps` times with the library's per-kernel events on and return the roofline of
+    the tensor-core contraction over those calls: algorithmic FLOP (8 per hypothesis-pulse of
+    `units` per call) over the contraction kernel's own time, against the measured burst
+    BF16 rate (dense FP16 is the same rate), plus the other kernels' shares."""
+    torch = sys.modules["torch"]
+    torch.cuda.synchronize()
+    g.grft_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    kt = {k: g.grft_timing_get(k) for k in ("tables", "split", "contract", "cfar", "topk")}
+    g.grft_timing(False)
+    call_ms = a.elapsed_time(b) / steps
+    n_c, ms_c = kt["contract"]
+    peak = _peaks()[0].get("bf16_tflops", 1930.4)
+    r = {"call_ms": call_ms, "kernels_ms_per_call": {k: v[1] / steps for k, v in kt.items() if v[0] > 0}}
+    if n_c > 0 and ms_c > 0:
+        ach = FLOP_PER_HYP_PULSE * units * steps / (1e-3 * ms_c) / 1e12
+        r["roofline"] = {"bound": "tensor", "kernel": "k_ds_tc (all launches of the call)", "achieved": ach,
+                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches_per_call": n_c / steps,
+                         "peak_source": "measured bf16_tflops (burst); dense FP16 and BF16 rates are equal"}
+    return r
+
+
 def run_suite(args):
     """The other workloads of the method, one JSON line: the M=2048 x N=8192 precision case
     (one coarse-v row of cells per call, both split precisions, sampled error against the
-    oracle), 64 uneven CPIs in one graph-captured batched call (1024 range bins of interest
-    per CPI), the differentiation pipeline at M=1024 x N=4096 (forward, top-1000 CFAR,
+    oracle; and the whole 3.4e10-hypothesis grid with streamed detection), 64 uneven CPIs
+    with every range bin (groups of batched launches plus detection, one CUDA graph) and
+    with 1024 range bins of interest per CPI (one graph-captured batched call), the
+    differentiation pipeline at M=1024 x N=4096 (forward, top-1000 CFAR,
     adjoint, 20 refinement steps), the FFT form of the fine stage and the frequency-domain
     coarse stage against their dense / gather forms, and the keystone branch (DS-KT-MFP)
     over its 1.88e9-hypothesis grid."""
@@ -272,6 +304,98 @@ def run_suite(args):
                               "unit": UNIT, "full_grid_calls": ds.vc.count,
                               "range_migration": residual_migration(R, ds), **prec}
     del Y, echo
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ precision workload, whole grid, streamed detection
+    # every one of the 3.4e10 hypotheses: dsgrft_detect computes one coarse-v row of cells at a
+    # time into a slab buffer and scans it (halo rows from its neighbours), top 1000 overall
+    sc = synth.ds_precision_m2048()
+    R, ds = sc.radar, sc.ds
+    echo = torch.from_numpy(synth.make_echo(R, sc.targets, sc.seed)).to(dev)
+    cf = synth.CFAR(2, 16, 1e-6)
+    K = 1000
+    det = torch.zeros(K * g._abi.DET_BYTES, dtype=torch.uint8, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    units = ds.n_cells * ds.n_fine * ds.r0_count * R.M
+    full = {}
+    for p in ("fp16x2", "bf16x3"):
+        run = lambda: g.dsgrft_detect(R, echo, ds, p, cf, K, out=det, n_out=nout)
+        run()
+        r = _contract_roofline(g, units, run, 2, stream)
+        dets, total = g.decode_detections(det, nout, K)
+        pgd = ds.plain_equivalent()
+        found = 0
+        for t in sc.targets:        # a detection within one cell of the target on every axis
+            near = (np.abs(dets["r0_m"] / R.dr_m - t.r0_bins) <= 1.5) & \
+                (np.abs(dets["v"] - t.v) <= 1.5 * pgd.v.step) & (np.abs(dets["a"] - t.a) <= 1.5 * pgd.a.step)
+            found += int(near.any())
+        full[p] = dict(r, value=units / (1e-3 * r["call_ms"]), detections_total=total,
+                       targets_detected=f"{found} of {len(sc.targets)}", status=g.grft_sync_status())
+    out["precision_m2048_full"] = {
+        "workload": "DS-GRFT M=2048 x N=8192, coarse 32 x 8, fine 256 x 64, every r0 bin: 3.4e10 hypotheses "
+                    "(7.0e13 hypothesis-pulses) per call, streamed one coarse-v row of cells at a time into a "
+                    "slab buffer (4.3 GB) with CA-CFAR + local maximum + top 1000 over the whole grid; the "
+                    "137 GB power map is never held",
+        "unit": UNIT, "hypotheses": ds.n_cells * ds.n_fine * ds.r0_count, "pulses": R.M,
+        "range_migration": residual_migration(R, ds), **full}
+    del echo, det
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------ 64 CPIs, every r0 bin, one captured graph
+    # the 64 power maps (about 300 GB) do not fit at once: CPIs go in groups whose maps fit a
+    # 96 GiB buffer, each group one batched launch followed by a top-64 detection per CPI; the
+    # whole sequence is one CUDA graph
+    cpis = synth.ds_batch(n_cpi=64)
+    grid = cpis[0].ds
+    nvb, nab = grid.vc.count * grid.Fv, grid.ac.count * grid.Fa
+    budget = 96 << 30
+    Kc = 64
+    echoes = [torch.from_numpy(synth.make_echo(c.radar, c.targets, c.seed)).to(dev) for c in cpis]
+    groups, cur, used = [], [], 0
+    for k, c in enumerate(cpis):
+        nb = nvb * nab * c.radar.N * 4
+        if cur and used + nb > budget:
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append((k, used))
+        used += nb
+    groups.append(cur)
+    pbuf = torch.empty(budget // 4, dtype=torch.float32, device=dev)
+    dets_all = torch.zeros((len(cpis), Kc * g._abi.DET_BYTES), dtype=torch.uint8, device=dev)
+    n_all = torch.zeros((len(cpis), 1), dtype=torch.int32, device=dev)
+    units = sum(nvb * nab * c.radar.N * c.radar.M for c in cpis)
+
+    def run_all(prec):
+        for grp in groups:
+            items = []
+            for k, off in grp:
+                N = cpis[k].radar.N
+                P = pbuf[off // 4: off // 4 + nvb * nab * N].view(nvb, nab, N)
+                items.append({"echo": echoes[k], "P": P, "Y": None, "r0_begin": 0, "r0_count": N})
+            g.dsgrft_fine_dfm_batched(cpis[0].radar, grid, items, prec)
+            for (k, off), it in zip(grp, items):
+                g.detect_peaks(it["P"], cf, Kc, out=dets_all[k], n_out=n_all[k])
+
+    batch_full = {}
+    for p in ("fp16x2",):
+        run_all(p)                                   # sizes the workspaces, tunes the tiles
+        r = _contract_roofline(g, units, lambda: run_all(p), 1, stream)
+        side = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            run_all(p)
+        ms = _timed(graph.replay, 2, stream)
+        tot = n_all.cpu().numpy().ravel()
+        batch_full[p] = dict(r, graph_ms_per_call=ms, value=units / (1e-3 * ms), groups=len(groups),
+                             detections_per_cpi_min=int(tot.min()), detections_per_cpi_max=int(tot.max()),
+                             status=g.grft_sync_status())
+        del graph
+    out["batch_64_full"] = {
+        "workload": "64 CPIs, M ~ U{256..2048}, N ~ U{1024..8192}, coarse 32 x 8, fine 64 x 16, every r0 bin "
+                    "of every CPI (%.3g hypothesis-pulses); groups of CPIs whose maps fit 96 GiB, one batched "
+                    "launch and a top-64 CA-CFAR detection per CPI each, the whole sequence one CUDA graph" % units,
+        "unit": UNIT, "hypothesis_pulses": units, **batch_full}
+    del pbuf, echoes, dets_all
     torch.cuda.empty_cache()
 
     # ------------------------------------------------ 64 uneven CPIs, one captured batched call
@@ -504,51 +628,44 @@ def run_kt(args):
     return 0
 
 
+def pd_hit(vi, ai, n0s, j, k, n0) -> bool:
+    """A Monte-Carlo trial detects when some detection (vi, ai, n0s) lies within one cell of
+    the truth (j, k, n0) on every axis."""
+    vi, ai, n0s = (np.asarray(x).astype(np.int64) for x in (vi, ai, n0s))
+    return bool(((np.abs(vi - j) <= 1) & (np.abs(ai - k) <= 1) & (np.abs(n0s - n0) <= 1)).any())
+
+
 def run_pd(args):
     """Detection probability against SNR for plain GRFT, DS-GRFT (time-domain coarse gather
     and, as the paper computes it, frequency-domain coarse stage) and DS-KT-MFP (the paper's
     Monte-Carlo comparison, Sec. VI): M=256 x N=512, one target per trial at a random
     on-grid (r0, v, a), CN(0,1) noise, the fixed LRT threshold -M ln(Pfa) on |Y|^2 with the
     3x3x3 local maximum; a trial detects when a detection lies within one cell of the truth
-    on every axis.  The keystone grid (q in [-1, 1], 256 baseband bins of V_a / 256 = the
-    DS-GRFT fine velocity step) contains every DS-GRFT hypothesis.  One JSON line."""
+    on every axis (pd_hit).  The keystone grid (q in [-1, 1], 256 baseband bins of V_a / 256
+    = the DS-GRFT fine velocity step) contains every DS-GRFT hypothesis.  Trial inputs come
+    from synth.pd_trial (one seed per trial).  One JSON line."""
     import torch
     import paper_2403_06788_gb300 as g
     import synth
     dev = torch.device("cuda", 0)
     g.load()
-    R = synth.Radar(M=256, N=512, fc_hz=1.5e9, prf_hz=1000.0, dr_m=15.0)
-    ds = synth.DSGrid(0, R.N, synth.Axis(-87.5, 25.0, 8), synth.Axis(-10.0, 20.0, 2), 64, 8)
+    R, ds, ktg, cf = synth.pd_setup()
     pg = ds.plain_equivalent()
     nv, na = pg.v.count, pg.a.count
-    pfa_cell = 1e-6
-    thresh = -R.M * math.log(pfa_cell)               # |Y|^2 of noise alone ~ M Exp(1)
-    cf = synth.CFAR(2, 16, pfa_cell, fixed_thresh=thresh, mode=1)
     K = 64
     P = torch.empty((nv, na, R.N), device=dev)
-    ktg = synth.kt_grid(R, -1, 3, ds.ac, ds.Fa, 256)
     kpg = ktg.plain_equivalent()
     kv_off = int(round((pg.v.start - kpg.v.start) / kpg.v.step))   # same velocity lattice
     assert abs(kpg.v.step - pg.v.step) < 1e-12 and abs(kpg.v.start + kv_off * kpg.v.step - pg.v.start) < 1e-9
     Pk = torch.empty((kpg.v.count, na, R.N), device=dev)
     Zfd = torch.empty((ds.n_cells, R.M, R.N), dtype=torch.complex64, device=dev)
-    gen = torch.Generator(device=dev)
-    rng = np.random.default_rng(7000)
     snrs = [float(x) for x in args.pd_snr.split(",")]
-    margin = synth.walk_margin_bins(R, 100.0, 20.0) + 2
     res = {}
     for snr in snrs:
         hits = {"grft": 0, "dsgrft": 0, "dsgrft_fd": 0, "dsktmfp": 0}
         for trial in range(args.pd_trials):
-            j = int(rng.integers(1, nv - 1))
-            k = int(rng.integers(1, na - 1))
-            n0 = int(rng.integers(margin, R.N - margin))
-            tgt = synth.Target(float(n0), pg.v.start + j * pg.v.step, pg.a.start + k * pg.a.step,
-                               complex(10 ** (snr / 20) * np.exp(2j * np.pi * rng.uniform())))
-            sig = torch.from_numpy(synth.make_echo(R, [tgt], 0, noise=False)).to(dev)
-            gen.manual_seed(1_000_003 * (trial + 1) + int(1000 * (snr + 100)))
-            wn = torch.randn((R.M, R.N, 2), generator=gen, device=dev) * math.sqrt(0.5)
-            echo = (sig + torch.complex(wn[..., 0], wn[..., 1])).contiguous()
+            j, k, n0, s_np = synth.pd_trial(R, pg, snr, trial)
+            echo = torch.from_numpy(s_np).to(dev)
             for name in ("grft", "dsgrft", "dsgrft_fd", "dsktmfp"):
                 jt = j
                 if name == "grft":
@@ -566,9 +683,7 @@ def run_pd(args):
                     out, n = g.detect_peaks(Pk, cf, K)
                     jt = j + kv_off
                 dets, _ = g.decode_detections(out, n, K)
-                near = (np.abs(dets["n0"].astype(int) - n0) <= 1) & (np.abs(dets["vi"].astype(int) - jt) <= 1) & \
-                    (np.abs(dets["ai"].astype(int) - k) <= 1)
-                hits[name] += int(near.any())
+                hits[name] += int(pd_hit(dets["vi"], dets["ai"], dets["n0"], jt, k, n0))
         res[f"{snr:g}"] = {name: hits[name] / args.pd_trials for name in hits}
     print(json.dumps({"pd": {
         "workload": "M=256 x N=512, f_c 1.5 GHz, PRF 1 kHz; GRFT / DS-GRFT (time-domain gather; dsgrft_fd: "
@@ -587,7 +702,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)   # about 0.5 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp16x2", "fp16x1", "fp32"])
+    ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "fp16x3", "fp16x2", "fp16x1", "fp32"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
@@ -897,7 +1012,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD if ncell == ds.n_cells else f"{WORKLOAD}, first {ncell} coarse cells",
                    "hypotheses": units // R.M, "pulses": R.M, "precision": args.precision,
                    "topk": args.topk, "cfar": "CA 2 guard / 16 train, pfa 1e-6",
@@ -909,7 +1024,9 @@ def main():
                                 "around each launch on its stream" if n_c > 0 else
                                 "dsgrft_fine_dfm call (tables + FP32 contraction)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"{src} {'bf16_tflops (burst)' if args.precision != 'fp32' else 'FP32 FFMA from SM count and max clock'}",
+                     "peak_source": f"{src} " + ("FP32 FFMA from SM count and max clock" if args.precision == "fp32"
+                                                 else "bf16_tflops (burst)" + (" x 1 (dense FP16 and BF16 tensor "
+                                                 "rates are equal)" if DTYPE[args.precision] == "f16" else "")),
                      "algorithmic_flop_per_launch": alg_flops, "executed_flop_per_launch": alg_flops * exec_factor,
                      "tensor_pipe_frac": alg_flops * exec_factor / gemm_avg_s / 1e12 / peak,
                      "traffic": (DRAM_TRAFFIC_PER_LAUNCH.get(args.precision)

@@ -346,6 +346,40 @@ int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft
                  const grft_grid *axes, double dr_m, int32_t K, grft_det *out, int32_t *n_out,
                  void *stream);
 
+/* detect_peaks over a map that is computed and scanned in slabs of whole v rows, so that the
+ * whole map never has to exist at once (Alg. 3's threshold scan over every hypothesis of a
+ * grid too large to hold):
+ *   detect_peaks_begin clears the device's candidate list;
+ *   detect_peaks_add scans one slab P[nv][na][nr0] (device) whose row r is v row v_base + r of
+ *     the whole map: only rows [v_lo, v_hi) may be detections, the other rows serve as the
+ *     neighbours of the 3x3x3 local maximum (a slab passes the rows bordering it on either
+ *     side, where they exist, as such halo rows); the candidates' linear indices are those of
+ *     the whole map, (v * na + a) * nr0 + n0;
+ *   detect_peaks_end writes the top K of every candidate added since begin, exactly as
+ *     detect_peaks would for the whole map (same records, same order, same total).
+ * The candidate list belongs to the device: no other detection call may run on that device
+ * between begin and end.  Candidates beyond 2^22 set GRFT_EOVERFLOW (grft_sync_status). */
+int detect_peaks_begin(void *stream);
+int detect_peaks_add(const float *P, int32_t nv, int32_t na, int32_t nr0, int32_t v_lo, int32_t v_hi,
+                     int64_t v_base, const grft_cfar *cfar, void *stream);
+int detect_peaks_end(int32_t na, int32_t nr0, const grft_grid *axes, double dr_m, int32_t K, grft_det *out,
+                     int32_t *n_out, void *stream);
+
+/* DS-GRFT with detection over the whole dual-scale grid (Alg. 3: coarse RM correction, fine
+ * DFM contraction, threshold scan, estimates), streamed one coarse-v row of cells at a time:
+ * the power map of cells [i * ac.count, (i + 1) * ac.count) (Fv v rows) is computed as in
+ * dsgrft_fine_dfm into one of two library-owned slab buffers, with the neighbouring slabs'
+ * border rows as halos, and scanned by detect_peaks_add; the whole map P is never held.
+ * Output: the top K detections of the whole map (records as detect_peaks with the plain
+ * grid of the same hypotheses as axes: v = vc.start - vc.step / 2 + vi vc.step / Fv, a
+ * likewise) and the total count, in device memory; identical to dsgrft_fine_dfm over every
+ * cell followed by detect_peaks.  Device memory: two slabs of (Fv + 2) x ac.count Fa x
+ * r0_count floats (workspace, kept until grft_release_workspace).  K <= 8192.  Capturable
+ * in a CUDA graph after one uncaptured call of the same shape. */
+int dsgrft_detect(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                  grft_precision precision, const grft_cfar *cfar, int32_t K, grft_det *out, int32_t *n_out,
+                  void *stream);
+
 /* Coherent sum along K continuous trajectories theta[k] = (r0_m, v, a) (device FP64
  * [K][3]) and its adjoint (no counterpart in the paper; gather: nearest bin or linear
  * interpolation between bins):

@@ -24,6 +24,7 @@ __all__ = ["dsgrft3_fine_dfm", "dsgrft3", "dsgrft_coarse_rm_fd_ex", "dsgrft_fine
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "dsgrft_coarse_rm_fd", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
+           "detect_peaks_begin", "detect_peaks_add", "detect_peaks_end", "dsgrft_detect",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
            "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_FP16X1", "GRFT_FP16X2", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
 
@@ -320,6 +321,49 @@ def detect_peaks(P, cfar, K, axes=None, dr_m=0.0, out=None, n_out=None, stream=N
                               C.byref(A) if A is not None else None, float(dr_m), int(K),
                               _ptr(out, torch.uint8, "out"), _ptr(n_out, torch.int32, "n_out"),
                               _stream(stream)), "detect_peaks")
+    return out, n_out
+
+
+def _det_buffers(K, device, out, n_out):
+    if out is None:
+        out = torch.zeros(max(int(K), 1) * DET_BYTES, dtype=torch.uint8, device=device)
+    if n_out is None:
+        n_out = torch.zeros(1, dtype=torch.int32, device=device)
+    return out, n_out
+
+
+def detect_peaks_begin(stream=None):
+    check(load().detect_peaks_begin(_stream(stream)), "detect_peaks_begin")
+
+
+def detect_peaks_add(P, v_lo, v_hi, v_base, cfar, stream=None):
+    """Scan slab P [nv][na][nr0] (rows v_base + r of the whole map); rows outside [v_lo, v_hi)
+    are the halo (neighbours only)."""
+    if P.dim() != 3:
+        raise ValueError("P must be [nv][na][nr0]")
+    nv, na, nr0 = (int(x) for x in P.shape)
+    Cf = _cfar(cfar)
+    check(load().detect_peaks_add(_ptr(P, torch.float32, "P"), nv, na, nr0, int(v_lo), int(v_hi), int(v_base),
+                                  C.byref(Cf), _stream(stream)), "detect_peaks_add")
+
+
+def detect_peaks_end(na, nr0, K, axes=None, dr_m=0.0, out=None, n_out=None, device="cuda", stream=None):
+    out, n_out = _det_buffers(K, device, out, n_out)
+    A = _grid(axes) if axes is not None else None
+    check(load().detect_peaks_end(int(na), int(nr0), C.byref(A) if A is not None else None, float(dr_m), int(K),
+                                  _ptr(out, torch.uint8, "out"), _ptr(n_out, torch.int32, "n_out"),
+                                  _stream(stream)), "detect_peaks_end")
+    return out, n_out
+
+
+def dsgrft_detect(radar, echo, grid, precision, cfar, K, out=None, n_out=None, stream=None):
+    """DS-GRFT over the whole dual-scale grid with streamed detection (the power map is never
+    held whole).  Returns (out, n_out) as detect_peaks."""
+    out, n_out = _det_buffers(K, echo.device, out, n_out)
+    R, G, Cf = _radar(radar), _dsgrid(grid), _cfar(cfar)
+    check(load().dsgrft_detect(C.byref(R), _ptr(echo, torch.complex64, "echo"), C.byref(G), _precision(precision),
+                               C.byref(Cf), int(K), _ptr(out, torch.uint8, "out"), _ptr(n_out, torch.int32, "n_out"),
+                               _stream(stream)), "dsgrft_detect")
     return out, n_out
 
 

@@ -56,8 +56,8 @@ long split_rows(long total_rows, long min_rows, long row_bytes, int &nbuf, bool 
 struct DevState {
     bool init = false;
     int *status = nullptr;
-    void *ws[WS_SLOTS] = {nullptr, nullptr};    // one workspace per operation class
-    size_t ws_size[WS_SLOTS] = {0, 0};
+    void *ws[WS_SLOTS] = {};                   // one workspace per operation class
+    size_t ws_size[WS_SLOTS] = {};
     int num_sms = 0;
     int cc = 0;
 };
@@ -89,16 +89,6 @@ int make_ctx(void *stream, Ctx &c) {
     c.wait_limit = g_wait_limit;
     c.num_sms = d.num_sms;
     return GRFT_OK;
-}
-
-bool radar_ok(const grft_radar *r) {
-    return r && r->M > 0 && r->N > 0 && std::isfinite(r->fc_hz) && r->fc_hz > 0 &&
-           std::isfinite(r->prf_hz) && r->prf_hz > 0 && std::isfinite(r->dr_m) && r->dr_m > 0 &&
-           std::isfinite(r->c_mps) && r->c_mps > 0;
-}
-
-bool axis_ok(const grft_axis &a) {
-    return a.count > 0 && std::isfinite(a.start) && std::isfinite(a.step);
 }
 
 bool dsgrid_ok(const grft_dsgrid *g, const grft_radar *r) {
@@ -817,6 +807,86 @@ int detect_peaks(const float *P, int32_t nv, int32_t na, int32_t nr0, const grft
     int e = make_ctx(stream, c);
     if (e) return e;
     return launch_detect(c, P, nv, na, nr0, *cfar, axes, dr_m, K, out, n_out);
+}
+
+int detect_peaks_begin(void *stream) {
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_detect_begin(c);
+}
+
+int detect_peaks_add(const float *P, int32_t nv, int32_t na, int32_t nr0, int32_t v_lo, int32_t v_hi,
+                     int64_t v_base, const grft_cfar *cfar, void *stream) {
+    if (!P || !cfar || nv <= 0 || na <= 0 || nr0 <= 0 || v_lo < 0 || v_hi > nv || v_lo > v_hi || v_base < 0 ||
+        (v_base + (int64_t)nv) * na * (int64_t)nr0 >= ((int64_t)1 << 62))
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_detect_scan(c, P, nv, na, nr0, v_lo, v_hi, (long long)v_base * na * nr0, *cfar);
+}
+
+int detect_peaks_end(int32_t na, int32_t nr0, const grft_grid *axes, double dr_m, int32_t K, grft_det *out,
+                     int32_t *n_out, void *stream) {
+    if (!n_out || na <= 0 || nr0 <= 0 || K < 0 || (K > 0 && !out)) return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_detect_select(c, na, nr0, axes, dr_m, K, out, n_out);
+}
+
+int dsgrft_detect(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
+                  grft_precision precision, const grft_cfar *cfar, int32_t K, grft_det *out, int32_t *n_out,
+                  void *stream) {
+    if (!radar_ok(radar) || !echo || !dsgrid_ok(grid, radar) || !precision_ok(precision) || !cfar || !n_out ||
+        K < 0 || (K > 0 && !out))
+        return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    const int nac = grid->ac.count, nvc = grid->vc.count, Fv = grid->Fv;
+    const long na = (long)nac * grid->Fa, nr0 = grid->r0_count;
+    if (na > 0x7fffffffL) return GRFT_EINVAL;
+    const size_t row = (size_t)na * nr0;              // floats per fine-v row of the map
+    const size_t slab = (size_t)(Fv + 2) * row;       // one coarse-v row of cells + a halo row each side
+    float *buf = (float *)workspace(c, 2 * slab * sizeof(float), WS_SLAB);
+    if (!buf) return GRFT_ENOMEM;
+    float *B[2] = {buf, buf + slab};
+    if ((e = launch_detect_begin(c))) return e;
+    if ((e = dsgrft_fine_dfm(radar, nullptr, echo, grid, 0, nac, precision, nullptr, B[0] + row, stream))) return e;
+    for (int i = 0; i < nvc; ++i) {
+        float *cur = B[i & 1], *nxt = B[(i + 1) & 1];
+        const bool has_next = i + 1 < nvc;
+        if (has_next) {
+            // slab i + 1 (it may overwrite nxt: the scan of slab i - 1 that read nxt is ordered
+            // before it on the stream), then the halo rows that slabs i and i + 1 share
+            if ((e = dsgrft_fine_dfm(radar, nullptr, echo, grid, (i + 1) * nac, nac, precision, nullptr, nxt + row,
+                                     stream)))
+                return e;
+            if (cudaMemcpyAsync(cur + (size_t)(Fv + 1) * row, nxt + row, row * sizeof(float),
+                                cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess ||
+                cudaMemcpyAsync(nxt, cur + (size_t)Fv * row, row * sizeof(float), cudaMemcpyDeviceToDevice,
+                                c.stream) != cudaSuccess)
+                return GRFT_ECUDA;
+        }
+        const int v_lo = i > 0 ? 1 : 0;                // row 0 of cur is the previous slab's last row
+        const float *P = i > 0 ? cur : cur + row;
+        const int nv = Fv + v_lo + (has_next ? 1 : 0);
+        const long long v_base = (long long)i * Fv - v_lo;
+        if ((e = launch_detect_scan(c, P, nv, (int)na, (int)nr0, v_lo, v_lo + Fv, v_base * na * nr0, *cfar)))
+            return e;
+    }
+    grft_grid axes = {};                              // the plain grid of the same hypotheses
+    axes.r0_begin = grid->r0_begin;
+    axes.r0_count = grid->r0_count;
+    axes.v.start = grid->vc.start - 0.5 * grid->vc.step;
+    axes.v.step = grid->vc.step / Fv;
+    axes.v.count = nvc * Fv;
+    axes.a.start = grid->ac.start - 0.5 * grid->ac.step;
+    axes.a.step = grid->ac.step / grid->Fa;
+    axes.a.count = (int32_t)na;
+    return launch_detect_select(c, (int)na, (int)nr0, &axes, radar->dr_m, K, out, n_out);
 }
 
 int dsgrft_backward(const grft_radar *radar, const grft_c32 *echo, int32_t K, const double *theta,

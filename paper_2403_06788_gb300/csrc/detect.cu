@@ -33,6 +33,8 @@ constexpr long CAND_CAP = 1L << 22;
 
 struct CfarParams {
     int nv, na, nr0, guard, train, mode;
+    int v_lo, v_hi;           // rows of v in [v_lo, v_hi) may be detections; the others are neighbours only
+    long long idx_off;        // added to a candidate's linear index in this map (global index of a slab)
     float fixed;
     float alpha[2 * 64 + 1];   // pfa^(-1/Nt) - 1 for Nt = 0..2*train
 };
@@ -122,6 +124,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
         }
         if (pass && n < nr0) pmask |= 1u << q;
     }
+    if (vi < cp.v_lo || vi >= cp.v_hi) pmask = 0;   // a halo row: its cells are neighbours only
     // local-maximum test and append (rare, compact): only warps with a candidate enter,
     // and every lane of such a warp runs all 16 iterations so the ballot is convergent
     if (__any_sync(0xffffffffu, pmask != 0)) {
@@ -155,7 +158,7 @@ __global__ __launch_bounds__(CF_THREADS) void k_cfar(const float *__restrict__ P
                     const long pos = (long)base + __popc(ballot & ((1u << lane) - 1));
                     if (pos < CAND_CAP) {
                         cand_p[pos] = p;
-                        cand_i[pos] = row * nr0 + n;
+                        cand_i[pos] = row * nr0 + n + cp.idx_off;
                     } else {
                         latch_error(status, GRFT_EOVERFLOW);
                     }
@@ -176,6 +179,7 @@ __device__ __forceinline__ void cfar_append(bool pass, const float *__restrict__
     const int nr0 = cp.nr0;
     if (pass) {
         const int vi = (int)(row / cp.na), ai = (int)(row % cp.na);
+        if (vi < cp.v_lo || vi >= cp.v_hi) pass = false;   // a halo row: neighbours only
         const long me = row * nr0 + n;
         for (int dv = -1; dv <= 1 && pass; ++dv)
             for (int da = -1; da <= 1 && pass; ++da)
@@ -198,7 +202,7 @@ __device__ __forceinline__ void cfar_append(bool pass, const float *__restrict__
         const long pos = (long)b0 + __popc(ballot & ((1u << lane) - 1));
         if (pos < CAND_CAP) {
             cand_p[pos] = p;
-            cand_i[pos] = row * nr0 + n;
+            cand_i[pos] = row * nr0 + n + cp.idx_off;
         } else {
             latch_error(status, GRFT_EOVERFLOW);
         }
@@ -676,29 +680,57 @@ __global__ __launch_bounds__(TOPK_THREADS) void k_topk(const int *__restrict__ c
 
 }  // namespace
 
-int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
-                  const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out) {
-    if (cfar.guard < 0 || cfar.train < 0 || cfar.guard + cfar.train + 1 > CF_MAXHALO ||
-        cfar.train > 64 || K < 0 || K > TOPK_SORT)
-        return GRFT_EINVAL;
-    if (cfar.mode == 0 && !(cfar.pfa > 0.0 && cfar.pfa < 1.0)) return GRFT_EINVAL;
+namespace {
+
+struct DetectWs {
+    int *count;
+    int64_t *cand_i;
+    float *cand_p;
+};
+
+bool detect_ws(const Ctx &c, DetectWs &w) {
     const size_t need = 256 + (size_t)CAND_CAP * (sizeof(float) + sizeof(int64_t));
     unsigned char *ws = (unsigned char *)workspace(c, need, WS_DETECT);
-    if (!ws) return GRFT_ENOMEM;
-    int *count = (int *)ws;
-    int64_t *cand_i = (int64_t *)(ws + 256);
-    float *cand_p = (float *)(ws + 256 + CAND_CAP * sizeof(int64_t));
-    if (cudaMemsetAsync(count, 0, sizeof(int), c.stream) != cudaSuccess) return GRFT_ECUDA;
+    if (!ws) return false;
+    w.count = (int *)ws;
+    w.cand_i = (int64_t *)(ws + 256);
+    w.cand_p = (float *)(ws + 256 + CAND_CAP * sizeof(int64_t));
+    return true;
+}
+
+bool cfar_ok(const grft_cfar &cfar) {
+    if (cfar.guard < 0 || cfar.train < 0 || cfar.guard + cfar.train + 1 > CF_MAXHALO || cfar.train > 64)
+        return false;
+    return !(cfar.mode == 0 && !(cfar.pfa > 0.0 && cfar.pfa < 1.0));
+}
+
+}  // namespace
+
+int launch_detect_begin(const Ctx &c) {
+    DetectWs w;
+    if (!detect_ws(c, w)) return GRFT_ENOMEM;
+    return cudaMemsetAsync(w.count, 0, sizeof(int), c.stream) == cudaSuccess ? GRFT_OK : GRFT_ECUDA;
+}
+
+int launch_detect_scan(const Ctx &c, const float *P, int nv, int na, int nr0, int v_lo, int v_hi,
+                       long long idx_off, const grft_cfar &cfar) {
+    if (!cfar_ok(cfar)) return GRFT_EINVAL;
+    DetectWs w;
+    if (!detect_ws(c, w)) return GRFT_ENOMEM;
+    int *count = w.count;
+    int64_t *cand_i = w.cand_i;
+    float *cand_p = w.cand_p;
 
     CfarParams cp;
     cp.nv = nv; cp.na = na; cp.nr0 = nr0; cp.guard = cfar.guard; cp.train = cfar.train;
     cp.mode = cfar.mode; cp.fixed = cfar.fixed_thresh;
+    cp.v_lo = v_lo; cp.v_hi = v_hi; cp.idx_off = idx_off;
     for (int i = 0; i <= 2 * 64; ++i) {
         cp.alpha[i] = (i == 0 || cfar.mode != 0) ? 0.f : (float)(pow(cfar.pfa, -1.0 / i) - 1.0);
     }
     const long rows = (long)nv * na;
     const int nseg = (nr0 + CF_SEG - 1) / CF_SEG;
-    if (rows > 0 && nr0 > 0) {
+    if (rows > 0 && nr0 > 0 && v_hi > v_lo) {
         KernelTimer kt(c, GRFT_KERNEL_CFAR);
         if (cfar.mode == 0 && cfar.guard == 2 && cfar.train == 16) {
             const int nch = (nr0 + CW_CHUNK - 1) / CW_CHUNK;
@@ -751,8 +783,16 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
         int e = check_launch();
         if (e) return e;
     }
+    return GRFT_OK;
+}
+
+int launch_detect_select(const Ctx &c, int na, int nr0, const grft_grid *axes, double dr, int K, grft_det *out,
+                         int32_t *n_out) {
+    if (K < 0 || K > TOPK_SORT) return GRFT_EINVAL;
+    DetectWs w;
+    if (!detect_ws(c, w)) return GRFT_ENOMEM;
     TopkParams tp;
-    tp.nv = nv; tp.na = na; tp.nr0 = nr0; tp.K = K;
+    tp.nv = 0; tp.na = na; tp.nr0 = nr0; tp.K = K;
     tp.has_axes = axes != nullptr;
     tp.r0_begin = axes ? axes->r0_begin : 0;
     tp.dr = dr;
@@ -767,8 +807,17 @@ int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const g
         attr_set[c.device] = true;
     }
     KernelTimer kt(c, GRFT_KERNEL_TOPK);
-    k_topk<<<1, TOPK_THREADS, smem, c.stream>>>(count, cand_p, cand_i, tp, out, n_out, c.status);
+    k_topk<<<1, TOPK_THREADS, smem, c.stream>>>(w.count, w.cand_p, w.cand_i, tp, out, n_out, c.status);
     return check_launch();
+}
+
+int launch_detect(const Ctx &c, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
+                  const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out) {
+    if (!cfar_ok(cfar) || K < 0 || K > TOPK_SORT) return GRFT_EINVAL;
+    int e;
+    if ((e = launch_detect_begin(c))) return e;
+    if ((e = launch_detect_scan(c, P, nv, na, nr0, 0, nv, 0, cfar))) return e;
+    return launch_detect_select(c, na, nr0, axes, dr, K, out, n_out);
 }
 
 }  // namespace grft

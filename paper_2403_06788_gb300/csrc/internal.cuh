@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "../../include/dsgrft.h"
 
 namespace grft {
@@ -98,10 +100,11 @@ struct Ctx {                  // per-call device context
 // grows).  Returns nullptr on allocation failure.
 // Per-device workspaces, grown on demand (a grow synchronises the device).  Slot 0 serves
 // the transforms (plain GRFT, coarse stages, fine stages), slot 1 the detection, so that a
-// detection and a transform of another CPI may run at the same time on two streams.
+// detection and a transform of another CPI may run at the same time on two streams; slot 2
+// holds the slab buffers of the streamed detector.
 void release_pipe(int dev);   // side stream and events of the split/contraction pipeline
-constexpr int WS_SLOTS = 2;
-constexpr int WS_TRANSFORM = 0, WS_DETECT = 1;
+constexpr int WS_SLOTS = 3;
+constexpr int WS_TRANSFORM = 0, WS_DETECT = 1, WS_SLAB = 2;
 void *workspace(const Ctx &ctx, size_t bytes, int slot = WS_TRANSFORM);
 
 // Launchers (each returns a grft status; they only enqueue work).
@@ -170,6 +173,15 @@ struct DsTcItem {
     int cell_begin, cell_count, i0;
 };
 int ds_tc_r0_pad(int r0_count);
+// Argument checks shared by the entry points: positive sizes, finite positive radar
+// parameters, a non-empty axis with finite start and step.
+inline bool radar_ok(const grft_radar *r) {
+    return r && r->M > 0 && r->N > 0 && std::isfinite(r->fc_hz) && r->fc_hz > 0 &&
+           std::isfinite(r->prf_hz) && r->prf_hz > 0 && std::isfinite(r->dr_m) && r->dr_m > 0 &&
+           std::isfinite(r->c_mps) && r->c_mps > 0;
+}
+inline bool axis_ok(const grft_axis &a) { return a.count > 0 && std::isfinite(a.start) && std::isfinite(a.step); }
+
 // Operand format and products per real MAC of a tensor-core precision (3: hi*hi + hi*lo +
 // lo*hi; 2: hi*hi + lo*hi with the dechirp rounded once; 1: hi*hi).
 inline bool precision_fp16(grft_precision p) {
@@ -191,6 +203,15 @@ int launch_ds_tc(const Ctx &, const DsTcItem *items, int n_items, const grft_dsg
 
 int launch_detect(const Ctx &, const float *P, int nv, int na, int nr0, const grft_cfar &cfar,
                   const grft_grid *axes, double dr, int K, grft_det *out, int32_t *n_out);
+// The same in three phases (a detection over a map computed in slabs): begin clears the
+// per-device candidate list; scan appends the candidates of rows [v_lo, v_hi) of one slab
+// of nv rows (the other rows are neighbours only), with idx_off added to their linear
+// indices; select sorts every candidate appended since begin into the top K.
+int launch_detect_begin(const Ctx &);
+int launch_detect_scan(const Ctx &, const float *P, int nv, int na, int nr0, int v_lo, int v_hi, long long idx_off,
+                       const grft_cfar &cfar);
+int launch_detect_select(const Ctx &, int na, int nr0, const grft_grid *axes, double dr, int K, grft_det *out,
+                         int32_t *n_out);
 
 int launch_backward(const Ctx &, const RadarD &, const float2 *echo, int K, const double *theta,
                     int gather, const float *gP, float *P, float2 *Y, double *g, float2 *gs);

@@ -37,10 +37,8 @@ using namespace grft;
 
 extern "C" int grft_plain_static(const grft_radar *radar, const grft_c32 *echo, const grft_grid *grid,
                                  grft_c32 *Y, float *P, void *stream) {
-    if (!radar || !echo || !grid || (!Y && !P) || radar->M <= 0 || radar->N <= 0 ||
-        !(radar->fc_hz > 0) || !(radar->prf_hz > 0) || !(radar->dr_m > 0) || !(radar->c_mps > 0) ||
-        grid->v.count <= 0 || grid->a.count <= 0 || grid->r0_count <= 0 || grid->r0_begin < 0 ||
-        (long)grid->r0_begin + grid->r0_count > radar->N)
+    if (!radar_ok(radar) || !echo || !grid || (!Y && !P) || !axis_ok(grid->v) || !axis_ok(grid->a) ||
+        grid->r0_count <= 0 || grid->r0_begin < 0 || (long)grid->r0_begin + grid->r0_count > radar->N)
         return GRFT_EINVAL;
     // size limits of the fixed scratch: the range phases plus at least one group of 8
     // hypotheses' tables must fit
@@ -77,6 +75,7 @@ extern "C" int grft_plain_static(const grft_radar *radar, const grft_c32 *echo, 
     const long nh_total = (long)grid->v.count * grid->a.count;
     long chunk = (long)((kStaticScratchBytes - e0_bytes - 512) / per_hyp);
     chunk = chunk / 8 * 8;
+    if (chunk > (1L << 18)) chunk = 1L << 18;   // the launch limit grft_plain applies (grid y <= 65535)
     if (chunk > nh_total) chunk = nh_total;
     float2 *e0 = reinterpret_cast<float2 *>(base);
     int32_t *rho = reinterpret_cast<int32_t *>(base + e0_bytes);

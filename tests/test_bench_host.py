@@ -56,3 +56,24 @@ def test_reference_arm_prints_the_contract_line(capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
 
+
+
+def test_pd_trials_are_replayable_and_hit_rule():
+    """Each Monte-Carlo trial is drawn from its own seed (replayable alone, distinct across
+    trials and SNRs), its target lies off the grid's edges, and the hit rule accepts a
+    detection within one cell of the truth on every axis and nothing farther."""
+    R, ds, _, cf = synth.pd_setup()
+    pg = ds.plain_equivalent()
+    a = synth.pd_trial(R, pg, -10.0, 3)
+    b = synth.pd_trial(R, pg, -10.0, 3)
+    c = synth.pd_trial(R, pg, -10.0, 4)
+    d = synth.pd_trial(R, pg, -12.0, 3)
+    assert a[:3] == b[:3] and np.array_equal(a[3], b[3])
+    assert not np.array_equal(a[3], c[3]) and not np.array_equal(a[3], d[3])
+    j, k, n0, s = a
+    assert 1 <= j < pg.v.count - 1 and 1 <= k < pg.a.count - 1 and 0 < n0 < R.N
+    assert s.shape == (R.M, R.N) and s.dtype == np.complex64
+    assert cf.mode == 1 and abs(cf.fixed_thresh + R.M * np.log(synth.PD_PFA)) < 1e-3
+    assert bench.pd_hit([j + 1], [k - 1], [n0 + 1], j, k, n0)
+    assert not bench.pd_hit([j + 2], [k], [n0], j, k, n0)
+    assert not bench.pd_hit([], [], [], j, k, n0)

@@ -53,8 +53,8 @@ def test_precision_config_slab_bf16x3_and_fp16x3(cuda_lib):
 
 def test_differentiation_config_pipeline(cuda_lib):
     """DS forward (bf16x3) -> CA-CFAR top-1000 -> 20 ascent steps with the adjoint (linear
-    gather).  Refined powers and points of 32 detections agree with the FP64 oracle's
-    refinement; gradients at the refined points agree with the oracle's to 1e-4 of scale."""
+    gather).  Refined powers and points of each of 32 detections agree with the FP64
+    oracle's refinement; gradients agree with the oracle's to 1e-4 of scale."""
     g = cuda_lib
     sc = synth.ds_adjoint_m1024()
     R, ds = sc.radar, sc.ds
@@ -78,9 +78,11 @@ def test_differentiation_config_pipeline(cuda_lib):
     sel = np.arange(min(32, th0.shape[0]))
     tho, Po = oracle.refine(R, s, th0[sel], cell, 20, mode=1)
     Pg = Pr.cpu().numpy()[sel]
-    assert np.median(np.abs(Pg - Po) / Po) <= 1e-3
+    rel = np.abs(Pg - Po) / Po
     d = np.abs(tht.cpu().numpy()[sel] - tho) / np.array(cell)
-    assert np.median(d.max(axis=1)) <= 0.05
+    print("config-5 refinement vs oracle: worst power difference", rel.max(), "worst distance (cells)", d.max())
+    assert np.all(rel <= 1e-3), rel
+    assert np.all(d.max(axis=1) <= 0.05), d
     # adjoint at the on-grid starting points (off the sub-grid peak, so the gradient is
     # well away from zero) against the FP64 gradient
     thr = th0[sel]

@@ -135,8 +135,9 @@ def test_adjoint_matches_oracle_gradient(cuda_lib, gather):
 
 
 def test_adjoint_central_differences(cuda_lib):
-    """dP/dtheta of the GPU adjoint against central differences (h = 1e-3 cell) of the GPU
-    forward, linear gather, at points where no gathered bin is crossed."""
+    """dP/dtheta of the GPU adjoint against central differences (h = 1e-3 cell, Richardson
+    extrapolated with h/2) of the FP64 forward, linear gather, at points where no gathered
+    bin is crossed: 1e-4 relative."""
     g = cuda_lib
     R, s, th, pg = _adj_case()
     es = torch.from_numpy(s).cuda()
@@ -146,9 +147,22 @@ def test_adjoint_central_differences(cuda_lib):
     g.dsgrft_backward(R, es, torch.from_numpy(th).cuda(), 1, grad_theta=gt)
     gg = gt.cpu().numpy()
     # the forward in FP32 cannot resolve h = 1e-3 cell differences to 1e-4: differentiate the
-    # FP64 oracle's forward instead and compare the GPU adjoint with it
+    # FP64 oracle's forward instead and compare the GPU adjoint with it.  The central
+    # difference at h = 1e-3 cell has a truncation error of up to about 1e-4 of the gradient
+    # (the phase turns by about 0.02 rad per step across the CPI), so the h and h/2
+    # differences are combined by Richardson extrapolation, (4 D(h/2) - D(h)) / 3, whose error
+    # is of fourth order in h
     t = np.arange(R.M) / R.prf_hz
-    ok = 0
+    ok, worst = 0, 0.0
+
+    def cdiff(k, j, h):
+        tp, tm = th[k].copy(), th[k].copy()
+        tp[j] += h
+        tm[j] -= h
+        Pp = oracle.trajectory_grad(R, s, tp[None], 1)[0][0]
+        Pm = oracle.trajectory_grad(R, s, tm[None], 1)[0][0]
+        return (Pp - Pm) / (2 * h)
+
     for k in range(K):
         for j in range(3):
             h = 1e-3 * cell[j]
@@ -159,12 +173,15 @@ def test_adjoint_central_differences(cuda_lib):
             xm = (tm[0] + tm[1] * t + 0.5 * tm[2] * t * t) / R.dr_m
             if np.any(np.floor(xp) != np.floor(xm)):
                 continue
-            Pp = oracle.trajectory_grad(R, s, tp[None], 1)[0][0]
-            Pm = oracle.trajectory_grad(R, s, tm[None], 1)[0][0]
-            fd = (Pp - Pm) / (2 * h)
+            fd = (4.0 * cdiff(k, j, 0.5 * h) - cdiff(k, j, h)) / 3.0
+            # 1e-4 relative; a gradient component within 1e-3 of its column's largest (near a
+            # peak, where the relative error of any finite-precision sum grows without bound)
+            # is compared at 1e-4 of that floor
             scale = max(abs(fd), 1e-3 * np.abs(gg[:, j]).max())
-            assert abs(gg[k, j] - fd) <= 1e-3 * scale + 1e-4 * np.abs(gg[:, j]).max()
+            worst = max(worst, abs(gg[k, j] - fd) / scale)
+            assert abs(gg[k, j] - fd) <= 1e-4 * scale, (k, j, gg[k, j], fd)
             ok += 1
+    print("adjoint vs central differences of the FP64 forward: worst relative error", worst, "over", ok)
     assert ok >= K
 
 
@@ -205,7 +222,9 @@ def test_refine_matches_oracle(cuda_lib):
     P0 = oracle.trajectory_grad(R, s, th0, 1)[0]
     Pg = Pg.cpu().numpy()
     assert np.all(Pg >= P0 * (1 - 1e-5))
-    # same final power (to the FP32 accept/reject noise) and same point to 0.05 cell
-    assert np.median(np.abs(Pg - Po) / Po) <= 1e-3
+    # every target: same final power and same point to 0.05 cell
+    rel = np.abs(Pg - Po) / Po
     d = np.abs(tht.cpu().numpy() - tho) / np.array(cell)
-    assert np.median(d.max(axis=1)) <= 0.05
+    print("refinement vs oracle: worst power difference", rel.max(), "worst distance (cells)", d.max())
+    assert np.all(rel <= 1e-3), rel
+    assert np.all(d.max(axis=1) <= 0.05), d
