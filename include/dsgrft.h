@@ -365,6 +365,18 @@ int detect_peaks_add(const float *P, int32_t nv, int32_t na, int32_t nr0, int32_
 int detect_peaks_end(int32_t na, int32_t nr0, const grft_grid *axes, double dr_m, int32_t K, grft_det *out,
                      int32_t *n_out, void *stream);
 
+/* Top K of the union of detection lists: n_lists lists of K_in records each (device memory,
+ * list l holding its min(K_in, totals[l]) strongest records, e.g. the top K_in of each slab
+ * or of each GPU a grid was split over, gathered into one buffer), sorted by power
+ * descending, ties by lower linear index.  Indices are unique across the lists (they index
+ * one map), so with K_in >= K the result is the top K of the whole map, and *n_out is the
+ * sum of totals[] (the whole map's total).  n_lists * K_in <= 8192, n_lists <= 1024;
+ * more records than that set GRFT_EOVERFLOW (grft_sync_status).  This is the merge step of
+ * a grid searched on several GPUs (each searches its own coarse cells; only these lists
+ * cross between them). */
+int detect_merge(const grft_det *lists, const int32_t *totals, int32_t n_lists, int32_t K_in, int32_t K,
+                 grft_det *out, int32_t *n_out, void *stream);
+
 /* DS-GRFT with detection over the whole dual-scale grid (Alg. 3: coarse RM correction, fine
  * DFM contraction, threshold scan, estimates), streamed one coarse-v row of cells at a time:
  * the power map of cells [i * ac.count, (i + 1) * ac.count) (Fv v rows) is computed as in

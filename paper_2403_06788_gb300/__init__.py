@@ -24,7 +24,7 @@ __all__ = ["dsgrft3_fine_dfm", "dsgrft3", "dsgrft_coarse_rm_fd_ex", "dsgrft_fine
            "grft_selftest_wait", "grft_timing", "grft_timing_get",
            "grft_bins_phases", "grft_plain", "grft_plain_static", "dsgrft_coarse_rm", "dsgrft_fine_dfm",
            "dsgrft_fine_dfm_batched", "dsgrft_fine_dfm_fft", "dsgrft_coarse_rm_fd", "detect_peaks", "dsgrft_backward", "dsgrft_refine",
-           "detect_peaks_begin", "detect_peaks_add", "detect_peaks_end", "dsgrft_detect",
+           "detect_peaks_begin", "detect_peaks_add", "detect_peaks_end", "detect_merge", "dsgrft_detect",
            "grft", "dsgrft", "decode_detections", "TrajectoryPower", "GrftError",
            "GRFT_FP32", "GRFT_BF16X3", "GRFT_FP16X3", "GRFT_FP16X1", "GRFT_FP16X2", "GRFT_GATHER_NEAREST", "GRFT_GATHER_LINEAR"]
 
@@ -353,6 +353,17 @@ def detect_peaks_end(na, nr0, K, axes=None, dr_m=0.0, out=None, n_out=None, devi
     check(load().detect_peaks_end(int(na), int(nr0), C.byref(A) if A is not None else None, float(dr_m), int(K),
                                   _ptr(out, torch.uint8, "out"), _ptr(n_out, torch.int32, "n_out"),
                                   _stream(stream)), "detect_peaks_end")
+    return out, n_out
+
+
+def detect_merge(lists, totals, K_in, K, out=None, n_out=None, stream=None):
+    """lists: uint8 CUDA buffer of n_lists * K_in grft_det records; totals: int32 CUDA tensor
+    [n_lists].  Returns (out, n_out): the top K of the union (see the header)."""
+    n_lists = int(totals.numel())
+    out, n_out = _det_buffers(K, totals.device, out, n_out)
+    check(load().detect_merge(_ptr(lists, torch.uint8, "lists"), _ptr(totals, torch.int32, "totals"), n_lists,
+                              int(K_in), int(K), _ptr(out, torch.uint8, "out"), _ptr(n_out, torch.int32, "n_out"),
+                              _stream(stream)), "detect_merge")
     return out, n_out
 
 

@@ -106,6 +106,7 @@ SIGNATURES = {
                                    C.POINTER(grft_cfar), _P]),
     "detect_peaks_end": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(grft_grid), C.c_double, C.c_int32, _P, _P,
                                    _P]),
+    "detect_merge": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
     "dsgrft_detect": (C.c_int, [C.POINTER(grft_radar), _P, C.POINTER(grft_dsgrid), C.c_int, C.POINTER(grft_cfar),
                                 C.c_int32, _P, _P, _P]),
     "dsgrft_backward": (C.c_int, [C.POINTER(grft_radar), _P, C.c_int32, _P, C.c_int, _P, _P, _P, _P,

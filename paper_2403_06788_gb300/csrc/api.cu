@@ -19,7 +19,7 @@ namespace {
 constexpr int MAX_DEV = 64;
 constexpr uint64_t DEFAULT_WAIT_LIMIT = 2000000000ull;   // ~1 s of SM cycles
 constexpr size_t PLAIN_TABLE_BUDGET = 256ull << 20;
-constexpr size_t SPLIT_OPERAND_DEFAULT = 4ull << 30;  // both planes of the split coarse-RM output
+constexpr size_t SPLIT_OPERAND_DEFAULT = 16ull << 30;  // both planes of the split coarse-RM output
 
 // Workspace budget of the split operand of the tensor-core DS path (both planes).  The
 // environment variable DSGRFT_SPLIT_BUDGET_BYTES overrides it (read once; smaller values
@@ -396,11 +396,35 @@ int dsgrft_coarse_rm(const grft_radar *radar, const grft_c32 *echo, const grft_d
 
 namespace {
 
+// Bytes of one plane of the dechirp operand D (the split modes keep a hi and a lo plane of
+// [2 Fpad][2 Mpad] 16-bit values; the FP32 contraction one [M][F] complex plane).
+size_t dechirp_plane_bytes(const RadarD &R, const grft_dsgrid &g, const Rate3 &rate, bool tc) {
+    const int F = g.Fv * g.Fa * rate.Fb;
+    const int Fpad = (F + 127) / 128 * 128;
+    const int Mpad = (R.M + 31) / 32 * 32;
+    return tc ? align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t)) : align_up((size_t)R.M * F * sizeof(float2));
+}
+
+// D of the fine offsets of grid (eq. H-DFM) in the layout of the precision: two planes of
+// dechirp_plane_bytes at dst for the tensor-core modes, one for FP32.
+int fill_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, const Rate3 &rate, grft_precision precision,
+                 unsigned char *dst) {
+    const bool tc = precision != GRFT_FP32;
+    if (!tc) return launch_dechirp(c, R, g, (float2 *)dst);
+    const int F = g.Fv * g.Fa * rate.Fb;
+    const int Fpad = (F + 127) / 128 * 128;
+    const int Mpad = (R.M + 31) / 32 * 32;
+    const size_t d_bytes = dechirp_plane_bytes(R, g, rate, true);
+    return launch_dechirp_split(c, R, g, Mpad, Fpad, precision_fp16(precision), (uint16_t *)dst,
+                                (uint16_t *)(dst + d_bytes), rate);
+}
+
 // The fine stage of dsgrft_fine_dfm (rate off) and dsgrft3_fine_dfm (P = 3, rate on): the
-// arguments are checked by the callers.
+// arguments are checked by the callers.  dechirp (nullable): D already in place, as
+// fill_dechirp writes it for this radar, grid, rate and precision (it is not recomputed).
 int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *echo, const grft_dsgrid *grid,
                   const Rate3 &rate, int32_t cell_begin, int32_t cell_count, grft_precision precision,
-                  grft_c32 *Y, float *P, void *stream) {
+                  grft_c32 *Y, float *P, void *stream, const unsigned char *dechirp = nullptr) {
     Ctx c;
     int e = make_ctx(stream, c);
     if (e) return e;
@@ -412,8 +436,7 @@ int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *ec
     const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));
     const size_t w_bytes = align_up((size_t)cell_count * R.M * sizeof(float2));
     const size_t e0_bytes = align_up((size_t)grid->r0_count * sizeof(float2));
-    const size_t d_bytes = tc ? align_up((size_t)2 * Fpad * 2 * Mpad * sizeof(uint16_t))
-                              : align_up((size_t)R.M * F * sizeof(float2));
+    const size_t d_bytes = dechirp_plane_bytes(R, *grid, rate, tc);
     // split operand: as many whole cells as fit the budget (at least one)
     const long row_bytes = 2L * Mpad * (long)sizeof(uint16_t);
     const long r0_pad = tc ? ds_tc_r0_pad(grid->r0_count) : 0;
@@ -440,17 +463,21 @@ int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *ec
         out.Fv = grid->Fv;
         out.Fa = grid->Fa;
         float2 *D = (float2 *)dptr;
-        if ((e = launch_dechirp(c, R, *grid, D))) return e;
+        if (dechirp)
+            D = (float2 *)dechirp;
+        else if ((e = fill_dechirp(c, R, *grid, rate, precision, dptr)))
+            return e;
         return launch_ds_simt(c, R, (const float2 *)echo, (const float2 *)Z, *grid, cell_count, rho, w,
                               D, e0, out);
     }
-    uint16_t *Bhi = (uint16_t *)dptr, *Blo = (uint16_t *)(dptr + d_bytes);
+    const unsigned char *dsrc = dechirp ? dechirp : dptr;
+    const uint16_t *Bhi = (const uint16_t *)dsrc, *Blo = (const uint16_t *)(dsrc + d_bytes);
     unsigned char *zp = dptr + 2 * d_bytes;
     uint16_t *const Zhi[2] = {(uint16_t *)zp, nbuf > 1 ? (uint16_t *)(zp + 2 * z_plane) : nullptr};
     uint16_t *const Zlo[2] = {(uint16_t *)(zp + z_plane), nbuf > 1 ? (uint16_t *)(zp + 3 * z_plane) : nullptr};
     const bool fp16 = precision_fp16(precision);
     const int nprod = precision_nprod(precision);
-    if ((e = launch_dechirp_split(c, R, *grid, Mpad, Fpad, fp16, Bhi, Blo, rate))) return e;
+    if (!dechirp && (e = fill_dechirp(c, R, *grid, rate, precision, dptr))) return e;
     DsTcItem it;
     it.echo = (const float2 *)echo;
     it.Z = (const float2 *)Z;
@@ -836,6 +863,15 @@ int detect_peaks_end(int32_t na, int32_t nr0, const grft_grid *axes, double dr_m
     return launch_detect_select(c, na, nr0, axes, dr_m, K, out, n_out);
 }
 
+int detect_merge(const grft_det *lists, const int32_t *totals, int32_t n_lists, int32_t K_in, int32_t K,
+                 grft_det *out, int32_t *n_out, void *stream) {
+    if (!lists || !totals || !n_out || n_lists <= 0 || K_in < 0 || K < 0 || (K > 0 && !out)) return GRFT_EINVAL;
+    Ctx c;
+    int e = make_ctx(stream, c);
+    if (e) return e;
+    return launch_detect_merge(c, lists, totals, n_lists, K_in, K, out, n_out);
+}
+
 int dsgrft_detect(const grft_radar *radar, const grft_c32 *echo, const grft_dsgrid *grid,
                   grft_precision precision, const grft_cfar *cfar, int32_t K, grft_det *out, int32_t *n_out,
                   void *stream) {
@@ -850,20 +886,28 @@ int dsgrft_detect(const grft_radar *radar, const grft_c32 *echo, const grft_dsgr
     if (na > 0x7fffffffL) return GRFT_EINVAL;
     const size_t row = (size_t)na * nr0;              // floats per fine-v row of the map
     const size_t slab = (size_t)(Fv + 2) * row;       // one coarse-v row of cells + a halo row each side
-    float *buf = (float *)workspace(c, 2 * slab * sizeof(float), WS_SLAB);
-    if (!buf) return GRFT_ENOMEM;
+    // the dechirp operand is the same for every slab: computed once, after the two slabs
+    const RadarD R = radar_d(*radar);
+    const size_t d_bytes = dechirp_plane_bytes(R, *grid, kNoRate, precision != GRFT_FP32);
+    const size_t slab_bytes = align_up(2 * slab * sizeof(float));
+    unsigned char *ws = (unsigned char *)workspace(c, slab_bytes + 2 * d_bytes, WS_SLAB);
+    if (!ws) return GRFT_ENOMEM;
+    float *buf = (float *)ws;
+    unsigned char *D = ws + slab_bytes;
     float *B[2] = {buf, buf + slab};
+    if ((e = fill_dechirp(c, R, *grid, kNoRate, precision, D))) return e;
+    auto slab_map = [&](int i, float *dst) {          // the power map of coarse-v row i
+        return fine_dfm_impl(radar, nullptr, echo, grid, kNoRate, i * nac, nac, precision, nullptr, dst, stream, D);
+    };
     if ((e = launch_detect_begin(c))) return e;
-    if ((e = dsgrft_fine_dfm(radar, nullptr, echo, grid, 0, nac, precision, nullptr, B[0] + row, stream))) return e;
+    if ((e = slab_map(0, B[0] + row))) return e;
     for (int i = 0; i < nvc; ++i) {
         float *cur = B[i & 1], *nxt = B[(i + 1) & 1];
         const bool has_next = i + 1 < nvc;
         if (has_next) {
             // slab i + 1 (it may overwrite nxt: the scan of slab i - 1 that read nxt is ordered
             // before it on the stream), then the halo rows that slabs i and i + 1 share
-            if ((e = dsgrft_fine_dfm(radar, nullptr, echo, grid, (i + 1) * nac, nac, precision, nullptr, nxt + row,
-                                     stream)))
-                return e;
+            if ((e = slab_map(i + 1, nxt + row))) return e;
             if (cudaMemcpyAsync(cur + (size_t)(Fv + 1) * row, nxt + row, row * sizeof(float),
                                 cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess ||
                 cudaMemcpyAsync(nxt, cur + (size_t)Fv * row, row * sizeof(float), cudaMemcpyDeviceToDevice,

@@ -678,6 +678,73 @@ __global__ __launch_bounds__(TOPK_THREADS) void k_topk(const int *__restrict__ c
     if (threadIdx.x == 0) *n_out = total;
 }
 
+// Merge of detection lists (the top-K lists of the slabs or ranks a map was split into; each
+// list sorted or not): the records of every list, up to min(K_in, totals[l]) from list l, are
+// sorted by power descending, index ascending (a bitonic sort in shared memory of the power,
+// the index and the record's position) and the first K written.  Linear indices are unique
+// across the lists, so the order is total and the result is the top K of the union.
+__global__ __launch_bounds__(TOPK_THREADS) void k_merge_dets(const grft_det *__restrict__ in,
+                                                             const int32_t *__restrict__ totals, int L, int K_in,
+                                                             int K, grft_det *__restrict__ out,
+                                                             int32_t *__restrict__ n_out, int *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int64_t *ki = reinterpret_cast<int64_t *>(smem);
+    float *kp = reinterpret_cast<float *>(smem + sizeof(int64_t) * TOPK_SORT);
+    int *kpos = reinterpret_cast<int *>(smem + (sizeof(int64_t) + sizeof(float)) * TOPK_SORT);
+    __shared__ int s_off[TOPK_THREADS + 1];
+    __shared__ long long s_total;
+    if (threadIdx.x == 0) {                  // list offsets (L <= TOPK_THREADS, checked by the launcher)
+        int off = 0;
+        long long tot = 0;
+        for (int l = 0; l < L; ++l) {
+            s_off[l] = off;
+            const int t = totals[l] > 0 ? totals[l] : 0;
+            off += t < K_in ? t : K_in;
+            tot += t;
+        }
+        s_off[L] = off;
+        s_total = tot;
+        if (off > TOPK_SORT) latch_error(status, GRFT_EOVERFLOW);
+    }
+    __syncthreads();
+    const int m = min(s_off[L], TOPK_SORT);
+    for (int l = 0; l < L; ++l)
+        for (int i = threadIdx.x; s_off[l] + i < min(s_off[l + 1], m); i += blockDim.x) {
+            const int slot = s_off[l] + i;
+            const grft_det &d = in[(long)l * K_in + i];
+            kp[slot] = d.p;
+            ki[slot] = d.idx;
+            kpos[slot] = l * K_in + i;
+        }
+    int np2 = 1;
+    while (np2 < m) np2 <<= 1;
+    for (int i = m + threadIdx.x; i < np2; i += blockDim.x) {
+        kp[i] = -1.0f;
+        ki[i] = INT64_MAX;
+        kpos[i] = -1;
+    }
+    __syncthreads();
+    for (int size = 2; size <= np2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool asc = (i & size) == 0;
+                    const bool sw = asc ? before(kp[j], ki[j], kp[i], ki[i]) : before(kp[i], ki[i], kp[j], ki[j]);
+                    if (sw) {
+                        const float tp = kp[i]; kp[i] = kp[j]; kp[j] = tp;
+                        const int64_t ti = ki[i]; ki[i] = ki[j]; ki[j] = ti;
+                        const int tq = kpos[i]; kpos[i] = kpos[j]; kpos[j] = tq;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    const int nw = min(K, m);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) out[i] = in[kpos[i]];
+    if (threadIdx.x == 0) *n_out = (int32_t)min(s_total, (long long)0x7fffffff);
+}
+
 }  // namespace
 
 namespace {
@@ -808,6 +875,24 @@ int launch_detect_select(const Ctx &c, int na, int nr0, const grft_grid *axes, d
     }
     KernelTimer kt(c, GRFT_KERNEL_TOPK);
     k_topk<<<1, TOPK_THREADS, smem, c.stream>>>(w.count, w.cand_p, w.cand_i, tp, out, n_out, c.status);
+    return check_launch();
+}
+
+int launch_detect_merge(const Ctx &c, const grft_det *lists, const int32_t *totals, int n_lists, int K_in, int K,
+                        grft_det *out, int32_t *n_out) {
+    if (n_lists <= 0 || n_lists > TOPK_THREADS || K_in < 0 || K < 0 || K > TOPK_SORT ||
+        (long)n_lists * K_in > TOPK_SORT)
+        return GRFT_EINVAL;
+    const size_t smem = (size_t)TOPK_SORT * (sizeof(int64_t) + sizeof(float) + sizeof(int));
+    static bool attr_set[64] = {false};
+    if (c.device < 64 && !attr_set[c.device]) {
+        if (cudaFuncSetAttribute(k_merge_dets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return GRFT_ECUDA;
+        attr_set[c.device] = true;
+    }
+    KernelTimer kt(c, GRFT_KERNEL_TOPK);
+    k_merge_dets<<<1, TOPK_THREADS, smem, c.stream>>>(lists, totals, n_lists, K_in, K, out, n_out, c.status);
     return check_launch();
 }
 

@@ -15,8 +15,9 @@
 // planes loaded or written.
 //
 // k_coarse_split (kernel a, the mGIFT of Alg. 1 in the time domain): one CTA per (cell,
-//   128-bin tile).  It gathers every bin's samples at n0 + rho_c(m) from the L2-resident
-//   echo (one contiguous run of bins per pulse and warp), multiplies by the coarse phase
+//   128-bin tile), consecutive CTAs on the same bin tile of consecutive cells.  It gathers
+//   every bin's samples at n0 + rho_c(m) from the L2-resident window of the echo (one
+//   contiguous run of bins per pulse and warp), multiplies by the coarse phase
 //   w_c(m), splits hi/lo, transposes through a warp-private shared tile and writes the
 //   K-major operand Zs[cell][bin][k'] (two 16-bit planes) as whole 128-byte lines; the TMA
 //   loads of kernel b apply the 128-byte swizzle.  Done once per (cell, bin) instead of once
@@ -262,8 +263,11 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
     int *s_rho = reinterpret_cast<int *>(s_w + tab_cap);
     const TcItem &p = B.it[find_item_cta(B, blockIdx.x)];
     const int local = blockIdx.x - p.cta0;
-    const int mt = local % p.tiles_m;
-    const int cl = local / p.tiles_m;
+    // consecutive CTAs take the same bin tile of consecutive cells: the CTAs in flight gather
+    // from one window of the echo (the tile's bins plus the cells' shifts), which stays in L2
+    // even where the whole echo does not
+    const int cl = local % p.ncell;
+    const int mt = local / p.ncell;
     const int c = p.cell0 + cl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool fp16 = B.fp16 != 0;
@@ -789,17 +793,20 @@ int launch_gemm(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
 
 int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo,
                         long zrows, const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Fpad) {
+    // The BK = 32 shapes fill shared memory to its 227 KB limit with stages: the more bytes in
+    // flight, the more of the L2 latency the ring hides (the loads run at 42 % of the L2-to-SM
+    // bandwidth; the pipe waits on their latency, not their rate).
     if (b.nprod == 2) {   // lo plane of A only: 64 KB (BK 64) or 32 KB (BK 32) per stage of 256 columns
         switch (variant) {
             case 1: return launch_gemm<128, 4, 64, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            case 2: return launch_gemm<256, 6, 32, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 2: return launch_gemm<256, 7, 32, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
             default: return launch_gemm<256, 3, 64, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
         }
     }
     if (b.nprod == 1) {   // no lo planes: twice the stages in the same shared memory
         switch (variant) {
             case 1: return launch_gemm<128, 6, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
-            case 2: return launch_gemm<256, 8, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
+            case 2: return launch_gemm<256, 9, 32, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
             default: return launch_gemm<256, 4, 64, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Fpad);
         }
     }

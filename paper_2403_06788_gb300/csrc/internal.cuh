@@ -212,6 +212,9 @@ int launch_detect_scan(const Ctx &, const float *P, int nv, int na, int nr0, int
                        const grft_cfar &cfar);
 int launch_detect_select(const Ctx &, int na, int nr0, const grft_grid *axes, double dr, int K, grft_det *out,
                          int32_t *n_out);
+// The top K of the union of n_lists detection lists of K_in records each (device memory).
+int launch_detect_merge(const Ctx &, const grft_det *lists, const int32_t *totals, int n_lists, int K_in, int K,
+                        grft_det *out, int32_t *n_out);
 
 int launch_backward(const Ctx &, const RadarD &, const float2 *echo, int K, const double *theta,
                     int gather, const float *gP, float *P, float2 *Y, double *g, float2 *gs);
