@@ -352,7 +352,7 @@ int grft_plain(const grft_radar *radar, const grft_c32 *echo, const grft_grid *g
     const RadarD R = radar_d(*radar);
     const long nh_total = (long)grid->v.count * grid->a.count;
     long chunk = (long)(PLAIN_TABLE_BUDGET / ((size_t)R.M * (sizeof(int32_t) + sizeof(float2))));
-    chunk = chunk / 8 * 8;
+    chunk = chunk / 16 * 16;
     if (chunk < 8) chunk = 8;
     if (chunk > (1L << 18)) chunk = 1L << 18;
     if (chunk > nh_total) chunk = nh_total;

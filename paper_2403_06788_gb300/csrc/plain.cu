@@ -2,7 +2,7 @@
 //   Y[h][n0] = e0(n0) * sum_m s[m][n0 + rho_h(m)] * w_h(m)
 // FP32 SIMT.  A CTA owns a group of PL_H hypotheses and a tile of PL_THREADS*PL_J range
 // bins; each thread accumulates PL_J bins (32 apart, so warp accesses are contiguous) for
-// all PL_H hypotheses.  Bins and phases come from a per-chunk table (FP64-built).
+// all PL_H hypotheses (8 x 4 by default, 16 x 2 selectable).  Bins and phases come from a per-chunk table (FP64-built).
 // Consecutive hypotheses of a group are neighbouring accelerations, whose bin shift is
 // nearly always the same at a given pulse: a per-pulse flag marks the pulses where all of
 // them share the first one's shift (one row of samples, no per-hypothesis check); at the
@@ -11,6 +11,7 @@
 // the phase and the phase times j staged in shared memory), which rounds exactly as the
 // scalar form and halves the FMA instruction count.
 #include <climits>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -19,10 +20,7 @@ namespace grft {
 namespace {
 
 constexpr int PL_THREADS = 256;
-constexpr int PL_J = 4;
-constexpr int PL_H = 8;
 constexpr int PL_MCHUNK = 128;
-constexpr int PL_TILE = PL_THREADS * PL_J;
 
 // Paired FP32 arithmetic (two independent IEEE fma.rn per instruction).
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
@@ -39,10 +37,14 @@ __device__ __forceinline__ void ffma2(uint64_t &acc, uint64_t a, uint64_t b) {
     asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 
+// PL_H hypotheses per CTA, PL_J bins per thread: a gathered sample serves PL_H hypotheses
+// (the L2 gathers per FMA fall as PL_H grows) and the accumulators take 2 PL_H PL_J registers.
+template <int PL_H, int PL_J>
 __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     const float2 *__restrict__ echo, int M, int N, const int32_t *__restrict__ rho_tab,
     const float2 *__restrict__ w_tab, int nh, int r0_begin, int r0_count,
     const float2 *__restrict__ e0, float2 *__restrict__ Y, float *__restrict__ P) {
+    constexpr int PL_TILE = PL_THREADS * PL_J;
     __shared__ int s_rho[PL_MCHUNK][PL_H];
     __shared__ alignas(16) float2 s_w[PL_MCHUNK][PL_H];     // w
     __shared__ alignas(16) float2 s_jw[PL_MCHUNK][PL_H];    // j w = (-w.im, w.re)
@@ -51,8 +53,8 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
 
     const int h0 = blockIdx.y * PL_H;
     const int nhl = min(PL_H, nh - h0);
-    // bins of this thread: j0 + 32 q, q = 0..PL_J-1 (a warp covers 128 consecutive bins, so
-    // every load and store instruction of the warp is one contiguous 256-byte run)
+    // bins of this thread: j0 + 32 q, q = 0..PL_J-1 (a warp covers 32 PL_J consecutive bins,
+    // so every load and store instruction of the warp is one contiguous 256-byte run)
     const int j0 = blockIdx.x * PL_TILE + (threadIdx.x >> 5) * (32 * PL_J) + (threadIdx.x & 31);
     const int n0 = r0_begin + j0;
     const int n0_tile = r0_begin + blockIdx.x * PL_TILE;   // first bin of the CTA's tile
@@ -125,14 +127,21 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
             if (s_same[mm]) {                // CTA-uniform: one row of samples for all hypotheses
                 const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0]);
                 const ulonglong2 *jp = reinterpret_cast<const ulonglong2 *>(&s_jw[mm][0]);
+                // per accumulator the same two FMAs in the same order (im * (j w), then
+                // re * w); the 2 PL_J independent accumulators of a hypothesis pair take their
+                // first products before their second ones, so dependent FMAs sit 2 PL_J
+                // instructions apart
 #pragma unroll
                 for (int h2 = 0; h2 < PL_H / 2; ++h2) {
                     const ulonglong2 w2 = wp[h2], j2 = jp[h2];
 #pragma unroll
                     for (int j = 0; j < PL_J; ++j) {
                         ffma2(acc[2 * h2][j], si[j], j2.x);
-                        ffma2(acc[2 * h2][j], sr[j], w2.x);
                         ffma2(acc[2 * h2 + 1][j], si[j], j2.y);
+                    }
+#pragma unroll
+                    for (int j = 0; j < PL_J; ++j) {
+                        ffma2(acc[2 * h2][j], sr[j], w2.x);
                         ffma2(acc[2 * h2 + 1][j], sr[j], w2.y);
                     }
                 }
@@ -196,20 +205,42 @@ __global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
     }
 }
 
+template <int PL_H, int PL_J>
+int launch_plain_shape(const Ctx &c, const RadarD &R, const float2 *echo, const grft_grid &g, int nh,
+                       const int32_t *rho, const float2 *w, const float2 *e0, float2 *Yc, float *Pc) {
+    constexpr int PL_TILE = PL_THREADS * PL_J;
+    dim3 grid((g.r0_count + PL_TILE - 1) / PL_TILE, (nh + PL_H - 1) / PL_H);
+    KernelTimer kt(c, GRFT_KERNEL_PLAIN);
+    k_plain<PL_H, PL_J><<<grid, PL_THREADS, 0, c.stream>>>(echo, R.M, R.N, rho, w, nh, g.r0_begin, g.r0_count, e0,
+                                                          Yc, Pc);
+    return check_launch();
+}
+
+// Tile shape of k_plain: 8 hypotheses x 4 bins per thread by default; DSGRFT_PLAIN_SHAPE=16x2
+// selects 16 x 2 (the same arithmetic per output, so the same results bit for bit; measured
+// equal in time: the L2 gathers, which 16 x 2 halves per FMA, do not bound the kernel).
+int plain_shape() {
+    static const int v = [] {
+        const char *e = getenv("DSGRFT_PLAIN_SHAPE");
+        return (e && e[0] == '1') ? 0 : 1;
+    }();
+    return v;
+}
+
 }  // namespace
 
 // Y and P point at hypothesis h0 of the full output; the table holds hypotheses h0..h0+nh-1.
+// Each output's sum runs over the pulses in the same order with the same FMAs whatever the
+// group it falls in (a partial last group included), so the shape and the chunking do not
+// change any result.
 int launch_plain(const Ctx &c, const RadarD &R, const float2 *echo, const grft_grid &g, long h0,
                  int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,
                  float *P) {
     if (nh == 0 || g.r0_count == 0) return GRFT_OK;
-    dim3 grid((g.r0_count + PL_TILE - 1) / PL_TILE, (nh + PL_H - 1) / PL_H);
     float2 *Yc = Y ? Y + h0 * g.r0_count : nullptr;
     float *Pc = P ? P + h0 * g.r0_count : nullptr;
-    KernelTimer kt(c, GRFT_KERNEL_PLAIN);
-    k_plain<<<grid, PL_THREADS, 0, c.stream>>>(echo, R.M, R.N, rho, w, nh, g.r0_begin, g.r0_count,
-                                               e0, Yc, Pc);
-    return check_launch();
+    if (plain_shape() == 1) return launch_plain_shape<8, 4>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    return launch_plain_shape<16, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
 }
 
 }  // namespace grft

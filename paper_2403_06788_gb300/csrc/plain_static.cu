@@ -74,7 +74,7 @@ extern "C" int grft_plain_static(const grft_radar *radar, const grft_c32 *echo, 
     const RadarD R = radar_d(*radar);
     const long nh_total = (long)grid->v.count * grid->a.count;
     long chunk = (long)((kStaticScratchBytes - e0_bytes - 512) / per_hyp);
-    chunk = chunk / 8 * 8;
+    chunk = chunk >= 16 ? chunk / 16 * 16 : chunk / 8 * 8;   // at least 8 (checked above)
     if (chunk > (1L << 18)) chunk = 1L << 18;   // the launch limit grft_plain applies (grid y <= 65535)
     if (chunk > nh_total) chunk = nh_total;
     float2 *e0 = reinterpret_cast<float2 *>(base);

@@ -25,7 +25,7 @@ def test_sharded_lists_merge_to_whole_map(cuda_lib, world):
     echo = torch.from_numpy(s).cuda()
     pg = ds.plain_equivalent()
     cf = CFAR(2, 16, 1e-2)
-    K = 512
+    K = 128
     P = g.dsgrft(R, echo, ds, precision="fp16x2")
     whole = g.detect_peaks(P, cf, K, axes=pg, dr_m=R.dr_m)
     nvc, Fv = ds.vc.count, ds.Fv
