@@ -35,7 +35,7 @@ FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
-DRAM_TRAFFIC_PER_LAUNCH = {}
+DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (272.699392e6 + 218.627584e6)}   # k_ds_tc<256,3,64,2>
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
 # arithmetic type of the contraction's operands (accumulation is FP32 in every mode)
 DTYPE = {"bf16x3": "bf16", "fp16x3": "f16", "fp16x2": "f16", "fp16x1": "f16", "fp32": "f32"}

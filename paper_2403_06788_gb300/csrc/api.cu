@@ -14,6 +14,14 @@
 
 namespace grft {
 
+bool ds_pair_form(const Rate3 &rate) {
+    static const bool on = [] {
+        const char *e = getenv("DSGRFT_PAIR");
+        return !(e && e[0] == '0');
+    }();
+    return on && (!rate.on || (rate.Fb == 1 && rate.step == 0.0));
+}
+
 namespace {
 
 constexpr int MAX_DEV = 64;
@@ -406,7 +414,8 @@ size_t dechirp_plane_bytes(const RadarD &R, const grft_dsgrid &g, const Rate3 &r
 }
 
 // D of the fine offsets of grid (eq. H-DFM) in the layout of the precision: two planes of
-// dechirp_plane_bytes at dst for the tensor-core modes, one for FP32.
+// dechirp_plane_bytes at dst for the tensor-core modes (the pair form's [2 Spad][Mpad]
+// layout where ds_pair_form holds, which fits the 4M form's [2 Fpad][2 Mpad]), one for FP32.
 int fill_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, const Rate3 &rate, grft_precision precision,
                  unsigned char *dst) {
     const bool tc = precision != GRFT_FP32;
@@ -415,6 +424,11 @@ int fill_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, const Rate
     const int Fpad = (F + 127) / 128 * 128;
     const int Mpad = (R.M + 31) / 32 * 32;
     const size_t d_bytes = dechirp_plane_bytes(R, g, rate, true);
+    if (ds_pair_form(rate)) {
+        const int Spad = (pair_slot_count(g.Fv, g.Fa) + 127) / 128 * 128;
+        return launch_dechirp_pair(c, R, g, Mpad, Spad, precision_fp16(precision), (uint16_t *)dst,
+                                   (uint16_t *)(dst + d_bytes), rate);
+    }
     return launch_dechirp_split(c, R, g, Mpad, Fpad, precision_fp16(precision), (uint16_t *)dst,
                                 (uint16_t *)(dst + d_bytes), rate);
 }
@@ -804,7 +818,9 @@ int dsgrft_fine_dfm_batched(const grft_radar *radar, const grft_dsgrid *grid,
     const int nprod = precision_nprod(precision);
     if ((e = launch_coarse_tables(c, R, g, 0, ncell, rho, w))) return e;
     if ((e = launch_range_phase(c, R, 0, Nmax, e0))) return e;
-    if ((e = launch_dechirp_split(c, R, g, Mpad, Fpad, fp16, Bhi, Blo))) return e;
+    if ((e = fill_dechirp(c, R, g, kNoRate, precision, (unsigned char *)Bhi))) return e;
+    (void)Blo;
+    (void)fp16;
     DsTcItem list[256];
     for (int i = 0; i < n_items; ++i) {
         const grft_batch_item &b = items[i];

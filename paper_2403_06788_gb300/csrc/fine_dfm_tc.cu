@@ -99,6 +99,7 @@ struct TcBatch {
     int Fb, nb_c;           // acceleration-rate axis (P = 3); 1, 1 for P = 2
     int fp16;
     int nprod;              // 3: hi*hi + hi*lo + lo*hi; 2: hi*hi + lo*hi; 1: hi*hi only
+    int slots;              // pair form: slots of mirrored hypotheses (pair_slot); 0 in the 4M form
     uint32_t idesc;
     int *status;
     uint64_t wait_limit;
@@ -631,6 +632,271 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// =========================================================================== kernel b, pair form
+// The contraction in the pair form (see pair_slot): tile = 64 range bins x 128 slots.  The A
+// tile interleaves each bin's real and imaginary parts (row 2 b: Re Z of bin b, row 2 b + 1:
+// Im Z): one box of the split operand through a 3-D tensor map (x: 32 pulses = one 64-byte
+// run of one part, y: 2 g + part, two of them, z: the operand row = bin).  The B tile holds
+// Re D and Im D of the slots' hypotheses (rows 2 s, 2 s + 1) over the same 32 pulses.  One
+// tcgen05.mma (M=128, N=256, K=16) per product and 16 pulses leaves, per bin and slot,
+// A = Zr Dr and C = Zr Di in TMEM lane 2 b and E = Zi Dr, B = Zi Di in lane 2 b + 1; the
+// epilogue swaps half of them between the two lanes by a shuffle and writes Y (and |Y|^2)
+// of each slot's hypothesis and its mirror: a complex MAC of a mirrored pair costs two real
+// MACs of one hypothesis in the 4M form.
+constexpr int PR_BINS = 64;                               // range bins per tile
+constexpr int PR_BK = 32;                                 // pulses per stage (64-byte rows)
+constexpr int PR_BN = 256;                                // B rows per tile (128 slots)
+constexpr uint32_t PR_A_BYTES = 2 * PR_BINS * PR_BK * 2;  // per plane (128 rows: re, im of 64 bins): 8 KB
+constexpr uint32_t PR_B_BYTES = PR_BN * PR_BK * 2;        // per plane: 16 KB
+constexpr size_t pr_stage_bytes(int NP) {
+    return (size_t)tc_planes_a(NP) * PR_A_BYTES + (size_t)tc_planes_b(NP) * PR_B_BYTES;
+}
+constexpr size_t pr_smem_bytes(int ST, int NP) { return (size_t)ST * pr_stage_bytes(NP) + 1024; }
+
+__device__ __forceinline__ const TcItem &decode_pair_unit(const TcBatch &b, int unit, int &nt, int &mt, int &cl) {
+    const TcItem &p = b.it[find_item_tile(b, unit)];
+    const int local = unit - p.tile0;
+    const int tm = (p.r0_count + PR_BINS - 1) / PR_BINS;
+    nt = local % b.tiles_n;
+    const int rest = local / b.tiles_n;
+    mt = rest % tm;
+    cl = rest / tm;
+    return p;
+}
+
+// Output row offset (canonical layout, bin 0) of fine hypothesis f of cell c, or -1.
+__device__ __forceinline__ long pair_row_offset(const TcBatch &B, const TcItem &p, int c, int f) {
+    if (f < 0) return -1;
+    const int iw = c % B.nb_c, c2 = c / B.nb_c;
+    const int iv = c2 / B.na_c - p.i0, il = c2 % B.na_c;
+    const int k = f / B.Fa, q = f % B.Fa;
+    const long na_full = (long)B.na_c * B.Fa, nb_full = (long)B.nb_c * B.Fb;
+    return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb) * p.r0_count;
+}
+
+template <int ST, int NP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_ds_pair(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+              const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+              const __grid_constant__ TcBatch B) {
+    constexpr uint32_t STAGE = (uint32_t)pr_stage_bytes(NP);
+    constexpr uint32_t B_OFF = tc_planes_a(NP) * PR_A_BYTES;
+    constexpr uint32_t TMEM_COLS = 2 * PR_BN;              // two accumulators
+    static_assert(NP >= 1 && NP <= 3, "three, two or one products per K step");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ alignas(8) uint64_t full[ST], empty[ST];
+    __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ volatile int abort_flag;
+    __shared__ volatile int s_fail;                        // an epilogue wait gave up (epilogue-uniform)
+    __shared__ long s_off_f[128], s_off_m[128];            // output rows of each slot's pair
+
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int cid = (int)blockIdx.x, ncl = (int)gridDim.x;
+
+    if (threadIdx.x == 0) {
+        tma_prefetch_desc(&mapAhi);
+        tma_prefetch_desc(&mapAlo);
+        tma_prefetch_desc(&mapBhi);
+        tma_prefetch_desc(&mapBlo);
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tmem_full[b], 1);
+            mbar_init(&tmem_empty[b], 128);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        s_fail = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_holder;
+    const uint64_t lim = B.wait_limit;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0, last_it = -1;
+            for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl) {
+                int nt, mt, cl;
+                const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
+                const int arow = (int)(p.zrow0 + (long)cl * p.r0_pad + mt * PR_BINS);
+                for (int kt = 0; kt < p.KT; ++kt, ++it) {
+                    const int s = it % ST;
+                    if (!mbar_wait_backoff(&empty[s], ((it / ST) & 1) ^ 1, lim, 32)) {
+                        latch_error(B.status, GRFT_ETIMEOUT);
+                        abort_flag = 1;
+                        break;
+                    }
+                    unsigned char *st = smem + s * STAGE;
+                    mbar_arrive_expect_tx(&full[s], STAGE);
+                    tma_load_3d(st, &mapAhi, 0, 2 * kt, arow, &full[s]);        // Re, Im Z of 64 bins
+                    if (NP >= 2) tma_load_3d(st + PR_A_BYTES, &mapAlo, 0, 2 * kt, arow, &full[s]);
+                    tma_load_2d(st + B_OFF, &mapBhi, kt * PR_BK, nt * PR_BN, &full[s]);
+                    if (NP == 3) tma_load_2d(st + B_OFF + PR_B_BYTES, &mapBlo, kt * PR_BK, nt * PR_BN, &full[s]);
+                    last_it = it;
+                }
+            }
+            for (int u = last_it; u >= 0 && u >= last_it - (ST - 1); --u)
+                mbar_wait(&full[u % ST], (u / ST) & 1, TC_DRAIN_LIMIT);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0, tcount = 0;
+            bool issued_any = false;
+            for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl, ++tcount) {
+                const int b = tcount & 1;
+                const int KT = B.it[find_item_tile(B, tile)].KT;
+                if (!mbar_wait(&tmem_empty[b], ((tcount >> 1) & 1) ^ 1, lim)) {
+                    latch_error(B.status, GRFT_ETIMEOUT);
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(b * PR_BN);
+                bool ok = true;
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const int s = it % ST;
+                    if (!mbar_wait(&full[s], (it / ST) & 1, lim)) {
+                        latch_error(B.status, GRFT_ETIMEOUT);
+                        abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * STAGE;
+                    const uint32_t a_hi = st, a_lo = st + PR_A_BYTES;
+                    const uint32_t b_hi = st + B_OFF, b_lo = b_hi + PR_B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < PR_BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;   // 16 pulses x 2 bytes inside the 64-byte row
+                        umma_f16(d_tmem, umma_desc<32>(a_hi + off), umma_desc<32>(b_hi + off), B.idesc,
+                                 (kt > 0 || kk > 0) ? 1u : 0u);
+                        if (NP == 3)
+                            umma_f16(d_tmem, umma_desc<32>(a_hi + off), umma_desc<32>(b_lo + off), B.idesc, 1u);
+                        if (NP >= 2)
+                            umma_f16(d_tmem, umma_desc<32>(a_lo + off), umma_desc<32>(b_hi + off), B.idesc, 1u);
+                    }
+                    issued_any = true;
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&tmem_full[b]);
+            }
+            if (issued_any) {
+                umma_commit(&drain_bar);
+                mbar_wait(&drain_bar, 0, TC_DRAIN_LIMIT);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // Thread (warp q4, lane) owns TMEM lane r = 32 q4 + lane: the real part (even lane) or
+        // the imaginary part (odd lane) of bin r / 2 of the tile.  Per 32-column chunk (16
+        // slots) the even lane keeps slots 0-7 and hands (A, C) of slots 8-15 to the odd lane,
+        // which keeps 8-15 and hands (E, B) of 0-7 back (one shuffle per value); both then
+        // write Y of their 8 slots' hypotheses and mirrors.  The named barriers run once per
+        // tile and are reached by all 128 epilogue threads: a wait that gives up is made known
+        // through s_fail before the barrier after it, and every warp then stops there.
+        const int q4 = warp & 3;
+        const int r = q4 * 32 + lane;
+        const bool odd = (lane & 1) != 0;
+        const int er = threadIdx.x - 64;          // 0..127 over the epilogue warps
+        bool aborted = false;
+        int tcount = 0;
+        for (int tile = cid; tile < B.total_tiles; tile += ncl, ++tcount) {
+            const int b = tcount & 1;
+            int nt, mt, cl;
+            const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
+            const int c = p.cell0 + cl;
+            named_bar_sync(1, 128);               // the previous tile's offsets are read
+            if (!aborted) {
+                const int slot = nt * (PR_BN / 2) + er;
+                int f = -1, fm = -1;
+                if (slot < B.slots) pair_slot(slot, B.Fv, B.Fa, f, fm);
+                s_off_f[er] = pair_row_offset(B, p, c, f);
+                s_off_m[er] = pair_row_offset(B, p, c, fm);
+            }
+            named_bar_sync(1, 128);
+            if (aborted) continue;
+            if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, B.status, 256) && lane == 0)
+                s_fail = 1;
+            named_bar_sync(1, 128);
+            if (s_fail) {                          // every epilogue warp stops here
+                aborted = true;
+                continue;
+            }
+            tc_fence_after();
+            const int j = mt * PR_BINS + (r >> 1);
+            const bool jok = j < p.r0_count;
+            float *const P = p.P;
+            float2 *const Y = p.Y;
+            const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
+            const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * PR_BN);
+#pragma unroll 1
+            for (int ch = 0; ch < PR_BN / 32; ++ch) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(taddr0 + ch * 32, v);
+                // own columns: 0-15 (even lane) or 16-31 (odd lane); the other half is swapped
+                float own[16], got[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
+                    own[i] = odd ? hi : lo;
+                    got[i] = __shfl_xor_sync(0xffffffffu, odd ? lo : hi, 1);
+                }
+                if (jok) {
+#pragma unroll
+                    for (int pp = 0; pp < 8; ++pp) {
+                        const int sl = ch * 16 + (odd ? 8 + pp : pp);
+                        // even lane: own = (A, C), got = (E, B); odd lane: own = (E, B), got = (A, C)
+                        const float A = odd ? got[2 * pp] : own[2 * pp];
+                        const float Cc = odd ? got[2 * pp + 1] : own[2 * pp + 1];
+                        const float E = odd ? own[2 * pp] : got[2 * pp];
+                        const float Bb = odd ? own[2 * pp + 1] : got[2 * pp + 1];
+                        const long of = s_off_f[sl], om = s_off_m[sl];
+                        if (of >= 0) {
+                            const float yr = A - Bb, yi = Cc + E;
+                            if (P) __stcs(P + of + j, yr * yr + yi * yi);
+                            if (Y) __stcs(Y + of + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                        }
+                        if (om >= 0) {
+                            const float yr = A + Bb, yi = E - Cc;
+                            if (P) __stcs(P + om + j, yr * yr + yi * yi);
+                            if (Y) __stcs(Y + om + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tmem_empty[b]);
+        }
+    }
+
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 bool set_smem_attr(const void *fn, size_t bytes, int device, bool *done) {
     if (device < 64 && done[device]) return true;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
@@ -817,6 +1083,55 @@ int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint1
     }
 }
 
+// The pair form: one shape per product count, filling shared memory with stages (6 x 32 KB,
+// 4 x 48 KB, 8 x 24 KB).
+template <int ST, int NP>
+int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
+                const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
+    static bool attr[64] = {false};
+    const size_t smem = pr_smem_bytes(ST, NP);
+    static_assert(pr_smem_bytes(ST, NP) <= 227 * 1024 - 2048, "shared memory (with the static part)");
+    if (!set_smem_attr((const void *)k_ds_pair<ST, NP>, smem, c.device, attr)) return GRFT_ECUDA;
+    // A: the split operand seen as [row][2 Mpad / 32 runs][32 pulses] (run y = 2 g + part); a
+    // box of both parts of 64 rows lands as 128 rows (bin, part) of 64 bytes
+    const uint64_t dims[3] = {(uint64_t)PR_BK, 2ull * (uint64_t)(Mpad / PR_BK), (uint64_t)zrows};
+    const uint64_t strides[2] = {(uint64_t)PR_BK * 2, 4ull * (uint64_t)Mpad};
+    const uint32_t box[3] = {(uint32_t)PR_BK, 2, (uint32_t)PR_BINS};
+    CUtensorMap mzh, mzl, mbh, mbl;
+    if (!encode_tma_3d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, dims, strides, box,
+                       CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !encode_tma_3d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, dims, strides, box,
+                       CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, (uint64_t)Mpad, 2ull * Spad,
+                       (uint64_t)Mpad * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, (uint64_t)Mpad, 2ull * Spad,
+                       (uint64_t)Mpad * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_64B))
+        return GRFT_ECUDA;
+    TcBatch bb = b;
+    bb.tiles_n = Spad / (PR_BN / 2);
+    long units = 0;
+    for (int i = 0; i < bb.n_items; ++i) {
+        bb.it[i].tile0 = (int)units;
+        units += (long)bb.it[i].ncell * ((bb.it[i].r0_count + PR_BINS - 1) / PR_BINS) * bb.tiles_n;
+    }
+    if (units > 0x7fffffffL) return GRFT_EINVAL;
+    bb.total_tiles = (int)units;
+    const uint32_t fmt = bb.fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
+    bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(PR_BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
+    if (grid <= 0) return GRFT_OK;
+    KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
+    k_ds_pair<ST, NP><<<grid, TC_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
+    return check_launch();
+}
+
+int launch_pair_nprod(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
+                      const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
+    if (b.nprod == 1) return launch_pair<8, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    if (b.nprod == 2) return launch_pair<6, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    return launch_pair<4, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+}
+
 // One round = the split kernel over every (item, cell, bin tile) of the batch, then the
 // persistent GEMM over every (item, cell, bin tile, hypothesis tile).
 struct Round {
@@ -841,6 +1156,10 @@ int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
 
 int launch_round_gemm(const Ctx &c, const Round &rd, int Mpad, int Fpad, const uint16_t *Bhi,
                       const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
+    if (rd.b.slots > 0) {   // pair form (one shape per product count)
+        const int Spad = (rd.b.slots + PR_BN / 2 - 1) / (PR_BN / 2) * (PR_BN / 2);
+        return launch_pair_nprod(c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Spad);
+    }
     if (variant < 0) {   // autotune: time the tile shapes on this round of cells, keep the fastest
         variant = tune_variant(c, rd.b, [&](int v) {
             return launch_gemm_variant(v, c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Fpad);
@@ -911,6 +1230,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     b.nb_c = rate.count;
     b.fp16 = fp16 ? 1 : 0;
     b.nprod = nprod;
+    b.slots = ds_pair_form(rate) ? pair_slot_count(g.Fv, g.Fa) : 0;
     b.idesc = 0;                     // set per variant by launch_gemm
     b.status = c.status;
     b.wait_limit = c.wait_limit;

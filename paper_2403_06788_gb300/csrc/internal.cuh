@@ -72,6 +72,41 @@ struct Rate3 {
 };
 constexpr Rate3 kNoRate{false, 0.0, 0.0, 1, 1};
 
+// Pairs of mirrored fine hypotheses.  The fine offsets (2k - F)/2 x step/F of k and F - k
+// are exact negatives, so the dechirp rows of hypothesis (k, q) and of its mirror
+// (Fv - k, Fa - q), k, q >= 1, are complex conjugates: D[m][f'] = conj(D[m][f]) (the
+// displacement, and with it the phase, changes sign).  One contraction of the gathered
+// operand's real and imaginary parts against Re D[m][f] and Im D[m][f] gives both sums:
+//   A = sum Zr Dr, B = sum Zi Di, C = sum Zr Di, E = sum Zi Dr,
+//   Y(f) = (A - B) + j (C + E),  Y(f') = (A + B) + j (E - C).
+// The slots list every hypothesis once, with its mirror where it has one: slots [0, Fa) are
+// k = 0 (no mirror), [Fa, Fa + Fv - 1) are q = 0, k >= 1 (no mirror), and the rest walk the
+// k, q >= 1 rectangle of R = Fv - 1 rows and C = Fa - 1 columns in row-major order up to its
+// middle (the mirror of linear index l is R C - 1 - l; the middle one, when R C is odd, is
+// its own mirror: the zero offset).
+__host__ __device__ inline int pair_slot_count(int Fv, int Fa) {
+    const long rc = (long)(Fv - 1) * (Fa - 1);
+    return Fa + (Fv - 1) + (int)((rc + 1) / 2);
+}
+// Hypothesis f = k Fa + q of slot s and its mirror fm (-1 if none or itself).
+__host__ __device__ inline void pair_slot(int s, int Fv, int Fa, int &f, int &fm) {
+    fm = -1;
+    if (s < Fa) {
+        f = s;
+        return;
+    }
+    s -= Fa;
+    if (s < Fv - 1) {
+        f = (s + 1) * Fa;
+        return;
+    }
+    s -= Fv - 1;
+    const int C = Fa - 1;
+    const long lm = (long)(Fv - 1) * C - 1 - s;
+    f = (s / C + 1) * Fa + (s % C + 1);
+    if (lm != s) fm = (int)(lm / C + 1) * Fa + (int)(lm % C + 1);
+}
+
 // --------------------------------------------------------------------------- host side
 struct RadarD {     // radar constants as the kernels use them
     int M, N;
@@ -119,6 +154,14 @@ int launch_dechirp(const Ctx &, const RadarD &, const grft_dsgrid &, float2 *D);
 // Dechirp matrix in the K-major real-GEMM operand layout of the tensor-core kernel.
 int launch_dechirp_split(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Fpad,
                          bool fp16, uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
+// The pair form's dechirp operand (pair_slot): rows 2 s and 2 s + 1 hold Re D and Im D of
+// the slot's first hypothesis over the pulses (K-major, pulses contiguous, Mpad per row),
+// hi and lo planes of [2 Spad][Mpad]; padding slots and pulses are zero.
+int launch_dechirp_pair(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Spad, bool fp16,
+                        uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
+// Whether the tensor-core contraction of a grid runs in the pair form: P = 2 grids (also a
+// P = 3 grid whose one fine rate offset is zero); DSGRFT_PAIR=0 selects the 4M form.
+bool ds_pair_form(const Rate3 &rate);
 
 int launch_plain(const Ctx &, const RadarD &, const float2 *echo, const grft_grid &, long h0,
                  int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,
