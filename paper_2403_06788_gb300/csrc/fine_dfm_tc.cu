@@ -674,8 +674,11 @@ __device__ __forceinline__ long pair_row_offset(const TcBatch &B, const TcItem &
     return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb) * p.r0_count;
 }
 
+constexpr int PR_EPI_WARPS = 8;                           // two per TMEM lane quarter
+constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;        // producer, MMA issuer, epilogue
+
 template <int ST, int NP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(PR_THREADS, 1)
     k_ds_pair(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
               const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
               const __grid_constant__ TcBatch B) {
@@ -707,7 +710,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tmem_full[b], 1);
-            mbar_init(&tmem_empty[b], 128);
+            mbar_init(&tmem_empty[b], 32 * PR_EPI_WARPS);
         }
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
@@ -805,17 +808,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        // Thread (warp q4, lane) owns TMEM lane r = 32 q4 + lane: the real part (even lane) or
-        // the imaginary part (odd lane) of bin r / 2 of the tile.  Per 32-column chunk (16
-        // slots) the even lane keeps slots 0-7 and hands (A, C) of slots 8-15 to the odd lane,
-        // which keeps 8-15 and hands (E, B) of 0-7 back (one shuffle per value); both then
-        // write Y of their 8 slots' hypotheses and mirrors.  The named barriers run once per
-        // tile and are reached by all 128 epilogue threads: a wait that gives up is made known
-        // through s_fail before the barrier after it, and every warp then stops there.
+        // Eight warps, two per TMEM lane quarter (warp w reads lanes 32 (w mod 4) .. + 31), the
+        // first of the two taking the tile's chunks 0-3, the second chunks 4-7.  Thread (warp,
+        // lane) owns TMEM lane r = 32 q4 + lane: the real part (even lane) or the imaginary
+        // part (odd lane) of bin r / 2.  Per 32-column chunk (16 slots) the even lane keeps
+        // slots 0-7 and hands its columns of slots 8-15 to the odd lane, which keeps 8-15 and
+        // hands its columns of 0-7 back (one shuffle per value).  With X the lane's own pair
+        // of a slot and W the received one, the even lane holds (A, C) = X, (E, B) = W and the
+        // odd lane the reverse, so
+        //   U = (X0 - W1)^2 + (X1 + W0)^2,  V = (X0 + W1)^2 + (X1 - W0)^2
+        // are |Y(f)|^2, |Y(f')|^2 on the even lane and |Y(f')|^2, |Y(f)|^2 on the odd lane.  The
+        // named barriers run once per tile and are reached by every epilogue thread: a wait
+        // that gives up is made known through s_fail before the barrier after it.
+        constexpr int NT = 32 * PR_EPI_WARPS;
         const int q4 = warp & 3;
+        const int half = (warp - 2) >> 2;         // chunks [4 half, 4 half + 4)
         const int r = q4 * 32 + lane;
         const bool odd = (lane & 1) != 0;
-        const int er = threadIdx.x - 64;          // 0..127 over the epilogue warps
+        const int er = threadIdx.x - 64;          // 0..NT-1 over the epilogue warps
         bool aborted = false;
         int tcount = 0;
         for (int tile = cid; tile < B.total_tiles; tile += ncl, ++tcount) {
@@ -823,19 +833,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int nt, mt, cl;
             const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
             const int c = p.cell0 + cl;
-            named_bar_sync(1, 128);               // the previous tile's offsets are read
-            if (!aborted) {
-                const int slot = nt * (PR_BN / 2) + er;
+            named_bar_sync(1, NT);                // the previous tile's offsets are read
+            if (!aborted) {                       // thread er: slot er mod 128, hypothesis or mirror
+                const int slot = nt * (PR_BN / 2) + (er & 127);
                 int f = -1, fm = -1;
                 if (slot < B.slots) pair_slot(slot, B.Fv, B.Fa, f, fm);
-                s_off_f[er] = pair_row_offset(B, p, c, f);
-                s_off_m[er] = pair_row_offset(B, p, c, fm);
+                if (er < 128)
+                    s_off_f[er] = pair_row_offset(B, p, c, f);
+                else
+                    s_off_m[er - 128] = pair_row_offset(B, p, c, fm);
             }
-            named_bar_sync(1, 128);
+            named_bar_sync(1, NT);
             if (aborted) continue;
             if (!warp_wait(&tmem_full[b], (tcount >> 1) & 1, lim, &abort_flag, B.status, 256) && lane == 0)
                 s_fail = 1;
-            named_bar_sync(1, 128);
+            named_bar_sync(1, NT);
             if (s_fail) {                          // every epilogue warp stops here
                 aborted = true;
                 continue;
@@ -848,37 +860,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
             const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * PR_BN);
 #pragma unroll 1
-            for (int ch = 0; ch < PR_BN / 32; ++ch) {
+            for (int ch = 4 * half; ch < 4 * half + 4; ++ch) {
                 uint32_t v[32];
                 __syncwarp();
                 tmem_ld32(taddr0 + ch * 32, v);
                 // own columns: 0-15 (even lane) or 16-31 (odd lane); the other half is swapped
-                float own[16], got[16];
+                float X[16], W[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
-                    own[i] = odd ? hi : lo;
-                    got[i] = __shfl_xor_sync(0xffffffffu, odd ? lo : hi, 1);
+                    X[i] = odd ? hi : lo;
+                    W[i] = __shfl_xor_sync(0xffffffffu, odd ? lo : hi, 1);
                 }
                 if (jok) {
 #pragma unroll
                     for (int pp = 0; pp < 8; ++pp) {
                         const int sl = ch * 16 + (odd ? 8 + pp : pp);
-                        // even lane: own = (A, C), got = (E, B); odd lane: own = (E, B), got = (A, C)
-                        const float A = odd ? got[2 * pp] : own[2 * pp];
-                        const float Cc = odd ? got[2 * pp + 1] : own[2 * pp + 1];
-                        const float E = odd ? own[2 * pp] : got[2 * pp];
-                        const float Bb = odd ? own[2 * pp + 1] : got[2 * pp + 1];
+                        const float x0 = X[2 * pp], x1 = X[2 * pp + 1], w0 = W[2 * pp], w1 = W[2 * pp + 1];
                         const long of = s_off_f[sl], om = s_off_m[sl];
-                        if (of >= 0) {
-                            const float yr = A - Bb, yi = Cc + E;
-                            if (P) __stcs(P + of + j, yr * yr + yi * yi);
-                            if (Y) __stcs(Y + of + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                        const long ou = odd ? om : of, ov = odd ? of : om;   // rows of U and V
+                        if (P) {
+                            const float ur = x0 - w1, ui = x1 + w0, vr = x0 + w1, vi = x1 - w0;
+                            if (ou >= 0) __stcs(P + ou + j, ur * ur + ui * ui);
+                            if (ov >= 0) __stcs(P + ov + j, vr * vr + vi * vi);
                         }
-                        if (om >= 0) {
-                            const float yr = A + Bb, yi = E - Cc;
-                            if (P) __stcs(P + om + j, yr * yr + yi * yi);
-                            if (Y) __stcs(Y + om + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                        if (Y) {                   // Y(f) and Y(f') from (A, B, C, E)
+                            const float A = odd ? w0 : x0, Cc = odd ? w1 : x1;
+                            const float E = odd ? x0 : w0, Bb = odd ? x1 : w1;
+                            if (of >= 0) {
+                                const float yr = A - Bb, yi = Cc + E;
+                                __stcs(Y + of + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                            }
+                            if (om >= 0) {
+                                const float yr = A + Bb, yi = E - Cc;
+                                __stcs(Y + om + j, make_float2(e.x * yr - e.y * yi, e.x * yi + e.y * yr));
+                            }
                         }
                     }
                 }
@@ -1121,7 +1137,7 @@ int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
     const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
     if (grid <= 0) return GRFT_OK;
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
-    k_ds_pair<ST, NP><<<grid, TC_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
+    k_ds_pair<ST, NP><<<grid, PR_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
     return check_launch();
 }
 
