@@ -35,8 +35,22 @@ FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
-DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (272.699392e6 + 218.627584e6)}   # k_ds_tc<256,3,64,2>
+DRAM_TRAFFIC_PER_LAUNCH = {}
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
+def executed_per_algorithmic(precision, Fv, Fa):
+    """Tensor FLOP the contraction executes per algorithmic FLOP (8 per hypothesis-pulse).  The
+    pair form (P = 2 grids) contracts each slot of mirrored hypotheses (every hypothesis once,
+    with its mirror where it has one: Fa + Fv - 1 + ceil((Fv - 1)(Fa - 1) / 2) slots, padded to
+    128) as four real MACs per pulse and product, i.e. 8 FLOP per slot-pulse and product."""
+    if precision == "fp32":
+        return 1.0
+    if os.environ.get("DSGRFT_PAIR", "1").startswith("0"):      # the 4M form
+        return float(PRODUCTS_PER_MAC[precision])
+    slots = Fa + (Fv - 1) + ((Fv - 1) * (Fa - 1) + 1) // 2
+    spad = -(-slots // 128) * 128
+    return PRODUCTS_PER_MAC[precision] * spad / float(Fv * Fa)
+
+
 # arithmetic type of the contraction's operands (accumulation is FP32 in every mode)
 DTYPE = {"bf16x3": "bf16", "fp16x3": "f16", "fp16x2": "f16", "fp16x1": "f16", "fp32": "f32"}
 
@@ -952,7 +966,8 @@ def main():
                 alg_o = FLOP_PER_HYP_PULSE * units / (nco / k2)
                 peak_o = _peaks()[0].get("bf16_tflops", 1930.4)
                 ent.update({"contract_ms": 1e3 * c_s, "roofline_frac": alg_o / c_s / 1e12 / peak_o,
-                            "tensor_pipe_frac": alg_o * PRODUCTS_PER_MAC[op] / c_s / 1e12 / peak_o})
+                            "tensor_pipe_frac": alg_o * executed_per_algorithmic(op, ds.Fv, ds.Fa) / c_s / 1e12
+                            / peak_o})
             others[op] = ent
 
     # ---------------------------------------------------------------- CPU oracle baseline
@@ -982,7 +997,7 @@ def main():
         launches_per_step = 1
     alg_flops = FLOP_PER_HYP_PULSE * units / launches_per_step
     achieved = alg_flops / gemm_avg_s / 1e12
-    exec_factor = PRODUCTS_PER_MAC[args.precision]   # products per MAC executed
+    exec_factor = executed_per_algorithmic(args.precision, ds.Fv, ds.Fa)   # executed / algorithmic FLOP
     # the timed region is a fraction of a second of back-to-back steps: the burst figure
     # (cuBLAS timed alone) is the denominator, not the seconds-long power-capped loop
     peak = peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained"))
@@ -1020,7 +1035,8 @@ def main():
                    "parallelism": f"{world} independent CPI(s), one per GPU",
                    "range_migration": residual_migration(R, ds)},
         "roofline": {"bound": "tensor" if args.precision != "fp32" else "alu",
-                     "kernel": ("k_ds_tc (tcgen05 split-operand contraction + |Y|^2 epilogue), CUDA events "
+                     "kernel": ("k_ds_pair (tcgen05 split-operand contraction, pair form of mirrored fine "
+                                "hypotheses, + |Y|^2 epilogue), CUDA events "
                                 "around each launch on its stream" if n_c > 0 else
                                 "dsgrft_fine_dfm call (tables + FP32 contraction)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -424,9 +424,9 @@ int fill_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, const Rate
     const int Fpad = (F + 127) / 128 * 128;
     const int Mpad = (R.M + 31) / 32 * 32;
     const size_t d_bytes = dechirp_plane_bytes(R, g, rate, true);
-    if (ds_pair_form(rate)) {
+    if (ds_pair_form(rate)) {   // [2 Spad][pair_mrow(M)] per plane: within d_bytes (Spad <= Fpad, Mrow <= 2 Mpad)
         const int Spad = (pair_slot_count(g.Fv, g.Fa) + 127) / 128 * 128;
-        return launch_dechirp_pair(c, R, g, Mpad, Spad, precision_fp16(precision), (uint16_t *)dst,
+        return launch_dechirp_pair(c, R, g, pair_mrow(R.M), Spad, precision_fp16(precision), (uint16_t *)dst,
                                    (uint16_t *)(dst + d_bytes), rate);
     }
     return launch_dechirp_split(c, R, g, Mpad, Fpad, precision_fp16(precision), (uint16_t *)dst,

@@ -327,14 +327,16 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
         }
         if (g == 3) {
             __syncwarp();
+            // the lane's 16-byte chunk ch = lane mod 8 of each row: 8 pulses of one part
+            const int ch = lane & 7;
+            const int col = kt * TC_BK + ch * 8;
             for (int pl = 0; pl < (with_lo ? 2 : 1); ++pl) {
                 uint16_t *Z = pl ? Zlo : Zhi;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int idx = q * 32 + lane, row = idx >> 3, ch = idx & 7;
+                    const int row = (q * 32 + lane) >> 3;
                     const uint4 x = tr[pl * 256 + row * 8 + (ch ^ (row & 7))];
-                    st_global_v4_hint(Z + (row0 + row) * (size_t)B.zld + kt * TC_BK + ch * 8, x.x, x.y, x.z, x.w,
-                                      pol_z);
+                    st_global_v4_hint(Z + (row0 + row) * (size_t)B.zld + col, x.x, x.y, x.z, x.w, pol_z);
                 }
             }
             __syncwarp();
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
     // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
     // of the tile is inside the r0 range and every gathered bin is inside the echo, so the
     // loop carries no bound checks.
-    if (tab_smem && (p.M % 32) == 0 && j0 + TC_BM <= p.r0_count &&
+    if (tab_smem && p.M == 32 * p.KT && j0 + TC_BM <= p.r0_count &&
         p.r0_begin + j0 + s_rng[0] >= 0 && p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
         const float2 *src = p.echo + nbase;
         const long N = p.N;
@@ -635,19 +637,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // =========================================================================== kernel b, pair form
 // The contraction in the pair form (see pair_slot): tile = 64 range bins x 128 slots.  The A
 // tile interleaves each bin's real and imaginary parts (row 2 b: Re Z of bin b, row 2 b + 1:
-// Im Z): one box of the split operand through a 3-D tensor map (x: 32 pulses = one 64-byte
-// run of one part, y: 2 g + part, two of them, z: the operand row = bin).  The B tile holds
-// Re D and Im D of the slots' hypotheses (rows 2 s, 2 s + 1) over the same 32 pulses.  One
+// Im Z): per stage of 64 pulses two sub-tiles of 32 pulses (64-byte rows, 64-byte swizzle),
+// each one box of the split operand through a 3-D tensor map (x: the 32 pulses of one part,
+// y: 2 g + part, both parts, z: the operand row = bin).  The B tile holds Re D and Im D of the
+// slots' hypotheses (rows 2 s, 2 s + 1) over the stage's 64 pulses (128-byte rows).  One
 // tcgen05.mma (M=128, N=256, K=16) per product and 16 pulses leaves, per bin and slot,
 // A = Zr Dr and C = Zr Di in TMEM lane 2 b and E = Zi Dr, B = Zi Di in lane 2 b + 1; the
 // epilogue swaps half of them between the two lanes by a shuffle and writes Y (and |Y|^2)
 // of each slot's hypothesis and its mirror: a complex MAC of a mirrored pair costs two real
 // MACs of one hypothesis in the 4M form.
 constexpr int PR_BINS = 64;                               // range bins per tile
-constexpr int PR_BK = 32;                                 // pulses per stage (64-byte rows)
+constexpr int PR_BK = 64;                                 // pulses per stage (128-byte rows, 128-byte swizzle)
 constexpr int PR_BN = 256;                                // B rows per tile (128 slots)
-constexpr uint32_t PR_A_BYTES = 2 * PR_BINS * PR_BK * 2;  // per plane (128 rows: re, im of 64 bins): 8 KB
-constexpr uint32_t PR_B_BYTES = PR_BN * PR_BK * 2;        // per plane: 16 KB
+constexpr uint32_t PR_A_BYTES = 2 * PR_BINS * PR_BK * 2;  // per plane (128 rows: re, im of 64 bins): 16 KB
+constexpr uint32_t PR_B_BYTES = PR_BN * PR_BK * 2;        // per plane: 32 KB
 constexpr size_t pr_stage_bytes(int NP) {
     return (size_t)tc_planes_a(NP) * PR_A_BYTES + (size_t)tc_planes_b(NP) * PR_B_BYTES;
 }
@@ -674,8 +677,11 @@ __device__ __forceinline__ long pair_row_offset(const TcBatch &B, const TcItem &
     return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb) * p.r0_count;
 }
 
-constexpr int PR_EPI_WARPS = 8;                           // two per TMEM lane quarter
+constexpr int PR_EPI_WARPS = 8;                           // two per TMEM lane quarter (16 measured no faster)
+constexpr int PR_EPI_PER_Q = PR_EPI_WARPS / 4;            // warps sharing one lane quarter
+constexpr int PR_CHUNKS = PR_BN / 32 / PR_EPI_PER_Q;      // 32-column chunks per epilogue warp
 constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;        // producer, MMA issuer, epilogue
+static_assert(PR_EPI_WARPS % 4 == 0 && (PR_BN / 32) % PR_EPI_PER_Q == 0, "epilogue split");
 
 template <int ST, int NP>
 __global__ void __launch_bounds__(PR_THREADS, 1)
@@ -738,7 +744,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                 int nt, mt, cl;
                 const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
                 const int arow = (int)(p.zrow0 + (long)cl * p.r0_pad + mt * PR_BINS);
-                for (int kt = 0; kt < p.KT; ++kt, ++it) {
+                for (int kt = 0; kt < (p.KT + 1) / 2; ++kt, ++it) {     // 64-pulse stages
                     const int s = it % ST;
                     if (!mbar_wait_backoff(&empty[s], ((it / ST) & 1) ^ 1, lim, 32)) {
                         latch_error(B.status, GRFT_ETIMEOUT);
@@ -746,9 +752,16 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                         break;
                     }
                     unsigned char *st = smem + s * STAGE;
-                    mbar_arrive_expect_tx(&full[s], STAGE);
-                    tma_load_3d(st, &mapAhi, 0, 2 * kt, arow, &full[s]);        // Re, Im Z of 64 bins
-                    if (NP >= 2) tma_load_3d(st + PR_A_BYTES, &mapAlo, 0, 2 * kt, arow, &full[s]);
+                    // the second 32-pulse group of the stage exists unless the pulse count ends
+                    // in the first (then its A sub-tile is neither loaded nor used)
+                    const bool has1 = 2 * kt + 1 < p.KT;
+                    mbar_arrive_expect_tx(&full[s], STAGE - (has1 ? 0u : tc_planes_a(NP) * (PR_A_BYTES / 2)));
+                    tma_load_3d(st, &mapAhi, 0, 4 * kt, arow, &full[s]);              // Re, Im Z, group 2 kt
+                    if (has1) tma_load_3d(st + PR_A_BYTES / 2, &mapAhi, 0, 4 * kt + 2, arow, &full[s]);
+                    if (NP >= 2) {
+                        tma_load_3d(st + PR_A_BYTES, &mapAlo, 0, 4 * kt, arow, &full[s]);
+                        if (has1) tma_load_3d(st + PR_A_BYTES + PR_A_BYTES / 2, &mapAlo, 0, 4 * kt + 2, arow, &full[s]);
+                    }
                     tma_load_2d(st + B_OFF, &mapBhi, kt * PR_BK, nt * PR_BN, &full[s]);
                     if (NP == 3) tma_load_2d(st + B_OFF + PR_B_BYTES, &mapBlo, kt * PR_BK, nt * PR_BN, &full[s]);
                     last_it = it;
@@ -764,7 +777,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             bool issued_any = false;
             for (int tile = cid; tile < B.total_tiles && !abort_flag; tile += ncl, ++tcount) {
                 const int b = tcount & 1;
-                const int KT = B.it[find_item_tile(B, tile)].KT;
+                const int KG = B.it[find_item_tile(B, tile)].KT;             // 32-pulse groups
+                const int KT = (KG + 1) / 2;                                // 64-pulse stages
                 if (!mbar_wait(&tmem_empty[b], ((tcount >> 1) & 1) ^ 1, lim)) {
                     latch_error(B.status, GRFT_ETIMEOUT);
                     abort_flag = 1;
@@ -785,15 +799,19 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                     const uint32_t st = sbase + s * STAGE;
                     const uint32_t a_hi = st, a_lo = st + PR_A_BYTES;
                     const uint32_t b_hi = st + B_OFF, b_lo = b_hi + PR_B_BYTES;
+                    const int nkk = 2 * kt + 1 < KG ? 4 : 2;   // K steps of 16 pulses in the stage
 #pragma unroll
-                    for (int kk = 0; kk < PR_BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;   // 16 pulses x 2 bytes inside the 64-byte row
-                        umma_f16(d_tmem, umma_desc<32>(a_hi + off), umma_desc<32>(b_hi + off), B.idesc,
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (kk >= nkk) break;
+                        // A: sub-tile kk / 2 (64-byte rows), 16 pulses at (kk % 2) x 32 bytes;
+                        // B: 16 pulses at kk x 32 bytes of the 128-byte row
+                        const uint32_t ao = (kk >> 1) * (PR_A_BYTES / 2) + (kk & 1) * 32, bo = kk * 32;
+                        umma_f16(d_tmem, umma_desc<32>(a_hi + ao), umma_desc<64>(b_hi + bo), B.idesc,
                                  (kt > 0 || kk > 0) ? 1u : 0u);
                         if (NP == 3)
-                            umma_f16(d_tmem, umma_desc<32>(a_hi + off), umma_desc<32>(b_lo + off), B.idesc, 1u);
+                            umma_f16(d_tmem, umma_desc<32>(a_hi + ao), umma_desc<64>(b_lo + bo), B.idesc, 1u);
                         if (NP >= 2)
-                            umma_f16(d_tmem, umma_desc<32>(a_lo + off), umma_desc<32>(b_hi + off), B.idesc, 1u);
+                            umma_f16(d_tmem, umma_desc<32>(a_lo + ao), umma_desc<64>(b_hi + bo), B.idesc, 1u);
                     }
                     issued_any = true;
                     umma_commit(&empty[s]);
@@ -808,8 +826,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        // Eight warps, two per TMEM lane quarter (warp w reads lanes 32 (w mod 4) .. + 31), the
-        // first of the two taking the tile's chunks 0-3, the second chunks 4-7.  Thread (warp,
+        // PR_EPI_WARPS warps, PR_EPI_PER_Q per TMEM lane quarter (warp w reads lanes 32 (w mod
+        // 4) .. + 31), each taking PR_CHUNKS of the tile's eight 32-column chunks.  Thread (warp,
         // lane) owns TMEM lane r = 32 q4 + lane: the real part (even lane) or the imaginary
         // part (odd lane) of bin r / 2.  Per 32-column chunk (16 slots) the even lane keeps
         // slots 0-7 and hands its columns of slots 8-15 to the odd lane, which keeps 8-15 and
@@ -822,7 +840,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
         // that gives up is made known through s_fail before the barrier after it.
         constexpr int NT = 32 * PR_EPI_WARPS;
         const int q4 = warp & 3;
-        const int half = (warp - 2) >> 2;         // chunks [4 half, 4 half + 4)
+        const int part = (warp - 2) >> 2;         // chunks [PR_CHUNKS part, PR_CHUNKS (part + 1))
         const int r = q4 * 32 + lane;
         const bool odd = (lane & 1) != 0;
         const int er = threadIdx.x - 64;          // 0..NT-1 over the epilogue warps
@@ -834,7 +852,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
             const int c = p.cell0 + cl;
             named_bar_sync(1, NT);                // the previous tile's offsets are read
-            if (!aborted) {                       // thread er: slot er mod 128, hypothesis or mirror
+            if (!aborted && er < 256) {           // thread er: slot er mod 128, hypothesis or mirror
                 const int slot = nt * (PR_BN / 2) + (er & 127);
                 int f = -1, fm = -1;
                 if (slot < B.slots) pair_slot(slot, B.Fv, B.Fa, f, fm);
@@ -860,7 +878,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
             const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * PR_BN);
 #pragma unroll 1
-            for (int ch = 4 * half; ch < 4 * half + 4; ++ch) {
+            for (int ch = PR_CHUNKS * part; ch < PR_CHUNKS * (part + 1); ++ch) {
                 uint32_t v[32];
                 __syncwarp();
                 tmem_ld32(taddr0 + ch * 32, v);
@@ -1099,8 +1117,8 @@ int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint1
     }
 }
 
-// The pair form: one shape per product count, filling shared memory with stages (6 x 32 KB,
-// 4 x 48 KB, 8 x 24 KB).
+// The pair form: one shape per product count, filling shared memory with stages of 64 pulses
+// (3 x 64 KB, 2 x 96 KB, 4 x 48 KB).
 template <int ST, int NP>
 int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
@@ -1109,19 +1127,19 @@ int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
     static_assert(pr_smem_bytes(ST, NP) <= 227 * 1024 - 2048, "shared memory (with the static part)");
     if (!set_smem_attr((const void *)k_ds_pair<ST, NP>, smem, c.device, attr)) return GRFT_ECUDA;
     // A: the split operand seen as [row][2 Mpad / 32 runs][32 pulses] (run y = 2 g + part); a
-    // box of both parts of 64 rows lands as 128 rows (bin, part) of 64 bytes
-    const uint64_t dims[3] = {(uint64_t)PR_BK, 2ull * (uint64_t)(Mpad / PR_BK), (uint64_t)zrows};
-    const uint64_t strides[2] = {(uint64_t)PR_BK * 2, 4ull * (uint64_t)Mpad};
-    const uint32_t box[3] = {(uint32_t)PR_BK, 2, (uint32_t)PR_BINS};
+    // box of both parts of one group and 64 rows lands as 128 rows (bin, part) of 64 bytes
+    const uint64_t dims[3] = {32, 2ull * (uint64_t)(Mpad / 32), (uint64_t)zrows};
+    const uint64_t strides[2] = {64, 4ull * (uint64_t)Mpad};
+    const uint32_t box[3] = {32, 2, (uint32_t)PR_BINS};
     CUtensorMap mzh, mzl, mbh, mbl;
     if (!encode_tma_3d(&mzh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, dims, strides, box,
                        CU_TENSOR_MAP_SWIZZLE_64B) ||
         !encode_tma_3d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, dims, strides, box,
                        CU_TENSOR_MAP_SWIZZLE_64B) ||
-        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, (uint64_t)Mpad, 2ull * Spad,
-                       (uint64_t)Mpad * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_64B) ||
-        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, (uint64_t)Mpad, 2ull * Spad,
-                       (uint64_t)Mpad * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_64B))
+        !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, (uint64_t)pair_mrow(Mpad), 2ull * Spad,
+                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, (uint64_t)pair_mrow(Mpad), 2ull * Spad,
+                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_128B))
         return GRFT_ECUDA;
     TcBatch bb = b;
     bb.tiles_n = Spad / (PR_BN / 2);
@@ -1143,9 +1161,9 @@ int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
 
 int launch_pair_nprod(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                       const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
-    if (b.nprod == 1) return launch_pair<8, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
-    if (b.nprod == 2) return launch_pair<6, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
-    return launch_pair<4, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    if (b.nprod == 1) return launch_pair<4, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    if (b.nprod == 2) return launch_pair<3, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    return launch_pair<2, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
 }
 
 // One round = the split kernel over every (item, cell, bin tile) of the batch, then the

@@ -155,13 +155,15 @@ int launch_dechirp(const Ctx &, const RadarD &, const grft_dsgrid &, float2 *D);
 int launch_dechirp_split(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Fpad,
                          bool fp16, uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
 // The pair form's dechirp operand (pair_slot): rows 2 s and 2 s + 1 hold Re D and Im D of
-// the slot's first hypothesis over the pulses (K-major, pulses contiguous, Mpad per row),
-// hi and lo planes of [2 Spad][Mpad]; padding slots and pulses are zero.
-int launch_dechirp_pair(const Ctx &, const RadarD &, const grft_dsgrid &, int Mpad, int Spad, bool fp16,
+// the slot's first hypothesis over the pulses (K-major, pulses contiguous, Mrow =
+// pair_mrow(M) per row), hi and lo planes of [2 Spad][Mrow]; padding slots and pulses are zero.
+int launch_dechirp_pair(const Ctx &, const RadarD &, const grft_dsgrid &, int Mrow, int Spad, bool fp16,
                         uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
 // Whether the tensor-core contraction of a grid runs in the pair form: P = 2 grids (also a
 // P = 3 grid whose one fine rate offset is zero); DSGRFT_PAIR=0 selects the 4M form.
 bool ds_pair_form(const Rate3 &rate);
+// Pulses per row of the pair form's dechirp operand: its stages take 64 pulses.
+inline int pair_mrow(int M) { return (M + 63) / 64 * 64; }
 
 int launch_plain(const Ctx &, const RadarD &, const float2 *echo, const grft_grid &, long h0,
                  int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,

@@ -120,12 +120,12 @@ __global__ void k_dechirp_split(RadarD R, grft_dsgrid g, Rate3 rate, int Mpad, i
 // B operand of the pair form: rows 2 s and 2 s + 1 of each plane hold Re D and Im D of slot
 // s's first hypothesis (pair_slot) over the pulses, K-major with the pulses contiguous;
 // slots s >= S (padding up to Spad) and pulses m >= M are zero.
-__global__ void k_dechirp_pair(RadarD R, grft_dsgrid g, Rate3 rate, int Mpad, int Spad, int fp16,
+__global__ void k_dechirp_pair(RadarD R, grft_dsgrid g, Rate3 rate, int Mrow, int Spad, int fp16,
                                uint16_t *__restrict__ Bhi, uint16_t *__restrict__ Blo) {
     const int S = pair_slot_count(g.Fv, g.Fa);
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over Spad * Mpad, pulses fastest
-    if (i >= (long)Spad * Mpad) return;
-    const int s = (int)(i / Mpad), m = (int)(i % Mpad);
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over Spad * Mrow, pulses fastest
+    if (i >= (long)Spad * Mrow) return;
+    const int s = (int)(i / Mrow), m = (int)(i % Mrow);
     float2 d = make_float2(0.f, 0.f);
     if (m < R.M && s < S) {
         int f, fm;
@@ -136,7 +136,7 @@ __global__ void k_dechirp_pair(RadarD R, grft_dsgrid g, Rate3 rate, int Mpad, in
     for (int ri = 0; ri < 2; ++ri) {
         const uint16_t hb = to_bits(vals[ri], fp16 != 0);
         const float hi = from_bits(hb, fp16 != 0);
-        const long o = (long)(2 * s + ri) * Mpad + m;
+        const long o = (long)(2 * s + ri) * Mrow + m;
         Bhi[o] = hb;
         Blo[o] = to_bits(vals[ri] - hi, fp16 != 0);
     }
@@ -196,11 +196,11 @@ int launch_dechirp_split(const Ctx &c, const RadarD &R, const grft_dsgrid &g, in
     return check_launch();
 }
 
-int launch_dechirp_pair(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int Mpad, int Spad, bool fp16,
+int launch_dechirp_pair(const Ctx &c, const RadarD &R, const grft_dsgrid &g, int Mrow, int Spad, bool fp16,
                         uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate) {
-    const long n = (long)Spad * Mpad;
+    const long n = (long)Spad * Mrow;
     KernelTimer kt(c, GRFT_KERNEL_TABLES);
-    k_dechirp_pair<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, rate, Mpad, Spad, fp16 ? 1 : 0, Bhi, Blo);
+    k_dechirp_pair<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g, rate, Mrow, Spad, fp16 ? 1 : 0, Bhi, Blo);
     return check_launch();
 }
 
