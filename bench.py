@@ -35,7 +35,7 @@ FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
-DRAM_TRAFFIC_PER_LAUNCH = {}
+DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (269.818112e6 + 219.337216e6)}   # k_ds_pair<3, 2>
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
 def executed_per_algorithmic(precision, Fv, Fa):
     """Tensor FLOP the contraction executes per algorithmic FLOP (8 per hypothesis-pulse).  The
