@@ -1056,8 +1056,11 @@ def main():
             "value": plain_units / (1e-3 * plain_ms), "ms_per_step": plain_ms,
             "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units),
             "max_rel_peak_err": plain_err,
-            "note": "both forms execute 8 flop per hypothesis-pulse here (time-domain gather): the speedup is "
-                    "tensor cores against FP32 SIMT, not an operation-count reduction"},
+            "note": "both forms sum every pulse of every hypothesis (time-domain gather, no FFT): plain GRFT "
+                    "executes 8 FP32 flop per hypothesis-pulse on the FMA pipes, the DS contraction "
+                    "%.3g flop (products x 8 x slots per hypothesis of the pair form); the speedup is "
+                    "the tensor cores and the pairing of mirrored hypotheses, not a shorter sum"
+                    % (FLOP_PER_HYP_PULSE * exec_factor)},
         "kernels": kernel_rooflines,
         "max_rel_peak_err": acc,
         "other_precisions": others or None,
