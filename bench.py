@@ -32,6 +32,7 @@ METRIC = "DS-GRFT vs plain GRFT hypothesis·pulse MACs/s, 1 GB300, ≤2e-3 rel p
 UNIT = "hyp*pulse/s"
 WORKLOAD = "DS-GRFT, M=512 x N=4096 complex64, 4096 r0 x (32x64) v x (8x16) a = 2^30 hypotheses"
 FLOP_PER_HYP_PULSE = 8          # one complex multiply-add
+ACC_ROWS = 512                  # random (v, a) rows of the accuracy check (every r0 bin)
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
@@ -713,7 +714,7 @@ def run_pd(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)   # about 0.5 s timed: several clock samples
+    ap.add_argument("--steps", type=int, default=100)  # about 0.5 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "fp16x3", "fp16x2", "fp16x1", "fp32"])
@@ -834,6 +835,13 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), dev)
     st = g.grft_sync_status()
     dets, ndet = g.decode_detections(det_out, n_out, args.topk)
+    # sampled (v, a) rows of the timed step's own power map (the P-only epilogue), every r0
+    # bin, kept for the accuracy check against the oracle below (P is reused after this)
+    rng = np.random.default_rng(1)
+    vf = list(rng.integers(0, nv, ACC_ROWS)) + [int(round((t.v - pg.v.start) / pg.v.step)) for t in sc.targets]
+    af = list(rng.integers(0, na, ACC_ROWS)) + [int(round((t.a - pg.a.start) / pg.a.step)) for t in sc.targets]
+    vf, af = np.clip(vf, 0, nv - 1), np.clip(af, 0, na - 1)
+    P_rows = P[torch.as_tensor(vf, device=dev), torch.as_tensor(af, device=dev)].cpu().numpy()
 
     # ---------------------------------------------------------------- end to end (host buffers)
     det_host = torch.empty_like(det_out, device="cpu").pin_memory()
@@ -875,8 +883,8 @@ def main():
     if args.plain_steps > 0 and rank == 0 and not args.no_cpu:
         import oracle
         rng = np.random.default_rng(2)
-        pv = list(rng.integers(0, nv, 6)) + [int(round((t.v - pg.v.start) / pg.v.step)) for t in sc.targets[:2]]
-        pa = list(rng.integers(0, na, 6)) + [int(round((t.a - pg.a.start) / pg.a.step)) for t in sc.targets[:2]]
+        pv = list(rng.integers(0, nv, ACC_ROWS // 4)) + [int(round((t.v - pg.v.start) / pg.v.step)) for t in sc.targets]
+        pa = list(rng.integers(0, na, ACC_ROWS // 4)) + [int(round((t.a - pg.a.start) / pg.a.step)) for t in sc.targets]
         pv, pa = np.clip(pv, 0, nv - 1), np.clip(pa, 0, na - 1)
         Ypl = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device=dev)
         g.grft_plain(R, echo, pg_slab, Ypl, None)
@@ -908,14 +916,10 @@ def main():
         torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- accuracy vs the oracle (sampled)
-    acc = None
+    acc = acc_p = None
     if rank == 0 and not args.no_cpu:
         import oracle
         from oracle.wrap import ds_rows_of_canonical
-        rng = np.random.default_rng(1)
-        vf = list(rng.integers(0, nv, 6)) + [int(round((t.v - pg.v.start) / pg.v.step)) for t in sc.targets[:2]]
-        af = list(rng.integers(0, na, 6)) + [int(round((t.a - pg.a.start) / pg.a.step)) for t in sc.targets[:2]]
-        vf, af = np.clip(vf, 0, nv - 1), np.clip(af, 0, na - 1)
         cell, fine = ds_rows_of_canonical(ds, vf, af)
         Yo = oracle.dsgrft_rows(R, s, ds, cell, fine)
         Y = torch.empty((nv, na, ds.r0_count), dtype=torch.complex64, device=dev)
@@ -923,6 +927,8 @@ def main():
         Yg = Y[torch.as_tensor(vf, device=dev), torch.as_tensor(af, device=dev)].cpu().numpy()
         del Y
         acc = float(np.abs(Yg - Yo).max() / np.abs(Yo).max())
+        Po = np.abs(Yo) ** 2
+        acc_p = float(np.abs(P_rows.astype(np.float64) - Po).max() / Po.max())
 
     # ---------------------------------------------------------------- the other contraction modes
     # (same step, same workload): bf16x3 / fp16x3 = hi/lo split of both operands, three
@@ -1056,6 +1062,8 @@ def main():
             "value": plain_units / (1e-3 * plain_ms), "ms_per_step": plain_ms,
             "ds_speedup": (plain_ms / plain_units) / ((total_ms / args.steps) / units),
             "max_rel_peak_err": plain_err,
+            "accuracy_sample": "%d (v, a) rows x %d r0 bins of the Y-writing call (random rows and the targets' rows)"
+                               % (ACC_ROWS // 4 + len(sc.targets), pg.r0_count),
             "note": "both forms sum every pulse of every hypothesis (time-domain gather, no FFT): plain GRFT "
                     "executes 8 FP32 flop per hypothesis-pulse on the FMA pipes, the DS contraction "
                     "%.3g flop (products x 8 x slots per hypothesis of the pair form); the speedup is "
@@ -1063,6 +1071,11 @@ def main():
                     % (FLOP_PER_HYP_PULSE * exec_factor)},
         "kernels": kernel_rooflines,
         "max_rel_peak_err": acc,
+        "max_rel_peak_err_power": acc_p,
+        "accuracy_sample": None if acc is None else
+            "%d (v, a) rows x %d r0 bins (%d random, the targets' rows): Y from the Y-writing call, "
+            "P from the timed step's buffer against |Y|^2 of the oracle (relative to the peak power)"
+            % (len(vf), ds.r0_count, ACC_ROWS),
         "other_precisions": others or None,
         "detections": {"total": ndet, "top1_p": float(dets["p"][0]) if len(dets) else None},
         "status": st,
