@@ -9,12 +9,14 @@
 // the threshold test compare themselves with their 26 neighbours and are appended to a
 // candidate list with a warp-aggregated atomic (one atomicAdd per warp via __ballot_sync).
 // HBM-bound: P is read once.
-// k_cfar_tma (rows of a multiple of 32 bins) / k_cfar_pipe / k_cfar_warp: the default
-// 2-guard / 16-train test, one warp per 1024-bin chunk (below).
+// k_cfar_tma (rows of a multiple of 32 bins) / k_cfar_pipe (any other row length) /
+// k_cfar_warp (fallback): the default 2-guard / 16-train test, one warp per 1024-bin chunk
+// (below).
 // k_topk: one CTA.  Up to 8192 candidates are sorted in shared memory (bitonic, by power
 // descending, index ascending); beyond that a 4-pass radix select over the power bits
 // finds the K-th largest value first and only the survivors are sorted.
 #include <cstdint>
+#include <cstdlib>
 
 #include "internal.cuh"
 #include "tma.cuh"
@@ -289,8 +291,14 @@ __device__ __forceinline__ void cfar_chunk(const float (&x)[CW_LANE], const floa
     }
 }
 
-// Any row length and alignment: each warp loads its chunk with plain loads and takes the
-// neighbouring bins from the adjacent lanes by shuffles (lanes 0 and 31 load theirs).
+// Any row length and alignment: each warp takes one chunk.  A whole chunk of a 16-byte
+// aligned row is read as float4 runs per lane; any other chunk (rows whose length is not a
+// multiple of 4 bins start at any 4-byte offset) is read coalesced, each load instruction
+// one contiguous 128-byte run of the warp (bin c0 + 32 q + lane), and turned into the lane's
+// 32 consecutive bins through a warp-private shared tile (4 pad floats per 32: conflict-free
+// on both sides, 16-byte aligned runs for the reads).  The neighbouring bins come from the
+// adjacent lanes by shuffles (lanes 0 and 31 load theirs).
+constexpr int CW_TILE = CW_CHUNK + CW_CHUNK / 8;   // floats of a warp's tile
 template <int G, int T>
 __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_warp(const float *__restrict__ P, CfarParams cp,
                                                            int nch, long rows, int *__restrict__ count,
@@ -298,16 +306,17 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_warp(const float *__rest
                                                            int64_t *__restrict__ cand_i, int *status) {
     constexpr int H = G + T;
     constexpr unsigned FULL = 0xffffffffu;
+    __shared__ alignas(16) float s_tile[CW_THREADS / 32][CW_TILE];
     const int lane = threadIdx.x & 31;
     const long gw = (long)blockIdx.x * (CW_THREADS / 32) + (threadIdx.x >> 5);
-    if (gw >= rows * nch) return;               // whole warp
+    if (gw >= rows * nch) return;               // whole warp (no CTA-wide barrier below)
     const long row = gw / nch;
     const int nr0 = cp.nr0;
     const float *prow = P + row * nr0;
     const int c0 = (int)(gw % nch) * CW_CHUNK;
     const int nb = c0 + lane * CW_LANE;
     float x[CW_LANE];
-    if (nb + CW_LANE <= nr0 && ((((uintptr_t)(prow + nb)) & 15) == 0)) {
+    if (c0 + CW_CHUNK <= nr0 && ((((uintptr_t)(prow + c0)) & 15) == 0)) {     // warp-uniform
         const float4 *src = reinterpret_cast<const float4 *>(prow + nb);
 #pragma unroll
         for (int q = 0; q < CW_LANE / 4; ++q) {
@@ -315,8 +324,18 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_warp(const float *__rest
             x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
         }
     } else {
+        float *st = s_tile[threadIdx.x >> 5];
 #pragma unroll
-        for (int q = 0; q < CW_LANE; ++q) x[q] = (nb + q < nr0) ? __ldg(prow + nb + q) : 0.f;
+        for (int q = 0; q < CW_LANE; ++q) {     // bin c0 + 32 q + lane -> slot 36 q + lane
+            const int b = c0 + 32 * q + lane;
+            st[36 * q + lane] = b < nr0 ? __ldg(prow + b) : 0.f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < CW_LANE / 4; ++q) {  // bins nb .. nb + 31 -> slots 36 lane + 0 .. 31
+            const float4 t = *reinterpret_cast<const float4 *>(st + 36 * lane + 4 * q);
+            x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
     }
     float hl[H], hr[H];
 #pragma unroll
@@ -330,7 +349,8 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_warp(const float *__rest
     cfar_chunk<G, T>(x, hl, hr, P, cp, row, c0, count, cand_p, cand_i, status);
 }
 
-// 16-byte aligned rows (nr0 % 4 == 0) and fewer than 2^31 chunks: persistent warps walk
+// Fewer than 2^31 chunks (rows at any 4-byte offset; A16: 16-byte aligned rows, nr0 % 4 ==
+// 0, copied in 16-byte units, else in 4-byte units): persistent warps walk
 // the chunks gw, gw + W, ... (W warps in the grid) with a CP_STAGES-deep pipeline of
 // asynchronous copies into shared memory, so that two chunks per warp are in flight while
 // one is tested.  Each lane copies its own 128 bytes (eight 16-byte cp.async whose
@@ -348,6 +368,10 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src, int byt
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -355,7 +379,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // 16-byte chunk c (0..7) of lane l's slot inside a stage
 __device__ __forceinline__ int cp_pos(int l, int c) { return l * CW_LANE + 4 * (c ^ (l & 7)); }
 
-template <int G, int T>
+template <int G, int T, bool A16>
 __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_pipe(const float *__restrict__ P, CfarParams cp,
                                                            int nch, int items, int *__restrict__ count,
                                                            float *__restrict__ cand_p,
@@ -380,7 +404,23 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_pipe(const float *__rest
             const int c0 = (int)((unsigned)i - row * (unsigned)nch) * CW_CHUNK;
             const float *prow = P + (size_t)row * nr0;
             const int nb = c0 + lane * CW_LANE;
-            if (c0 + CW_CHUNK <= nr0) {
+            if constexpr (!A16) {
+                // rows at any 4-byte offset: 4-byte copies, each instruction one contiguous
+                // 128-byte run of the warp (bin c0 + 32 q + lane into its owner lane q's
+                // slot), and the halo bins one per lane (lanes 0..19, both sides)
+#pragma unroll
+                for (int q = 0; q < CW_LANE; ++q) {
+                    const int b = c0 + 32 * q + lane;
+                    const bool in = b < nr0;
+                    cp_async4(st + cp_pos(q, lane >> 2) + (lane & 3), in ? prow + b : prow, in ? 4 : 0);
+                }
+                if (lane < CP_HALO) {
+                    const int bl = c0 - CP_HALO + lane, br = c0 + CW_CHUNK + lane;
+                    const bool il = bl >= 0 && bl < nr0, ir = br < nr0;
+                    cp_async4(st + CP_SEG + lane, il ? prow + bl : prow, il ? 4 : 0);
+                    cp_async4(st + CP_SEG + CP_HALO + lane, ir ? prow + br : prow, ir ? 4 : 0);
+                }
+            } else if (c0 + CW_CHUNK <= nr0) {
 #pragma unroll
                 for (int c = 0; c < CW_LANE / 4; ++c) cp_async16(st + cp_pos(lane, c), prow + nb + 4 * c, 16);
             } else {
@@ -391,7 +431,7 @@ __global__ __launch_bounds__(CW_THREADS, 2) void k_cfar_pipe(const float *__rest
                     cp_async16(st + cp_pos(lane, c), in ? prow + b : prow, in ? 16 : 0);
                 }
             }
-            if (hlane) {
+            if (A16 && hlane) {
 #pragma unroll
                 for (int c = 0; c < CP_HALO / 4; ++c) {
                     const int b = c0 + hoff + 4 * c;
@@ -804,9 +844,12 @@ int launch_detect_scan(const Ctx &c, const float *P, int nv, int na, int nr0, in
             const long warps = rows * nch;
             const long blocks = (warps + CW_THREADS / 32 - 1) / (CW_THREADS / 32);
             if (blocks > 0x7fffffffL) return GRFT_EINVAL;
-            static bool pipe_attr[64] = {false}, tma_attr[64] = {false};
-            const bool aligned = (nr0 % 4) == 0 && (((uintptr_t)P) & 15) == 0 && c.device < 64 &&
-                                 warps + 2L * c.num_sms * (CW_THREADS / 32) * CP_STAGES < 0x7fffffffL;
+            static bool pipe_attr[64] = {false}, pipe4_attr[64] = {false}, tma_attr[64] = {false};
+            const bool fits = c.device < 64 && warps + 2L * c.num_sms * (CW_THREADS / 32) * CP_STAGES < 0x7fffffffL;
+            // DSGRFT_CFAR_WARP (read per call) forces the fallback kernel, which the tests compare
+            const bool force_warp = getenv("DSGRFT_CFAR_WARP") != nullptr;
+            const bool aligned = !force_warp && fits && (nr0 % 4) == 0 && (((uintptr_t)P) & 15) == 0;
+            const bool pipe4 = !force_warp && fits && !aligned && (((uintptr_t)P) & 3) == 0;
             CUtensorMap mapc, maph;
             bool use_tma = aligned && (nr0 % 32) == 0;
             if (use_tma) {
@@ -826,20 +869,29 @@ int launch_detect_scan(const Ctx &c, const float *P, int nv, int na, int nr0, in
                 tma_attr[c.device] = true;
             }
             if (aligned && !pipe_attr[c.device]) {
-                if (cudaFuncSetAttribute(k_cfar_pipe<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                if (cudaFuncSetAttribute(k_cfar_pipe<2, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)CP_SMEM) != cudaSuccess)
                     return GRFT_ECUDA;
                 pipe_attr[c.device] = true;
+            }
+            if (pipe4 && !pipe4_attr[c.device]) {
+                if (cudaFuncSetAttribute(k_cfar_pipe<2, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CP_SMEM) != cudaSuccess)
+                    return GRFT_ECUDA;
+                pipe4_attr[c.device] = true;
             }
             if (use_tma) {
                 const long pblocks = blocks < 2L * c.num_sms ? blocks : 2L * c.num_sms;
                 k_cfar_tma<2, 16><<<(unsigned)pblocks, CW_THREADS, CT_SMEM, c.stream>>>(
                     mapc, maph, cp, nch, (int)warps, count, cand_p, cand_i, c.status, c.wait_limit, P);
-            } else if (aligned) {
+            } else if (aligned || pipe4) {
                 const long pblocks = blocks < 2L * c.num_sms ? blocks : 2L * c.num_sms;
-                k_cfar_pipe<2, 16><<<(unsigned)pblocks, CW_THREADS, CP_SMEM, c.stream>>>(P, cp, nch, (int)warps,
-                                                                                      count, cand_p, cand_i,
-                                                                                      c.status);
+                if (aligned)
+                    k_cfar_pipe<2, 16, true><<<(unsigned)pblocks, CW_THREADS, CP_SMEM, c.stream>>>(
+                        P, cp, nch, (int)warps, count, cand_p, cand_i, c.status);
+                else
+                    k_cfar_pipe<2, 16, false><<<(unsigned)pblocks, CW_THREADS, CP_SMEM, c.stream>>>(
+                        P, cp, nch, (int)warps, count, cand_p, cand_i, c.status);
             } else {
                 k_cfar_warp<2, 16><<<(unsigned)blocks, CW_THREADS, 0, c.stream>>>(P, cp, nch, rows, count, cand_p,
                                                                                   cand_i, c.status);

@@ -343,28 +343,46 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
         }
     };
 
-    // Fast path (block-uniform): the tables are staged, every pulse group is whole, every bin
-    // of the tile is inside the r0 range and every gathered bin is inside the echo, so the
-    // loop carries no bound checks.
-    if (tab_smem && p.M == 32 * p.KT && j0 + TC_BM <= p.r0_count &&
-        p.r0_begin + j0 + s_rng[0] >= 0 && p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
+    // Fast path (block-uniform): the tables are staged, every bin of the tile is inside the
+    // r0 range and every gathered bin is inside the echo, so the loop carries no bound checks
+    // but the pulse count's: the sub-steps of 8 pulses past the last pulse (a ragged M) write
+    // zeros, as the operand's K padding must hold, and load nothing.
+    if (tab_smem && j0 + TC_BM <= p.r0_count && p.r0_begin + j0 + s_rng[0] >= 0 &&
+        p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
         const float2 *src = p.echo + nbase;
         const long N = p.N;
+        const int M = p.M;
         const uint64_t pol_e = l2_policy_evict_last();
         auto ld = [&](int s, float2 (&v)[8]) {
             const int m0 = s * 8;
             const float2 *rowp = src + (long)m0 * N;
+            if (m0 + 8 <= M) {                  // warp-uniform: a whole sub-step
 #pragma unroll
-            for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
+                for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i, rowp += N)
+                    v[i] = m0 + i < M ? ld_global_nc_hint(rowp + s_rho[min(m0 + i, M - 1)], pol_e)
+                                      : make_float2(0.f, 0.f);
+            }
         };
         auto cv = [&](int s, const float2 (&v)[8]) {
             const int m0 = s * 8;
             float re[8], im[8];
+            if (m0 + 8 <= M) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float2 x = cmul(v[i], s_w[m0 + i]);
-                re[i] = x.x;
-                im[i] = x.y;
+                for (int i = 0; i < 8; ++i) {
+                    const float2 x = cmul(v[i], s_w[m0 + i]);
+                    re[i] = x.x;
+                    im[i] = x.y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 x = m0 + i < M ? cmul(v[i], s_w[min(m0 + i, M - 1)]) : make_float2(0.f, 0.f);
+                    re[i] = x.x;
+                    im[i] = x.y;
+                }
             }
             put(s, re, im);
         };

@@ -63,6 +63,27 @@ def test_cfar_topk_matches_oracle_on_same_power(cuda_lib, nr0):
     assert g.grft_sync_status() == 0
 
 
+@pytest.mark.parametrize("nr0", [3001, 1043, 50, 2052, 2080])
+def test_cfar_kernels_agree(cuda_lib, nr0, monkeypatch):
+    """The pipelined kernels (tensor-map copies for rows of a multiple of 32 bins, 16-byte
+    copies for 16-byte aligned rows, 4-byte copies for rows at any offset) and the fallback
+    one-chunk-per-warp kernel (DSGRFT_CFAR_WARP) give the same detections and totals."""
+    g = cuda_lib
+    rng = np.random.default_rng(nr0 + 1)
+    P = rng.exponential(1.0, size=(13, 5, nr0)).astype(np.float32)
+    for k in range(60):
+        P[rng.integers(13), rng.integers(5), rng.integers(nr0)] = np.float32(rng.uniform(15, 200))
+    Pd = torch.from_numpy(P).cuda()
+    cfar = CFAR(2, 16, 1e-3)
+    K = 256
+    a = g.decode_detections(*g.detect_peaks(Pd, cfar, K), K)
+    monkeypatch.setenv("DSGRFT_CFAR_WARP", "1")
+    b = g.decode_detections(*g.detect_peaks(Pd, cfar, K), K)
+    assert a[1] == b[1] and a[1] > 10
+    assert a[0].tobytes() == b[0].tobytes()
+    assert g.grft_sync_status() == 0
+
+
 def test_topk_radix_select_path_and_ties(cuda_lib):
     """More than 8192 candidates (fixed threshold, every local max passes) takes the radix
     select path; equal powers are ordered by index."""
