@@ -36,19 +36,32 @@ ACC_ROWS = 512                  # random (v, a) rows of the accuracy check (ever
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
-DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (269.818112e6 + 219.337216e6)}   # k_ds_pair<3, 2>
+DRAM_TRAFFIC_PER_LAUNCH = {}
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
+def pair_bn(slots):
+    """Tile width (B rows, two per slot) the pair form's contraction takes: of 256, 224 and 192
+    the one whose tiles cover the slots with the fewest columns, the wider on a tie."""
+    best, best_cols = 256, -(-slots // 128) * 256
+    for bn in (224, 192):
+        cols = -(-slots // (bn // 2)) * bn
+        if cols < best_cols:
+            best, best_cols = bn, cols
+    return best
+
+
 def executed_per_algorithmic(precision, Fv, Fa):
     """Tensor FLOP the contraction executes per algorithmic FLOP (8 per hypothesis-pulse).  The
     pair form (P = 2 grids) contracts each slot of mirrored hypotheses (every hypothesis once,
     with its mirror where it has one: Fa + Fv - 1 + ceil((Fv - 1)(Fa - 1) / 2) slots, padded to
-    128) as four real MACs per pulse and product, i.e. 8 FLOP per slot-pulse and product."""
+    whole tiles of pair_bn / 2 slots) as four real MACs per pulse and product, i.e. 8 FLOP per
+    slot-pulse and product."""
     if precision == "fp32":
         return 1.0
     if os.environ.get("DSGRFT_PAIR", "1").startswith("0"):      # the 4M form
         return float(PRODUCTS_PER_MAC[precision])
     slots = Fa + (Fv - 1) + ((Fv - 1) * (Fa - 1) + 1) // 2
-    spad = -(-slots // 128) * 128
+    half = pair_bn(slots) // 2
+    spad = -(-slots // half) * half
     return PRODUCTS_PER_MAC[precision] * spad / float(Fv * Fa)
 
 

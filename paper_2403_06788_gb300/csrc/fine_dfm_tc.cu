@@ -344,55 +344,65 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
     };
 
     // Fast path (block-uniform): the tables are staged, every bin of the tile is inside the
-    // r0 range and every gathered bin is inside the echo, so the loop carries no bound checks
-    // but the pulse count's: the sub-steps of 8 pulses past the last pulse (a ragged M) write
-    // zeros, as the operand's K padding must hold, and load nothing.
+    // r0 range and every gathered bin is inside the echo, so the loop over the whole sub-steps
+    // of 8 pulses carries no bound checks; the sub-steps past the last whole one (a pulse
+    // count that is not a multiple of 32) follow with the pulse check, writing zeros past the
+    // last pulse as the operand's K padding must hold.
     if (tab_smem && j0 + TC_BM <= p.r0_count && p.r0_begin + j0 + s_rng[0] >= 0 &&
         p.r0_begin + j0 + TC_BM - 1 + s_rng[1] < p.N) {
         const float2 *src = p.echo + nbase;
         const long N = p.N;
-        const int M = p.M;
         const uint64_t pol_e = l2_policy_evict_last();
         auto ld = [&](int s, float2 (&v)[8]) {
             const int m0 = s * 8;
             const float2 *rowp = src + (long)m0 * N;
-            if (m0 + 8 <= M) {                  // warp-uniform: a whole sub-step
 #pragma unroll
-                for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i, rowp += N)
-                    v[i] = m0 + i < M ? ld_global_nc_hint(rowp + s_rho[min(m0 + i, M - 1)], pol_e)
-                                      : make_float2(0.f, 0.f);
-            }
+            for (int i = 0; i < 8; ++i, rowp += N) v[i] = ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e);
         };
         auto cv = [&](int s, const float2 (&v)[8]) {
             const int m0 = s * 8;
             float re[8], im[8];
-            if (m0 + 8 <= M) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 x = cmul(v[i], s_w[m0 + i]);
-                    re[i] = x.x;
-                    im[i] = x.y;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 x = m0 + i < M ? cmul(v[i], s_w[min(m0 + i, M - 1)]) : make_float2(0.f, 0.f);
-                    re[i] = x.x;
-                    im[i] = x.y;
-                }
+            for (int i = 0; i < 8; ++i) {
+                const float2 x = cmul(v[i], s_w[m0 + i]);
+                re[i] = x.x;
+                im[i] = x.y;
             }
             put(s, re, im);
         };
         float2 va[8], vb[8];
-        ld(0, va);
-        for (int s = 0; s < S; s += 2) {        // the two buffers alternate
+        if (p.M == 32 * p.KT) {                 // whole 32-pulse groups: every sub-step is whole
+            ld(0, va);
+            for (int s = 0; s < S; s += 2) {    // the two buffers alternate
+                ld(s + 1, vb);
+                cv(s, va);
+                if (s + 2 < S) ld(s + 2, va);
+                cv(s + 1, vb);
+            }
+            return;
+        }
+        const int Sw = p.M / 8;                 // whole sub-steps
+        if (Sw > 0) ld(0, va);
+        int s = 0;
+        for (; s + 1 < Sw; s += 2) {            // the two buffers alternate
             ld(s + 1, vb);
             cv(s, va);
-            if (s + 2 < S) ld(s + 2, va);
+            if (s + 2 < Sw) ld(s + 2, va);
             cv(s + 1, vb);
+        }
+        if (s < Sw) cv(s++, va);                // an odd count: the last whole one is in va
+        for (; s < S; ++s) {                    // at most four: the partial one, then zeros
+            const int m0 = s * 8;
+            const float2 *rowp = src + (long)m0 * N;
+            float re[8], im[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i, rowp += N) {
+                float2 x = make_float2(0.f, 0.f);
+                if (m0 + i < p.M) x = cmul(ld_global_nc_hint(rowp + s_rho[m0 + i], pol_e), s_w[m0 + i]);
+                re[i] = x.x;
+                im[i] = x.y;
+            }
+            put(s, re, im);
         }
         return;
     }
@@ -666,13 +676,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // MACs of one hypothesis in the 4M form.
 constexpr int PR_BINS = 64;                               // range bins per tile
 constexpr int PR_BK = 64;                                 // pulses per stage (128-byte rows, 128-byte swizzle)
-constexpr int PR_BN = 256;                                // B rows per tile (128 slots)
+// B rows per tile BN (BN / 2 slots): 256, 224 or 192, whichever pads the slot count least
+// (pair_bn); the MMA's N and the tensor work of a tile scale with it.
 constexpr uint32_t PR_A_BYTES = 2 * PR_BINS * PR_BK * 2;  // per plane (128 rows: re, im of 64 bins): 16 KB
-constexpr uint32_t PR_B_BYTES = PR_BN * PR_BK * 2;        // per plane: 32 KB
-constexpr size_t pr_stage_bytes(int NP) {
-    return (size_t)tc_planes_a(NP) * PR_A_BYTES + (size_t)tc_planes_b(NP) * PR_B_BYTES;
+constexpr uint32_t pr_b_bytes(int BN) { return (uint32_t)BN * PR_BK * 2; }   // per plane: BN rows of 128 bytes
+constexpr size_t pr_stage_bytes(int NP, int BN) {
+    return (size_t)tc_planes_a(NP) * PR_A_BYTES + (size_t)tc_planes_b(NP) * pr_b_bytes(BN);
 }
-constexpr size_t pr_smem_bytes(int ST, int NP) { return (size_t)ST * pr_stage_bytes(NP) + 1024; }
+constexpr size_t pr_smem_bytes(int ST, int NP, int BN) { return (size_t)ST * pr_stage_bytes(NP, BN) + 1024; }
 
 __device__ __forceinline__ const TcItem &decode_pair_unit(const TcBatch &b, int unit, int &nt, int &mt, int &cl) {
     const TcItem &p = b.it[find_item_tile(b, unit)];
@@ -695,21 +706,24 @@ __device__ __forceinline__ long pair_row_offset(const TcBatch &B, const TcItem &
     return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb) * p.r0_count;
 }
 
-constexpr int PR_EPI_WARPS = 8;                           // two per TMEM lane quarter (16 measured no faster)
+constexpr int PR_EPI_WARPS = 12;                          // three per TMEM lane quarter (ds_m512: 8 -> 3.21 ms, 12 -> 3.12, 16 -> 3.14)
 constexpr int PR_EPI_PER_Q = PR_EPI_WARPS / 4;            // warps sharing one lane quarter
-constexpr int PR_CHUNKS = PR_BN / 32 / PR_EPI_PER_Q;      // 32-column chunks per epilogue warp
 constexpr int PR_THREADS = 64 + 32 * PR_EPI_WARPS;        // producer, MMA issuer, epilogue
-static_assert(PR_EPI_WARPS % 4 == 0 && (PR_BN / 32) % PR_EPI_PER_Q == 0, "epilogue split");
+static_assert(PR_EPI_WARPS % 4 == 0 && PR_EPI_WARPS <= 16, "whole lane quarters");
 
-template <int ST, int NP>
+template <int ST, int NP, int BN>
 __global__ void __launch_bounds__(PR_THREADS, 1)
     k_ds_pair(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
               const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
               const __grid_constant__ TcBatch B) {
-    constexpr uint32_t STAGE = (uint32_t)pr_stage_bytes(NP);
+    constexpr uint32_t STAGE = (uint32_t)pr_stage_bytes(NP, BN);
     constexpr uint32_t B_OFF = tc_planes_a(NP) * PR_A_BYTES;
-    constexpr uint32_t TMEM_COLS = 2 * PR_BN;              // two accumulators
+    constexpr uint32_t PR_B_BYTES = pr_b_bytes(BN);
+    constexpr uint32_t TMEM_COLS = 512;                    // two accumulators of BN columns (a power of 2)
+    constexpr int SL = BN / 2;                             // slots per tile
+    constexpr int NCH = BN / 32;                           // 32-column chunks per tile
     static_assert(NP >= 1 && NP <= 3, "three, two or one products per K step");
+    static_assert(BN % 32 == 0 && BN >= 128 && BN <= 256 && STAGE % 1024 == 0, "pair tile");
     extern __shared__ unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t full[ST], empty[ST];
     __shared__ alignas(8) uint64_t tmem_full[2], tmem_empty[2], drain_bar;
@@ -780,8 +794,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                         tma_load_3d(st + PR_A_BYTES, &mapAlo, 0, 4 * kt, arow, &full[s]);
                         if (has1) tma_load_3d(st + PR_A_BYTES + PR_A_BYTES / 2, &mapAlo, 0, 4 * kt + 2, arow, &full[s]);
                     }
-                    tma_load_2d(st + B_OFF, &mapBhi, kt * PR_BK, nt * PR_BN, &full[s]);
-                    if (NP == 3) tma_load_2d(st + B_OFF + PR_B_BYTES, &mapBlo, kt * PR_BK, nt * PR_BN, &full[s]);
+                    tma_load_2d(st + B_OFF, &mapBhi, kt * PR_BK, nt * BN, &full[s]);
+                    if (NP == 3) tma_load_2d(st + B_OFF + PR_B_BYTES, &mapBlo, kt * PR_BK, nt * BN, &full[s]);
                     last_it = it;
                 }
             }
@@ -803,7 +817,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(b * PR_BN);
+                const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
                 bool ok = true;
                 for (int kt = 0; kt < KT; ++kt, ++it) {
                     const int s = it % ST;
@@ -845,7 +859,8 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         // PR_EPI_WARPS warps, PR_EPI_PER_Q per TMEM lane quarter (warp w reads lanes 32 (w mod
-        // 4) .. + 31), each taking PR_CHUNKS of the tile's eight 32-column chunks.  Thread (warp,
+        // 4) .. + 31), warp part p of the quarter the tile's 32-column chunks [ceil(p NCH /
+        // PR_EPI_PER_Q), ceil((p + 1) NCH / PR_EPI_PER_Q)).  Thread (warp,
         // lane) owns TMEM lane r = 32 q4 + lane: the real part (even lane) or the imaginary
         // part (odd lane) of bin r / 2.  Per 32-column chunk (16 slots) the even lane keeps
         // slots 0-7 and hands its columns of slots 8-15 to the odd lane, which keeps 8-15 and
@@ -858,7 +873,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
         // that gives up is made known through s_fail before the barrier after it.
         constexpr int NT = 32 * PR_EPI_WARPS;
         const int q4 = warp & 3;
-        const int part = (warp - 2) >> 2;         // chunks [PR_CHUNKS part, PR_CHUNKS (part + 1))
+        const int part = (warp - 2) >> 2;         // 0 .. PR_EPI_PER_Q - 1
+        const int ch0 = (part * NCH + PR_EPI_PER_Q - 1) / PR_EPI_PER_Q;
+        const int ch1 = ((part + 1) * NCH + PR_EPI_PER_Q - 1) / PR_EPI_PER_Q;
         const int r = q4 * 32 + lane;
         const bool odd = (lane & 1) != 0;
         const int er = threadIdx.x - 64;          // 0..NT-1 over the epilogue warps
@@ -870,14 +887,15 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             const TcItem &p = decode_pair_unit(B, tile, nt, mt, cl);
             const int c = p.cell0 + cl;
             named_bar_sync(1, NT);                // the previous tile's offsets are read
-            if (!aborted && er < 256) {           // thread er: slot er mod 128, hypothesis or mirror
-                const int slot = nt * (PR_BN / 2) + (er & 127);
+            if (!aborted && er < 2 * SL) {        // thread er: slot er mod SL, hypothesis or mirror
+                const int sl = er < SL ? er : er - SL;
+                const int slot = nt * SL + sl;
                 int f = -1, fm = -1;
                 if (slot < B.slots) pair_slot(slot, B.Fv, B.Fa, f, fm);
-                if (er < 128)
-                    s_off_f[er] = pair_row_offset(B, p, c, f);
+                if (er < SL)
+                    s_off_f[sl] = pair_row_offset(B, p, c, f);
                 else
-                    s_off_m[er - 128] = pair_row_offset(B, p, c, fm);
+                    s_off_m[sl] = pair_row_offset(B, p, c, fm);
             }
             named_bar_sync(1, NT);
             if (aborted) continue;
@@ -894,9 +912,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             float *const P = p.P;
             float2 *const Y = p.Y;
             const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
-            const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * PR_BN);
+            const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
-            for (int ch = PR_CHUNKS * part; ch < PR_CHUNKS * (part + 1); ++ch) {
+            for (int ch = ch0; ch < ch1; ++ch) {
                 uint32_t v[32];
                 __syncwarp();
                 tmem_ld32(taddr0 + ch * 32, v);
@@ -1135,15 +1153,18 @@ int launch_gemm_variant(int variant, const Ctx &c, const TcBatch &b, const uint1
     }
 }
 
-// The pair form: one shape per product count, filling shared memory with stages of 64 pulses
-// (3 x 64 KB, 2 x 96 KB, 4 x 48 KB).
-template <int ST, int NP>
+// The pair form: one shape per product count and tile width, filling shared memory with
+// stages of 64 pulses (3 stages with two products, 2 with three, 4 with one).  Spad is the
+// slot count of the dechirp operand (a multiple of 128, at least the tiles' slots).
+template <int ST, int NP, int BN>
 int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                 const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
     static bool attr[64] = {false};
-    const size_t smem = pr_smem_bytes(ST, NP);
-    static_assert(pr_smem_bytes(ST, NP) <= 227 * 1024 - 2048, "shared memory (with the static part)");
-    if (!set_smem_attr((const void *)k_ds_pair<ST, NP>, smem, c.device, attr)) return GRFT_ECUDA;
+    const size_t smem = pr_smem_bytes(ST, NP, BN);
+    static_assert(pr_smem_bytes(ST, NP, BN) <= 227 * 1024 - 2048, "shared memory (with the static part)");
+    const int tiles_n = (b.slots + BN / 2 - 1) / (BN / 2);
+    if (tiles_n * (BN / 2) > Spad) return GRFT_EINVAL;
+    if (!set_smem_attr((const void *)k_ds_pair<ST, NP, BN>, smem, c.device, attr)) return GRFT_ECUDA;
     // A: the split operand seen as [row][2 Mpad / 32 runs][32 pulses] (run y = 2 g + part); a
     // box of both parts of one group and 64 rows lands as 128 rows (bin, part) of 64 bytes
     const uint64_t dims[3] = {32, 2ull * (uint64_t)(Mpad / 32), (uint64_t)zrows};
@@ -1155,12 +1176,12 @@ int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
         !encode_tma_3d(&mzl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zlo, dims, strides, box,
                        CU_TENSOR_MAP_SWIZZLE_64B) ||
         !encode_tma_2d(&mbh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Bhi, (uint64_t)pair_mrow(Mpad), 2ull * Spad,
-                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_tma_2d(&mbl, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Blo, (uint64_t)pair_mrow(Mpad), 2ull * Spad,
-                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, PR_BN, CU_TENSOR_MAP_SWIZZLE_128B))
+                       (uint64_t)pair_mrow(Mpad) * 2, PR_BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
         return GRFT_ECUDA;
     TcBatch bb = b;
-    bb.tiles_n = Spad / (PR_BN / 2);
+    bb.tiles_n = tiles_n;
     long units = 0;
     for (int i = 0; i < bb.n_items; ++i) {
         bb.it[i].tile0 = (int)units;
@@ -1169,19 +1190,20 @@ int launch_pair(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint1
     if (units > 0x7fffffffL) return GRFT_EINVAL;
     bb.total_tiles = (int)units;
     const uint32_t fmt = bb.fp16 ? 0u : 1u;   // kind::f16 operand format: 0 = F16, 1 = BF16
-    bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(PR_BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    bb.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     const int grid = bb.total_tiles < c.num_sms ? bb.total_tiles : c.num_sms;
     if (grid <= 0) return GRFT_OK;
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT);
-    k_ds_pair<ST, NP><<<grid, PR_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
+    k_ds_pair<ST, NP, BN><<<grid, PR_THREADS, smem, c.stream>>>(mzh, mzl, mbh, mbl, bb);
     return check_launch();
 }
 
+template <int BN>
 int launch_pair_nprod(const Ctx &c, const TcBatch &b, const uint16_t *Zhi, const uint16_t *Zlo, long zrows,
                       const uint16_t *Bhi, const uint16_t *Blo, int Mpad, int Spad) {
-    if (b.nprod == 1) return launch_pair<4, 1>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
-    if (b.nprod == 2) return launch_pair<3, 2>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
-    return launch_pair<2, 3>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    if (b.nprod == 1) return launch_pair<4, 1, BN>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    if (b.nprod == 2) return launch_pair<3, 2, BN>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
+    return launch_pair<2, 3, BN>(c, b, Zhi, Zlo, zrows, Bhi, Blo, Mpad, Spad);
 }
 
 // One round = the split kernel over every (item, cell, bin tile) of the batch, then the
@@ -1209,8 +1231,14 @@ int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
 int launch_round_gemm(const Ctx &c, const Round &rd, int Mpad, int Fpad, const uint16_t *Bhi,
                       const uint16_t *Blo, uint16_t *Zhi, uint16_t *Zlo, int &variant, const TuneKey &key) {
     if (rd.b.slots > 0) {   // pair form (one shape per product count)
-        const int Spad = (rd.b.slots + PR_BN / 2 - 1) / (PR_BN / 2) * (PR_BN / 2);
-        return launch_pair_nprod(c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Spad);
+        const int Spad = (rd.b.slots + 127) / 128 * 128;     // the dechirp operand's slots
+        int bn = pair_bn(rd.b.slots);
+        if (const char *e = getenv("DSGRFT_PAIR_BN")) bn = atoi(e);   // explicit width (experiments)
+        switch (bn) {
+            case 224: return launch_pair_nprod<224>(c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Spad);
+            case 192: return launch_pair_nprod<192>(c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Spad);
+            default: return launch_pair_nprod<256>(c, rd.b, Zhi, Zlo, rd.rows, Bhi, Blo, Mpad, Spad);
+        }
     }
     if (variant < 0) {   // autotune: time the tile shapes on this round of cells, keep the fastest
         variant = tune_variant(c, rd.b, [&](int v) {

@@ -164,6 +164,22 @@ int launch_dechirp_pair(const Ctx &, const RadarD &, const grft_dsgrid &, int Mr
 bool ds_pair_form(const Rate3 &rate);
 // Pulses per row of the pair form's dechirp operand: its stages take 64 pulses.
 inline int pair_mrow(int M) { return (M + 63) / 64 * 64; }
+// Tile width (B rows, two per slot) of the pair form's contraction: of 256, 224 and 192 the
+// one whose tiles cover the slots with the fewest columns (the tensor work is proportional to
+// them), the wider on a tie (fewer tiles, fewer loads of the gathered operand).  For the
+// 64 x 16 fine grid's 552 slots: 224 (5 tiles, 1120 columns against 1280 at 256).
+inline int pair_bn(int slots) {
+    int best = 256;
+    long best_cols = (long)((slots + 127) / 128) * 256;
+    for (int bn : {224, 192}) {
+        const long cols = (long)((slots + bn / 2 - 1) / (bn / 2)) * bn;
+        if (cols < best_cols) {
+            best = bn;
+            best_cols = cols;
+        }
+    }
+    return best;
+}
 
 int launch_plain(const Ctx &, const RadarD &, const float2 *echo, const grft_grid &, long h0,
                  int nh, const int32_t *rho, const float2 *w, const float2 *e0, float2 *Y,

@@ -7,7 +7,8 @@ DSGRFT_TUNE_CACHE, and a later process reuses it.  The tile shapes and the tuner
 
 The pair form (two mirrored hypotheses per contraction, the default for P = 2 grids)
 matches the 4M form within the split tolerance and the FP64 oracle on every output, for
-fine grids with even and odd sizes and with a fine axis of one point."""
+fine grids with even and odd sizes and with a fine axis of one point, in each of its tile
+widths (256, 224 and 192 columns)."""
 import json
 import os
 import subprocess
@@ -83,8 +84,10 @@ np.save(sys.argv[1] + ".echo.npy", s)
 """
 
 
+# tile widths (pair_bn): 16 x 16, 5 x 3, 7 x 1, 1 x 6 take 192 columns; 15 x 14 (119 slots) 256;
+# 64 x 16 (552 slots) and 48 x 16 224
 @pytest.mark.parametrize("Fv,Fa,precision", [(16, 16, "fp16x2"), (5, 3, "fp16x2"), (7, 1, "bf16x3"), (1, 6, "fp16x1"),
-                                             (64, 16, "bf16x3")])
+                                             (64, 16, "bf16x3"), (15, 14, "fp16x2"), (48, 16, "fp16x2")])
 def test_pair_form_matches_4m_form_and_oracle(cuda_lib, tmp_path, Fv, Fa, precision):
     import numpy as np
     import oracle
