@@ -489,7 +489,7 @@ def run_suite(args):
 
     out.update(measure_forms(0, 3, 1))
     out["keystone_m512"] = measure_kt(rows=0, steps=3, warmup=1)
-    out["p3_m512"] = measure_p3(3, 1)
+    out["p3_m512"] = {p: measure_p3(3, 1, p) for p in ("fp16x2", "bf16x3")}
     print(json.dumps({"suite": out}))
     return 0
 

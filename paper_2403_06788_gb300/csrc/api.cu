@@ -19,7 +19,9 @@ bool ds_pair_form(const Rate3 &rate) {
         const char *e = getenv("DSGRFT_PAIR");
         return !(e && e[0] == '0');
     }();
-    return on && (!rate.on || (rate.Fb == 1 && rate.step == 0.0));
+    // P = 2; P = 3 whose rate axis is one zero offset (the P = 2 pairs); P = 3 with Fb >= 2
+    // rate offsets (mirrors on all three axes).  A single nonzero rate offset has no mirror.
+    return on && (!rate.on || (rate.Fb == 1 && rate.step == 0.0) || rate.Fb >= 2);
 }
 
 namespace {
@@ -425,7 +427,7 @@ int fill_dechirp(const Ctx &c, const RadarD &R, const grft_dsgrid &g, const Rate
     const int Mpad = (R.M + 31) / 32 * 32;
     const size_t d_bytes = dechirp_plane_bytes(R, g, rate, true);
     if (ds_pair_form(rate)) {   // [2 Spad][pair_mrow(M)] per plane: within d_bytes (Spad <= Fpad, Mrow <= 2 Mpad)
-        const int Spad = (pair_slot_count(g.Fv, g.Fa) + 127) / 128 * 128;
+        const int Spad = (pair_slot_count3(g.Fv, g.Fa, rate.Fb) + 127) / 128 * 128;
         return launch_dechirp_pair(c, R, g, pair_mrow(R.M), Spad, precision_fp16(precision), (uint16_t *)dst,
                                    (uint16_t *)(dst + d_bytes), rate);
     }

@@ -696,14 +696,16 @@ __device__ __forceinline__ const TcItem &decode_pair_unit(const TcBatch &b, int 
     return p;
 }
 
-// Output row offset (canonical layout, bin 0) of fine hypothesis f of cell c, or -1.
+// Output row offset (canonical layout, bin 0) of fine hypothesis f = (k Fa + q) Fb + u of
+// cell c, or -1.
 __device__ __forceinline__ long pair_row_offset(const TcBatch &B, const TcItem &p, int c, int f) {
     if (f < 0) return -1;
     const int iw = c % B.nb_c, c2 = c / B.nb_c;
     const int iv = c2 / B.na_c - p.i0, il = c2 % B.na_c;
-    const int k = f / B.Fa, q = f % B.Fa;
+    const int u = f % B.Fb, kq = f / B.Fb;
+    const int k = kq / B.Fa, q = kq % B.Fa;
     const long na_full = (long)B.na_c * B.Fa, nb_full = (long)B.nb_c * B.Fb;
-    return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb) * p.r0_count;
+    return (((long)(iv * B.Fv + k) * na_full + (il * B.Fa + q)) * nb_full + (long)iw * B.Fb + u) * p.r0_count;
 }
 
 constexpr int PR_EPI_WARPS = 12;                          // three per TMEM lane quarter (ds_m512: 8 -> 3.21 ms, 12 -> 3.12, 16 -> 3.14)
@@ -891,7 +893,7 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                 const int sl = er < SL ? er : er - SL;
                 const int slot = nt * SL + sl;
                 int f = -1, fm = -1;
-                if (slot < B.slots) pair_slot(slot, B.Fv, B.Fa, f, fm);
+                if (slot < B.slots) pair_slot3(slot, B.Fv, B.Fa, B.Fb, f, fm);
                 if (er < SL)
                     s_off_f[sl] = pair_row_offset(B, p, c, f);
                 else
@@ -1310,7 +1312,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     b.nb_c = rate.count;
     b.fp16 = fp16 ? 1 : 0;
     b.nprod = nprod;
-    b.slots = ds_pair_form(rate) ? pair_slot_count(g.Fv, g.Fa) : 0;
+    b.slots = ds_pair_form(rate) ? pair_slot_count3(g.Fv, g.Fa, rate.Fb) : 0;
     b.idesc = 0;                     // set per variant by launch_gemm
     b.status = c.status;
     b.wait_limit = c.wait_limit;

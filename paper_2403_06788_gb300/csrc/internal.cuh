@@ -107,6 +107,50 @@ __host__ __device__ inline void pair_slot(int s, int Fv, int Fa, int &f, int &fm
     if (lm != s) fm = (int)(lm / C + 1) * Fa + (int)(lm % C + 1);
 }
 
+// P = 3 grids with Fb >= 2 rate offsets: the mirror of hypothesis (k, q, u) is (Fv - k,
+// Fa - q, Fb - u) for k, q, u >= 1 (all three offsets change sign).  The slots list first
+// the hypotheses without a mirror (k = 0: Fa Fb of them; q = 0, k >= 1: (Fv - 1) Fb; u = 0,
+// k, q >= 1: (Fv - 1)(Fa - 1)), then walk the k, q, u >= 1 box in row-major order up to its
+// middle.  f is the full fine index (k Fa + q) Fb + u.  Fb <= 1 is the P = 2 rule (the rate
+// axis is a single zero offset) with f = (k Fa + q) Fb.
+__host__ __device__ inline int pair_slot_count3(int Fv, int Fa, int Fb) {
+    if (Fb <= 1) return pair_slot_count(Fv, Fa);
+    const long box = (long)(Fv - 1) * (Fa - 1) * (Fb - 1);
+    return Fa * Fb + (Fv - 1) * Fb + (Fv - 1) * (Fa - 1) + (int)((box + 1) / 2);
+}
+__host__ __device__ inline void pair_slot3(int s, int Fv, int Fa, int Fb, int &f, int &fm) {
+    if (Fb <= 1) {
+        pair_slot(s, Fv, Fa, f, fm);
+        f *= Fb;
+        if (fm >= 0) fm *= Fb;
+        return;
+    }
+    fm = -1;
+    if (s < Fa * Fb) {                         // k = 0
+        f = s;
+        return;
+    }
+    s -= Fa * Fb;
+    if (s < (Fv - 1) * Fb) {                   // q = 0, k >= 1
+        f = (s / Fb + 1) * Fa * Fb + s % Fb;
+        return;
+    }
+    s -= (Fv - 1) * Fb;
+    const int C = Fa - 1, D = Fb - 1;
+    if (s < (Fv - 1) * C) {                    // u = 0, k, q >= 1
+        f = ((s / C + 1) * Fa + s % C + 1) * Fb;
+        return;
+    }
+    s -= (Fv - 1) * C;
+    const long lm = (long)(Fv - 1) * C * D - 1 - s;
+    auto full = [&](long l) {
+        const int u = (int)(l % D) + 1, kq = (int)(l / D);
+        return ((kq / C + 1) * Fa + kq % C + 1) * Fb + u;
+    };
+    f = full(s);
+    if (lm != s) fm = full(lm);
+}
+
 // --------------------------------------------------------------------------- host side
 struct RadarD {     // radar constants as the kernels use them
     int M, N;
@@ -159,8 +203,9 @@ int launch_dechirp_split(const Ctx &, const RadarD &, const grft_dsgrid &, int M
 // pair_mrow(M) per row), hi and lo planes of [2 Spad][Mrow]; padding slots and pulses are zero.
 int launch_dechirp_pair(const Ctx &, const RadarD &, const grft_dsgrid &, int Mrow, int Spad, bool fp16,
                         uint16_t *Bhi, uint16_t *Blo, const Rate3 &rate = kNoRate);
-// Whether the tensor-core contraction of a grid runs in the pair form: P = 2 grids (also a
-// P = 3 grid whose one fine rate offset is zero); DSGRFT_PAIR=0 selects the 4M form.
+// Whether the tensor-core contraction of a grid runs in the pair form: P = 2 grids, a P = 3
+// grid whose one fine rate offset is zero, and P = 3 grids with Fb >= 2 rate offsets
+// (pair_slot3); DSGRFT_PAIR=0 selects the 4M form.
 bool ds_pair_form(const Rate3 &rate);
 // Pulses per row of the pair form's dechirp operand: its stages take 64 pulses.
 inline int pair_mrow(int M) { return (M + 63) / 64 * 64; }

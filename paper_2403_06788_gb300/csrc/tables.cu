@@ -118,19 +118,19 @@ __global__ void k_dechirp_split(RadarD R, grft_dsgrid g, Rate3 rate, int Mpad, i
 }
 
 // B operand of the pair form: rows 2 s and 2 s + 1 of each plane hold Re D and Im D of slot
-// s's first hypothesis (pair_slot) over the pulses, K-major with the pulses contiguous;
+// s's first hypothesis (pair_slot3) over the pulses, K-major with the pulses contiguous;
 // slots s >= S (padding up to Spad) and pulses m >= M are zero.
 __global__ void k_dechirp_pair(RadarD R, grft_dsgrid g, Rate3 rate, int Mrow, int Spad, int fp16,
                                uint16_t *__restrict__ Bhi, uint16_t *__restrict__ Blo) {
-    const int S = pair_slot_count(g.Fv, g.Fa);
+    const int S = pair_slot_count3(g.Fv, g.Fa, rate.Fb);
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over Spad * Mrow, pulses fastest
     if (i >= (long)Spad * Mrow) return;
     const int s = (int)(i / Mrow), m = (int)(i % Mrow);
     float2 d = make_float2(0.f, 0.f);
     if (m < R.M && s < S) {
         int f, fm;
-        pair_slot(s, g.Fv, g.Fa, f, fm);
-        d = dechirp_value(R, g, m, f * rate.Fb, rate);      // u = 0: the one fine rate offset
+        pair_slot3(s, g.Fv, g.Fa, rate.Fb, f, fm);         // f: the full fine index
+        d = dechirp_value(R, g, m, f, rate);
     }
     const float vals[2] = {d.x, d.y};
     for (int ri = 0; ri < 2; ++ri) {

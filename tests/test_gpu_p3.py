@@ -139,3 +139,49 @@ def test_p3_empty_cell_range_writes_nothing(cuda_lib):
     g.dsgrft3_fine_dfm(R, torch.from_numpy(s).cuda(), g3, 5, 0, "bf16x3", None, P)
     torch.cuda.synchronize()
     assert g.grft_sync_status() == 0 and torch.all(P == 3.0)
+
+
+P3_CODE = r"""
+import sys, dataclasses, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2403_06788_gb300 as g
+from tests.test_gpu_p3 import _small
+R, g3, s = _small()
+g3 = dataclasses.replace(g3, Fb=int(sys.argv[2]))
+P, Y = g.dsgrft3(R, torch.from_numpy(s).cuda(), g3, precision=sys.argv[3], want_Y=True)
+assert g.grft_sync_status() == 0
+np.save(sys.argv[1], Y.cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("Fb,precision", [(3, "fp16x2"), (4, "bf16x3"), (2, "fp16x1")])
+def test_p3_pair_form_matches_4m_form_and_oracle(cuda_lib, tmp_path, Fb, precision):
+    """Mirrored hypotheses on all three fine axes ((k, q, u) and (Fv - k, Fa - q, Fb - u)
+    have conjugate dechirp rows; pair_slot3): the pair form of the P = 3 contraction matches
+    the 4M form (DSGRFT_PAIR=0) within the split tolerance and the FP64 oracle on every
+    output, for odd and even rate-offset counts."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def run(name, **env):
+        out = os.path.join(str(tmp_path), name + ".npy")
+        e = dict(os.environ)
+        e.update(env)
+        r = subprocess.run([sys.executable, "-c", P3_CODE % root, out, str(Fb), precision], env=e,
+                           capture_output=True, text=True, timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return np.load(out)
+
+    Yp = run("pair")
+    Y4 = run("m4", DSGRFT_PAIR="0")
+    R, g3, s = _small()
+    g3 = dataclasses.replace(g3, Fb=Fb)
+    cell, fine, shape = _rows(g3)
+    Yo = oracle.dsgrft3_rows(R, s, g3, cell, fine).reshape(*shape, g3.r0_count)
+    ep, e4 = rel_peak_err(Yp, Yo), rel_peak_err(Y4, Yo)
+    print(f"P=3 Fb={Fb} {precision}: pair form {ep:.3g}, 4M form {e4:.3g} of peak")
+    assert ep <= TOL_SPLIT and e4 <= TOL_SPLIT
+    assert ep <= 2 * e4 + 1e-6
+    assert rel_peak_err(Yp, Y4) <= TOL_SPLIT
