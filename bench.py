@@ -40,12 +40,13 @@ DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (269.658880e6 + 219.599872e6)}   # k_d
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
 def pair_bn(slots):
     """Tile width (B rows, two per slot) the pair form's contraction takes: of 256, 224 and 192
-    the one whose tiles cover the slots with the fewest columns, the wider on a tie."""
-    best, best_cols = 256, -(-slots // 128) * 256
+    the one with the fewest tiles, then the fewest columns."""
+    best, best_tiles = 256, -(-slots // 128)
+    best_cols = best_tiles * 256
     for bn in (224, 192):
-        cols = -(-slots // (bn // 2)) * bn
-        if cols < best_cols:
-            best, best_cols = bn, cols
+        tiles = -(-slots // (bn // 2))
+        if tiles < best_tiles or (tiles == best_tiles and tiles * bn < best_cols):
+            best, best_tiles, best_cols = bn, tiles, tiles * bn
     return best
 
 

@@ -210,16 +210,18 @@ bool ds_pair_form(const Rate3 &rate);
 // Pulses per row of the pair form's dechirp operand: its stages take 64 pulses.
 inline int pair_mrow(int M) { return (M + 63) / 64 * 64; }
 // Tile width (B rows, two per slot) of the pair form's contraction: of 256, 224 and 192 the
-// one whose tiles cover the slots with the fewest columns (the tensor work is proportional to
-// them), the wider on a tie (fewer tiles, fewer loads of the gathered operand).  For the
-// 64 x 16 fine grid's 552 slots: 224 (5 tiles, 1120 columns against 1280 at 256).
+// one with the fewest tiles (each tile loads the gathered operand again and has its own
+// epilogue: the kernel's time follows the tile count more than the columns), then the
+// fewest columns.  552 slots (the 64 x 16 fine grid): 224 (5 tiles of 112 slots, against
+// 5 of 128 at 256); 8352 slots (256 x 64): 256 (66 tiles; 192 would take 87).
 inline int pair_bn(int slots) {
     int best = 256;
-    long best_cols = (long)((slots + 127) / 128) * 256;
+    long best_tiles = (slots + 127) / 128, best_cols = best_tiles * 256;
     for (int bn : {224, 192}) {
-        const long cols = (long)((slots + bn / 2 - 1) / (bn / 2)) * bn;
-        if (cols < best_cols) {
+        const long tiles = (slots + bn / 2 - 1) / (bn / 2), cols = tiles * bn;
+        if (tiles < best_tiles || (tiles == best_tiles && cols < best_cols)) {
             best = bn;
+            best_tiles = tiles;
             best_cols = cols;
         }
     }
