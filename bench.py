@@ -875,7 +875,7 @@ def main():
     e2e_s = max_over_ranks(e2e_tot / e2e_steps, dev)
 
     # ---------------------------------------------------------------- plain GRFT, same hypotheses
-    plain_ms = None
+    plain_ms = plain_kernel_ms = plain_tables_ms = None
     # the plain grid restricted to the v-slab the DS step covers (the whole grid by default),
     # written into the same P buffer, whose shape it matches
     pg_slab = synth.PlainGrid(pg.r0_begin, pg.r0_count, synth.Axis(pg.v.start, pg.v.step, nv), pg.a)
@@ -885,12 +885,16 @@ def main():
         g.grft_plain(R, echo, pg_slab, None, P)
         torch.cuda.synchronize()
         a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g.grft_timing(True)                     # k_plain's own launches beside the whole call
         a_ev.record(stream)
         for _ in range(args.plain_steps):
             g.grft_plain(R, echo, pg_slab, None, P)
         b_ev.record(stream)
         torch.cuda.synchronize()
         plain_ms = a_ev.elapsed_time(b_ev) / args.plain_steps
+        plain_kernel_ms = g.grft_timing_get("plain")[1] / args.plain_steps
+        plain_tables_ms = g.grft_timing_get("tables")[1] / args.plain_steps
+        g.grft_timing(False)
     # plain GRFT's error at this size: Y of the whole grid (the timed calls write P only)
     # against the oracle on sampled (v, a) rows, every r0 bin (targets' rows included)
     plain_err = None
@@ -1041,8 +1045,11 @@ def main():
         "cfar": _bw("cfar", hyps_step * 4, ktime["cfar"][1] / args.steps if ktime["cfar"][0] else None),
         "coarse_rm (kernel a, standalone)": _bw("coarse_rm", crm_bytes, crm_ms) if crm_ms else None,
         "plain_grft": None if plain_ms is None else {
-            "bound": "fp32 fma", "ms": plain_ms, "achieved": 8 * plain_units / (1e-3 * plain_ms) / 1e12,
-            "unit": "TFLOP/s", "peak": fma_peak, "frac": 8 * plain_units / (1e-3 * plain_ms) / 1e12 / fma_peak},
+            "bound": "fp32 fma", "kernel": "k_plain (CUDA events around its launches)", "ms": plain_kernel_ms,
+            "achieved": 8 * plain_units / (1e-3 * plain_kernel_ms) / 1e12, "unit": "TFLOP/s", "peak": fma_peak,
+            "frac": 8 * plain_units / (1e-3 * plain_kernel_ms) / 1e12 / fma_peak,
+            "call_ms": plain_ms, "tables_ms": plain_tables_ms,
+            "call_frac": 8 * plain_units / (1e-3 * plain_ms) / 1e12 / fma_peak},
     }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -445,8 +445,6 @@ int fine_dfm_impl(const grft_radar *radar, const grft_c32 *Z, const grft_c32 *ec
     int e = make_ctx(stream, c);
     if (e) return e;
     const RadarD R = radar_d(*radar);
-    const int F = grid->Fv * grid->Fa * rate.Fb;
-    const int Fpad = (F + 127) / 128 * 128;
     const int Mpad = (R.M + 31) / 32 * 32;
     const bool tc = precision != GRFT_FP32;
     const size_t rho_bytes = align_up((size_t)cell_count * R.M * sizeof(int32_t));

@@ -22,19 +22,39 @@ __global__ void k_bins_phases(RadarD R, const double *__restrict__ v, const doub
     w[i] = range_phase(d, R.lambda);
 }
 
-// Plain grid: hypothesis h = vi * na + ai (global index h0 + local).
+// Plain grid: hypothesis h = vi * na + ai (global index h0 + local).  One thread per pulse m
+// and group of PT_GROUP hypotheses: t = m / PRF (an FP64 division) once for the group, and
+// the phase's cycle count 2 d / lambda as d x (2 / lambda) (within two ulps of the divided
+// one, far below the FP32 phase's resolution), so the bin's division d / dr is the only one
+// per entry: FP64 throughput is what bounds this kernel on GB300.  The bins are the same
+// IEEE operations as the definition's.
+constexpr int PT_GROUP = 8;
 __global__ void k_plain_tables(RadarD R, double v0, double dv, double a0, double da, int na,
-                               long h0, int nh, int32_t *__restrict__ rho, float2 *__restrict__ w) {
-    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long)nh * R.M) return;
-    long h = h0 + i / R.M;
-    int m = (int)(i % R.M);
-    double v = axis_value(v0, dv, (int)(h / na));
-    double a = axis_value(a0, da, (int)(h % na));
-    double t = slow_time(m, R.prf);
-    double d = displacement(v, a, t);
-    rho[i] = bin_shift(d, R.dr);
-    w[i] = range_phase(d, R.lambda);
+                               long h0, int nh, double two_over_lambda, int32_t *__restrict__ rho,
+                               float2 *__restrict__ w) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ngrp = (nh + PT_GROUP - 1) / PT_GROUP;
+    if (i >= (long)ngrp * R.M) return;
+    const int g = (int)(i / R.M), m = (int)(i % R.M);
+    const double t = slow_time(m, R.prf);
+    const double tt = __dmul_rn(t, t);
+#pragma unroll 2
+    for (int j = 0; j < PT_GROUP; ++j) {
+        const int hl = g * PT_GROUP + j;
+        if (hl >= nh) break;
+        const long h = h0 + hl;
+        const double v = axis_value(v0, dv, (int)(h / na));
+        const double a = axis_value(a0, da, (int)(h % na));
+        // displacement(v, a, t) with t t shared: (v t) + ((0.5 a)(t t))
+        const double d = __dadd_rn(__dmul_rn(v, t), __dmul_rn(__dmul_rn(0.5, a), tt));
+        const long o = (long)hl * R.M + m;
+        rho[o] = bin_shift(d, R.dr);
+        const double u = __dmul_rn(d, two_over_lambda);
+        const double f = __dsub_rn(u, rint(u));
+        float s, c;
+        sincospif(2.0f * (float)f, &s, &c);
+        w[o] = make_float2(c, s);
+    }
 }
 
 // Coarse cells c = i * na_c + l: bins of the coarse trajectory and H_pre-DFM.
@@ -157,11 +177,11 @@ int launch_bins_phases(const Ctx &c, const RadarD &R, const double *v, const dou
 
 int launch_plain_tables(const Ctx &c, const RadarD &R, const grft_grid &g, long h0, int nh,
                         int32_t *rho, float2 *w) {
-    long n = (long)nh * R.M;
+    const long n = (long)((nh + PT_GROUP - 1) / PT_GROUP) * R.M;
     if (n == 0) return GRFT_OK;
     KernelTimer kt(c, GRFT_KERNEL_TABLES);
-    k_plain_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g.v.start, g.v.step, g.a.start,
-                                                              g.a.step, g.a.count, h0, nh, rho, w);
+    k_plain_tables<<<blocks_for(n, 256), 256, 0, c.stream>>>(R, g.v.start, g.v.step, g.a.start, g.a.step,
+                                                              g.a.count, h0, nh, 2.0 / R.lambda, rho, w);
     return check_launch();
 }
 
