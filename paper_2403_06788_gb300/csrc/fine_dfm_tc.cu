@@ -914,6 +914,9 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
             float *const P = p.P;
             float2 *const Y = p.Y;
             const float2 e = (jok && Y) ? p.e0[j] : make_float2(1.f, 0.f);
+            // P only, rows of an even bin count, P 8-byte aligned: bin pairs (warp-uniform)
+            const bool p2 = P && !Y && (p.r0_count & 1) == 0 && (((uintptr_t)P) & 7) == 0;
+            const bool ob = (lane & 2) != 0;      // this lane's bin r / 2 is odd
             const uint32_t taddr0 = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
             for (int ch = ch0; ch < ch1; ++ch) {
@@ -928,7 +931,25 @@ __global__ void __launch_bounds__(PR_THREADS, 1)
                     X[i] = odd ? hi : lo;
                     W[i] = __shfl_xor_sync(0xffffffffu, odd ? lo : hi, 1);
                 }
-                if (jok) {
+                if (p2) {
+                    // lanes L and L ^ 2 hold bins b and b ^ 1 (b = r / 2) of the same two rows:
+                    // the lane of the even bin writes the U row's two bins, the other the V
+                    // row's (one shuffle, one 8-byte store per lane and slot)
+#pragma unroll
+                    for (int pp = 0; pp < 8; ++pp) {
+                        const int sl = ch * 16 + (odd ? 8 + pp : pp);
+                        const float x0 = X[2 * pp], x1 = X[2 * pp + 1], w0 = W[2 * pp], w1 = W[2 * pp + 1];
+                        const long of = s_off_f[sl], om = s_off_m[sl];
+                        const long ou = odd ? om : of, ov = odd ? of : om;
+                        const float ur = x0 - w1, ui = x1 + w0, vr = x0 + w1, vi = x1 - w0;
+                        const float U = ur * ur + ui * ui, V = vr * vr + vi * vi;
+                        const float recv = __shfl_xor_sync(0xffffffffu, ob ? U : V, 2);
+                        const long row = ob ? ov : ou;
+                        if (jok && row >= 0)
+                            __stcs(reinterpret_cast<float2 *>(P + row + (ob ? j - 1 : j)),
+                                   ob ? make_float2(recv, V) : make_float2(U, recv));
+                    }
+                } else if (jok) {
 #pragma unroll
                     for (int pp = 0; pp < 8; ++pp) {
                         const int sl = ch * 16 + (odd ? 8 + pp : pp);
