@@ -108,6 +108,128 @@ __global__ __launch_bounds__(256) void k_ds_simt(
     }
 }
 
+// The pair form in FP32 (the slots of pair_slot: a fine hypothesis and its mirror, whose
+// dechirp row is the conjugate): per slot and bin the four real sums A = sum Zr Dr,
+// E = sum Zi Dr, C = sum Zr Di, B = sum Zi Di, kept as the pairs (A, E) and (C, B) of two
+// paired FMAs per pulse with the gathered sample (Zr, Zi) as it lies in shared memory and the
+// slot's (Dr, Dr) and (Di, Di); then Y(f) = (A - B) + j (C + E), Y(f') = (A + B) + j (E - C).
+// Two FP32 FMAs per hypothesis and pulse, where the complex form takes four.
+// CTA tile: 128 bins x 64 slots, 256 threads, thread tile 8 bins x 4 slots.
+constexpr int SP_BS = 64;    // slots per CTA
+
+__device__ __forceinline__ void ffma2p(uint64_t &acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float2 unpack2p(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__global__ __launch_bounds__(256) void k_ds_simt_pair(
+    const float2 *__restrict__ echo, const float2 *__restrict__ Z, int M, int N,
+    const int32_t *__restrict__ rho_c, const float2 *__restrict__ w_c,
+    const float2 *__restrict__ D, const float2 *__restrict__ e0, int r0_begin, int r0_count,
+    int F, int S, DsOut out) {
+    __shared__ alignas(16) float2 sA[SM_BK][SM_BN];
+    __shared__ alignas(16) float4 sB[SM_BK][SP_BS];      // (Dr, Dr, Di, Di) of each slot's first hypothesis
+    __shared__ int s_f[SP_BS], s_fm[SP_BS];
+
+    const int cl = blockIdx.z;
+    const int jt = blockIdx.x * SM_BN;
+    const int st = blockIdx.y * SP_BS;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    if (threadIdx.x < SP_BS) {
+        int f = -1, fm = -1;
+        if (st + threadIdx.x < S) pair_slot(st + threadIdx.x, out.Fv, out.Fa, f, fm);
+        s_f[threadIdx.x] = f;
+        s_fm[threadIdx.x] = fm;
+    }
+
+    uint64_t ae[SM_TN][SM_TF], cb[SM_TN][SM_TF];
+#pragma unroll
+    for (int a = 0; a < SM_TN; ++a)
+#pragma unroll
+        for (int b = 0; b < SM_TF; ++b) ae[a][b] = cb[a][b] = 0ull;
+
+    __syncthreads();
+    for (int m0 = 0; m0 < M; m0 += SM_BK) {
+        for (int i = threadIdx.x; i < SM_BK * SM_BN; i += 256) {
+            const int mm = i / SM_BN, jn = i % SM_BN;
+            const int m = m0 + mm, j = jt + jn;
+            float2 v = make_float2(0.f, 0.f);
+            if (m < M && j < r0_count) {
+                const long o = (long)cl * M + m;
+                if (Z) {
+                    v = Z[o * r0_count + j];
+                } else {
+                    const int n = r0_begin + j + rho_c[o];
+                    if ((unsigned)n < (unsigned)N) v = cmul(__ldg(echo + (long)m * N + n), w_c[o]);
+                }
+            }
+            sA[mm][jn] = v;
+        }
+        for (int i = threadIdx.x; i < SM_BK * SP_BS; i += 256) {
+            const int mm = i / SP_BS, sn = i % SP_BS;
+            const int m = m0 + mm, f = s_f[sn];
+            const float2 d = (m < M && f >= 0) ? D[(long)m * F + f] : make_float2(0.f, 0.f);
+            sB[mm][sn] = make_float4(d.x, d.x, d.y, d.y);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int mm = 0; mm < SM_BK; ++mm) {
+            uint64_t a[SM_TN];
+            ulonglong2 b[SM_TF];
+            const ulonglong2 *pa = reinterpret_cast<const ulonglong2 *>(&sA[mm][tx * SM_TN]);
+#pragma unroll
+            for (int q = 0; q < SM_TN / 2; ++q) {
+                const ulonglong2 t = pa[q];
+                a[2 * q] = t.x;
+                a[2 * q + 1] = t.y;
+            }
+            const ulonglong2 *pb = reinterpret_cast<const ulonglong2 *>(&sB[mm][ty * SM_TF]);
+#pragma unroll
+            for (int y = 0; y < SM_TF; ++y) b[y] = pb[y];
+#pragma unroll
+            for (int x = 0; x < SM_TN; ++x)
+#pragma unroll
+                for (int y = 0; y < SM_TF; ++y) {
+                    ffma2p(ae[x][y], a[x], b[y].x);     // (A, E) += (Zr, Zi) (Dr, Dr)
+                    ffma2p(cb[x][y], a[x], b[y].y);     // (C, B) += (Zr, Zi) (Di, Di)
+                }
+        }
+        __syncthreads();
+    }
+
+    // epilogue: both hypotheses of each slot, canonical v-slab layout
+    const int c = out.cell_begin + cl;
+    const int iv = c / out.na_c - out.i0, il = c % out.na_c;
+    const int na_full = out.na_c * out.Fa;
+#pragma unroll
+    for (int y = 0; y < SM_TF; ++y) {
+        const int sn = ty * SM_TF + y;
+        const int f = s_f[sn], fm = s_fm[sn];
+        if (f < 0) continue;
+        const long rf = ((long)(iv * out.Fv + f / out.Fa) * na_full + (il * out.Fa + f % out.Fa)) * r0_count;
+        const long rm =
+            fm < 0 ? -1 : ((long)(iv * out.Fv + fm / out.Fa) * na_full + (il * out.Fa + fm % out.Fa)) * r0_count;
+#pragma unroll
+        for (int x = 0; x < SM_TN; ++x) {
+            const int j = jt + tx * SM_TN + x;
+            if (j >= r0_count) break;
+            const float2 AE = unpack2p(ae[x][y]), CB = unpack2p(cb[x][y]);
+            const float2 yf = make_float2(AE.x - CB.y, CB.x + AE.y);     // (A - B, C + E)
+            const float2 ym = make_float2(AE.x + CB.y, AE.y - CB.x);     // (A + B, E - C)
+            if (out.Y) out.Y[rf + j] = cmul(e0[j], yf);
+            if (out.P) out.P[rf + j] = yf.x * yf.x + yf.y * yf.y;
+            if (rm >= 0) {
+                if (out.Y) out.Y[rm + j] = cmul(e0[j], ym);
+                if (out.P) out.P[rm + j] = ym.x * ym.x + ym.y * ym.y;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int launch_ds_simt(const Ctx &c, const RadarD &R, const float2 *echo, const float2 *Z,
@@ -115,8 +237,15 @@ int launch_ds_simt(const Ctx &c, const RadarD &R, const float2 *echo, const floa
                    const float2 *D, const float2 *e0, const DsOut &out) {
     if (cell_count == 0 || g.r0_count == 0) return GRFT_OK;
     const int F = g.Fv * g.Fa;
-    dim3 grid((g.r0_count + SM_BN - 1) / SM_BN, (F + SM_BF - 1) / SM_BF, cell_count);
     KernelTimer kt(c, GRFT_KERNEL_CONTRACT_FP32);
+    if (ds_pair_form(kNoRate)) {             // the pair form (DSGRFT_PAIR=0: the complex form)
+        const int S = pair_slot_count(g.Fv, g.Fa);
+        dim3 grid((g.r0_count + SM_BN - 1) / SM_BN, (S + SP_BS - 1) / SP_BS, cell_count);
+        k_ds_simt_pair<<<grid, 256, 0, c.stream>>>(echo, Z, R.M, R.N, rho, w, D, e0, g.r0_begin, g.r0_count,
+                                                   F, S, out);
+        return check_launch();
+    }
+    dim3 grid((g.r0_count + SM_BN - 1) / SM_BN, (F + SM_BF - 1) / SM_BF, cell_count);
     k_ds_simt<<<grid, 256, 0, c.stream>>>(echo, Z, R.M, R.N, rho, w, D, e0, g.r0_begin, g.r0_count,
                                           F, out);
     return check_launch();

@@ -85,9 +85,10 @@ np.save(sys.argv[1] + ".echo.npy", s)
 
 
 # tile widths (pair_bn): 16 x 16, 5 x 3, 7 x 1, 1 x 6 take 192 columns; 15 x 14 (119 slots) 256;
-# 64 x 16 (552 slots) and 48 x 16 224
+# 64 x 16 (552 slots) and 48 x 16 224; fp32: the SIMT contraction's pair form
 @pytest.mark.parametrize("Fv,Fa,precision", [(16, 16, "fp16x2"), (5, 3, "fp16x2"), (7, 1, "bf16x3"), (1, 6, "fp16x1"),
-                                             (64, 16, "bf16x3"), (15, 14, "fp16x2"), (48, 16, "fp16x2")])
+                                             (64, 16, "bf16x3"), (15, 14, "fp16x2"), (48, 16, "fp16x2"),
+                                             (9, 5, "fp32")])
 def test_pair_form_matches_4m_form_and_oracle(cuda_lib, tmp_path, Fv, Fa, precision):
     import numpy as np
     import oracle
