@@ -153,30 +153,59 @@ __global__ __launch_bounds__(256) void k_ds_simt_pair(
         for (int b = 0; b < SM_TF; ++b) ae[a][b] = cb[a][b] = 0ull;
 
     __syncthreads();
-    for (int m0 = 0; m0 < M; m0 += SM_BK) {
-        for (int i = threadIdx.x; i < SM_BK * SM_BN; i += 256) {
+    // Staging, double-buffered through registers: the next stage's samples (echo value and
+    // coarse phase, multiplied when stored) and dechirp entries are loaded before the current
+    // stage is accumulated.  Thread i of the CTA stages elements i, i + 256, ... of each tile.
+    constexpr int NA = SM_BK * SM_BN / 256, NB = SM_BK * SP_BS / 256;
+    float2 ra[NA], rw[NA], rb[NB];
+    auto fetch = [&](int m0) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int i = threadIdx.x + 256 * u;
             const int mm = i / SM_BN, jn = i % SM_BN;
             const int m = m0 + mm, j = jt + jn;
-            float2 v = make_float2(0.f, 0.f);
+            float2 v = make_float2(0.f, 0.f), wv = make_float2(1.f, 0.f);
             if (m < M && j < r0_count) {
                 const long o = (long)cl * M + m;
                 if (Z) {
                     v = Z[o * r0_count + j];
                 } else {
                     const int n = r0_begin + j + rho_c[o];
-                    if ((unsigned)n < (unsigned)N) v = cmul(__ldg(echo + (long)m * N + n), w_c[o]);
+                    if ((unsigned)n < (unsigned)N) {
+                        v = __ldg(echo + (long)m * N + n);
+                        wv = w_c[o];
+                    }
                 }
             }
-            sA[mm][jn] = v;
+            ra[u] = v;
+            rw[u] = wv;
         }
-        for (int i = threadIdx.x; i < SM_BK * SP_BS; i += 256) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int i = threadIdx.x + 256 * u;
             const int mm = i / SP_BS, sn = i % SP_BS;
             const int m = m0 + mm, f = s_f[sn];
-            const float2 d = (m < M && f >= 0) ? D[(long)m * F + f] : make_float2(0.f, 0.f);
-            sB[mm][sn] = make_float4(d.x, d.x, d.y, d.y);
+            rb[u] = (m < M && f >= 0) ? D[(long)m * F + f] : make_float2(0.f, 0.f);
         }
-        __syncthreads();
-#pragma unroll 4
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int i = threadIdx.x + 256 * u;
+            sA[i / SM_BN][i % SM_BN] = Z ? ra[u] : cmul(ra[u], rw[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int i = threadIdx.x + 256 * u;
+            sB[i / SP_BS][i % SP_BS] = make_float4(rb[u].x, rb[u].x, rb[u].y, rb[u].y);
+        }
+    };
+    fetch(0);
+    store();
+    __syncthreads();
+    for (int m0 = 0; m0 < M; m0 += SM_BK) {
+        if (m0 + SM_BK < M) fetch(m0 + SM_BK);
+#pragma unroll 2
         for (int mm = 0; mm < SM_BK; ++mm) {
             uint64_t a[SM_TN];
             ulonglong2 b[SM_TF];
@@ -199,6 +228,10 @@ __global__ __launch_bounds__(256) void k_ds_simt_pair(
                 }
         }
         __syncthreads();
+        if (m0 + SM_BK < M) {
+            store();
+            __syncthreads();
+        }
     }
 
     // epilogue: both hypotheses of each slot, canonical v-slab layout
