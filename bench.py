@@ -36,7 +36,7 @@ ACC_ROWS = 512                  # random (v, a) rows of the accuracy check (ever
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the contraction kernel on the first 16
 # coarse cells, scaled by 16 to one launch of this workload (all 256 cells in one launch),
 # per precision.  None until a capture of the current kernel exists.
-DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (269.658880e6 + 219.599872e6)}   # k_ds_pair<3, 2, 224>
+DRAM_TRAFFIC_PER_LAUNCH = {"fp16x2": 16 * (269.672960e6 + 219.864064e6)}   # k_ds_pair<3, 2, 224>
 PRODUCTS_PER_MAC = {"bf16x3": 3, "fp16x3": 3, "fp16x2": 2, "fp16x1": 1, "fp32": 1}
 def pair_bn(slots):
     """Tile width (B rows, two per slot) the pair form's contraction takes: of 256, 224 and 192
