@@ -2,7 +2,7 @@
 //   Y[h][n0] = e0(n0) * sum_m s[m][n0 + rho_h(m)] * w_h(m)
 // FP32 SIMT.  A CTA owns a group of PL_H hypotheses and a tile of PL_THREADS*PL_J range
 // bins; each thread accumulates PL_J bins (32 apart, so warp accesses are contiguous) for
-// all PL_H hypotheses (8 x 4 by default, 16 x 2 selectable).  Bins and phases come from a per-chunk table (FP64-built).
+// all PL_H hypotheses (8 x 2 by default; 8 x 4 and 16 x 2 selectable).  Bins and phases come from a per-chunk table (FP64-built).
 // Consecutive hypotheses of a group are neighbouring accelerations, whose bin shift is
 // nearly always the same at a given pulse: a per-pulse flag marks the pulses where all of
 // them share the first one's shift (one row of samples, no per-hypothesis check); at the
@@ -40,7 +40,7 @@ __device__ __forceinline__ void ffma2(uint64_t &acc, uint64_t a, uint64_t b) {
 // PL_H hypotheses per CTA, PL_J bins per thread: a gathered sample serves PL_H hypotheses
 // (the L2 gathers per FMA fall as PL_H grows) and the accumulators take 2 PL_H PL_J registers.
 template <int PL_H, int PL_J>
-__global__ __launch_bounds__(PL_THREADS, 2) void k_plain(
+__global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_plain(
     const float2 *__restrict__ echo, int M, int N, const int32_t *__restrict__ rho_tab,
     const float2 *__restrict__ w_tab, int nh, int r0_begin, int r0_count,
     const float2 *__restrict__ e0, float2 *__restrict__ Y, float *__restrict__ P) {
@@ -216,13 +216,17 @@ int launch_plain_shape(const Ctx &c, const RadarD &R, const float2 *echo, const 
     return check_launch();
 }
 
-// Tile shape of k_plain: 8 hypotheses x 4 bins per thread by default; DSGRFT_PLAIN_SHAPE=16x2
-// selects 16 x 2 (the same arithmetic per output, so the same results bit for bit; measured
-// equal in time: the L2 gathers, which 16 x 2 halves per FMA, do not bound the kernel).
+// Tile shape of k_plain (hypotheses x bins per thread): 8 x 2 at three CTAs per SM by
+// default; DSGRFT_PLAIN_SHAPE=8x4 or 16x2 selects the two-CTA shapes (the same arithmetic
+// per output, so the same results bit for bit).  For 2^39 hypothesis-pulses: 8 x 2 114.7 ms,
+// 8 x 4 115.9, 16 x 2 116.9 (whole calls, tables included): neither the L2 gathers, which
+// 16 x 2 halves per FMA, nor the occupancy bounds the kernel much.
 int plain_shape() {
     static const int v = [] {
         const char *e = getenv("DSGRFT_PLAIN_SHAPE");
-        return (e && e[0] == '1') ? 0 : 1;
+        if (e && e[0] == '1') return 2;
+        if (e && e[0] == '8' && e[2] == '4') return 1;
+        return 0;
     }();
     return v;
 }
@@ -239,8 +243,11 @@ int launch_plain(const Ctx &c, const RadarD &R, const float2 *echo, const grft_g
     if (nh == 0 || g.r0_count == 0) return GRFT_OK;
     float2 *Yc = Y ? Y + h0 * g.r0_count : nullptr;
     float *Pc = P ? P + h0 * g.r0_count : nullptr;
-    if (plain_shape() == 1) return launch_plain_shape<8, 4>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
-    return launch_plain_shape<16, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    switch (plain_shape()) {
+    case 1: return launch_plain_shape<8, 4>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    case 2: return launch_plain_shape<16, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    default: return launch_plain_shape<8, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    }
 }
 
 }  // namespace grft
