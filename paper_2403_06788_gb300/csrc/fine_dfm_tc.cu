@@ -1423,7 +1423,11 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     flush();
     if (rounds.empty()) return GRFT_OK;
     int e;
-    if (rounds.size() == 1 || !Zhi[1] || !Zlo[1]) {   // one buffer: rounds on the caller's stream
+    static const bool overlap = [] {             // DSGRFT_OVERLAP=0: every round on the caller's stream
+        const char *e = getenv("DSGRFT_OVERLAP");
+        return !(e && e[0] == '0');
+    }();
+    if (rounds.size() == 1 || !Zhi[1] || !Zlo[1] || !overlap) {   // rounds in sequence on the caller's stream
         for (const Round &rd : rounds) {
             if ((e = launch_split(c, rd.b, Zhi[0], Zlo[0]))) return e;
             if ((e = launch_round_gemm(c, rd, Mpad, Fpad, Bhi, Blo, Zhi[0], Zlo[0], variant, key))) return e;
