@@ -247,7 +247,7 @@ __device__ __forceinline__ float2 ld_global_nc_hint(const float2 *src, uint64_t 
     return v;
 }
 
-__global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_constant__ TcBatch B,
+__global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_constant__ TcBatch B,
                                                              uint16_t *__restrict__ Zhi,
                                                              uint16_t *__restrict__ Zlo, int tab_cap) {
     // One CTA per (item, cell, 128-bin tile), four warps; warp w owns the 32 bins 32w + lane of
@@ -372,12 +372,20 @@ __global__ void __launch_bounds__(SP_THREADS, 5) k_coarse_split(const __grid_con
         };
         float2 va[8], vb[8];
         if (p.M == 32 * p.KT) {                 // whole 32-pulse groups: every sub-step is whole
+            float2 vc[8], vd[8];
             ld(0, va);
-            for (int s = 0; s < S; s += 2) {    // the two buffers alternate
-                ld(s + 1, vb);
+            ld(1, vb);
+            for (int s = 0; s < S; s += 4) {    // four buffers, two sub-steps ahead (S % 4 == 0)
+                ld(s + 2, vc);
+                ld(s + 3, vd);
                 cv(s, va);
-                if (s + 2 < S) ld(s + 2, va);
                 cv(s + 1, vb);
+                if (s + 4 < S) {
+                    ld(s + 4, va);
+                    ld(s + 5, vb);
+                }
+                cv(s + 2, vc);
+                cv(s + 3, vd);
             }
             return;
         }
