@@ -7,9 +7,9 @@
 // nearly always the same at a given pulse: a per-pulse flag marks the pulses where all of
 // them share the first one's shift (one row of samples, no per-hypothesis check); at the
 // others the samples are reloaded when the (CTA-uniform) shift changes.  The complex
-// multiply-adds run as paired FP32 FMAs (fma.rn.f32x2 on (re, im) accumulator pairs, with
-// the phase and the phase times j staged in shared memory), which rounds exactly as the
-// scalar form and halves the FMA instruction count.
+// multiply-adds run as paired FP32 FMAs (fma.rn.f32x2 over a pair of hypotheses, the
+// phases staged in shared memory), which round exactly as the scalar form and halve the
+// FMA instruction count.
 #include <climits>
 #include <cstdlib>
 
@@ -39,15 +39,21 @@ __device__ __forceinline__ void ffma2(uint64_t &acc, uint64_t a, uint64_t b) {
 
 // PL_H hypotheses per CTA, PL_J bins per thread: a gathered sample serves PL_H hypotheses
 // (the L2 gathers per FMA fall as PL_H grows) and the accumulators take 2 PL_H PL_J registers.
+// The paired FMAs pair two hypotheses (h, h + 1) of one bin: the real parts of both in one
+// accumulator pair and the imaginary parts in another, against the pair's phases (re_h,
+// re_h+1) and (im_h, im_h+1), one 16-byte shared word per hypothesis pair and pulse.  Per
+// output component the FMAs and their order are those of the scalar form
+//   re += (-s.im) w.im, re += s.re w.re;   im += s.im w.re, im += s.re w.im.
 template <int PL_H, int PL_J>
 __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_plain(
     const float2 *__restrict__ echo, int M, int N, const int32_t *__restrict__ rho_tab,
     const float2 *__restrict__ w_tab, int nh, int r0_begin, int r0_count,
     const float2 *__restrict__ e0, float2 *__restrict__ Y, float *__restrict__ P) {
+    static_assert(PL_H % 2 == 0, "hypotheses are paired");
     constexpr int PL_TILE = PL_THREADS * PL_J;
+    constexpr int H2 = PL_H / 2;
     __shared__ int s_rho[PL_MCHUNK][PL_H];
-    __shared__ alignas(16) float2 s_w[PL_MCHUNK][PL_H];     // w
-    __shared__ alignas(16) float2 s_jw[PL_MCHUNK][PL_H];    // j w = (-w.im, w.re)
+    __shared__ alignas(16) float s_w[PL_MCHUNK][H2][4];   // (re h, re h+1, im h, im h+1)
     __shared__ int s_same[PL_MCHUNK];            // every hypothesis of the group shifts like the first
     __shared__ int s_rng[2];                     // least and greatest shift of the chunk
 
@@ -59,23 +65,23 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
     const int n0 = r0_begin + j0;
     const int n0_tile = r0_begin + blockIdx.x * PL_TILE;   // first bin of the CTA's tile
 
-    uint64_t acc[PL_H][PL_J];                  // (re, im) pairs for the paired FMA
+    uint64_t are[H2][PL_J], aim[H2][PL_J];     // (re h, re h+1) and (im h, im h+1)
 #pragma unroll
-    for (int h = 0; h < PL_H; ++h)
+    for (int h = 0; h < H2; ++h)
 #pragma unroll
-        for (int j = 0; j < PL_J; ++j) acc[h][j] = 0ull;
+        for (int j = 0; j < PL_J; ++j) are[h][j] = aim[h][j] = 0ull;
 
     for (int mc = 0; mc < M; mc += PL_MCHUNK) {
         const int mn = min(PL_MCHUNK, M - mc);
         __syncthreads();
         for (int i = threadIdx.x; i < PL_H * PL_MCHUNK; i += PL_THREADS) {
-            const int h = i % PL_H, mm = i / PL_H;   // consecutive threads: consecutive smem words
+            const int h = i % PL_H, mm = i / PL_H;
             bool ok = h < nhl && mm < mn;
             long o = (long)(h0 + h) * M + mc + mm;
             const float2 wv = ok ? w_tab[o] : make_float2(0.f, 0.f);
             s_rho[mm][h] = ok ? rho_tab[o] : 0;
-            s_w[mm][h] = wv;
-            s_jw[mm][h] = make_float2(-wv.y, wv.x);
+            s_w[mm][h >> 1][h & 1] = wv.x;
+            s_w[mm][h >> 1][2 + (h & 1)] = wv.y;
         }
         if (threadIdx.x == 0) {
             s_rng[0] = INT_MAX;
@@ -115,61 +121,57 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
                     v[j] = ((unsigned)(base + 32 * j) < (unsigned)N) ? __ldg(row + 32 * j) : make_float2(0.f, 0.f);
             }
         };
-        // Accumulate pulse mm whose samples (at the first hypothesis' shift) are in sv.
+        // the four paired FMAs of hypothesis pair h2 and bin j: samples (re, re'), (im, im'),
+        // (-im, -im') of the pair's two hypotheses, phases w = ((re h, re h+1), (im h, im h+1))
+        auto mac = [&](int h2, int j, uint64_t sr, uint64_t si, uint64_t sn, const ulonglong2 &w) {
+            ffma2(are[h2][j], sn, w.y);
+            ffma2(aim[h2][j], si, w.x);
+            ffma2(are[h2][j], sr, w.x);
+            ffma2(aim[h2][j], sr, w.y);
+        };
+        // Accumulate pulse mm whose samples (at the first hypothesis' shift) are in sv0.
         auto pulse = [&](int mm, const float2 (&sv0)[PL_J]) {
-            // (re, re) and (im, im) of every sample, reused by all hypotheses of the pulse
-            uint64_t sr[PL_J], si[PL_J];
-#pragma unroll
-            for (int j = 0; j < PL_J; ++j) {
-                sr[j] = pack2(sv0[j].x, sv0[j].x);
-                si[j] = pack2(sv0[j].y, sv0[j].y);
-            }
+            const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0][0]);
             if (s_same[mm]) {                // CTA-uniform: one row of samples for all hypotheses
-                const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0]);
-                const ulonglong2 *jp = reinterpret_cast<const ulonglong2 *>(&s_jw[mm][0]);
-                // per accumulator the same two FMAs in the same order (im * (j w), then
-                // re * w); the 2 PL_J independent accumulators of a hypothesis pair take their
-                // first products before their second ones, so dependent FMAs sit 2 PL_J
-                // instructions apart
+                // (re, re), (im, im) and (-im, -im) of every sample, reused by all hypotheses
+                uint64_t sr[PL_J], si[PL_J], sn[PL_J];
 #pragma unroll
-                for (int h2 = 0; h2 < PL_H / 2; ++h2) {
-                    const ulonglong2 w2 = wp[h2], j2 = jp[h2];
+                for (int j = 0; j < PL_J; ++j) {
+                    sr[j] = pack2(sv0[j].x, sv0[j].x);
+                    si[j] = pack2(sv0[j].y, sv0[j].y);
+                    sn[j] = pack2(-sv0[j].y, -sv0[j].y);
+                }
 #pragma unroll
-                    for (int j = 0; j < PL_J; ++j) {
-                        ffma2(acc[2 * h2][j], si[j], j2.x);
-                        ffma2(acc[2 * h2 + 1][j], si[j], j2.y);
-                    }
+                for (int h2 = 0; h2 < H2; ++h2) {
+                    const ulonglong2 w = wp[h2];
 #pragma unroll
-                    for (int j = 0; j < PL_J; ++j) {
-                        ffma2(acc[2 * h2][j], sr[j], w2.x);
-                        ffma2(acc[2 * h2 + 1][j], sr[j], w2.y);
-                    }
+                    for (int j = 0; j < PL_J; ++j) mac(h2, j, sr[j], si[j], sn[j], w);
                 }
                 return;
             }
             int prev = s_rho[mm][0];
+            float2 cur[PL_J];
 #pragma unroll
-            for (int h = 0; h < PL_H; ++h) {
-                const int r = s_rho[mm][h];
-                if (r != prev) {             // CTA-uniform branch
-                    prev = r;
-                    float2 sv[PL_J];
-                    load_row(mm, r, sv);
+            for (int j = 0; j < PL_J; ++j) cur[j] = sv0[j];
 #pragma unroll
-                    for (int j = 0; j < PL_J; ++j) {
-                        sr[j] = pack2(sv[j].x, sv[j].x);
-                        si[j] = pack2(sv[j].y, sv[j].y);
-                    }
+            for (int h2 = 0; h2 < H2; ++h2) {
+                float2 sa[PL_J];
+                const int ra = s_rho[mm][2 * h2], rb = s_rho[mm][2 * h2 + 1];
+                if (ra != prev) {            // CTA-uniform branches
+                    prev = ra;
+                    load_row(mm, ra, cur);
                 }
-                const uint64_t w = *reinterpret_cast<const uint64_t *>(&s_w[mm][h]);
-                const uint64_t jw = *reinterpret_cast<const uint64_t *>(&s_jw[mm][h]);
-                // acc += im * (j w), then acc += re * w: per component the same two
-                // roundings, in the same order, as fmaf(re, w, fmaf(-im, w.im, acc)) etc.
 #pragma unroll
-                for (int j = 0; j < PL_J; ++j) {
-                    ffma2(acc[h][j], si[j], jw);
-                    ffma2(acc[h][j], sr[j], w);
+                for (int j = 0; j < PL_J; ++j) sa[j] = cur[j];
+                if (rb != prev) {
+                    prev = rb;
+                    load_row(mm, rb, cur);
                 }
+                const ulonglong2 w = wp[h2];
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j)
+                    mac(h2, j, pack2(sa[j].x, cur[j].x), pack2(sa[j].y, cur[j].y),
+                        pack2(-sa[j].y, -cur[j].y), w);
             }
         };
         // two pulses of look-ahead over three buffers in rotation: the samples of pulses mm+1
@@ -195,12 +197,17 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
         if (jj >= r0_count) break;
         const float2 e = e0[jj];
 #pragma unroll
-        for (int h = 0; h < PL_H; ++h) {
-            if (h >= nhl) break;
-            const float2 a = unpack2(acc[h][j]);
-            const long o = (long)(h0 + h) * r0_count + jj;
-            if (Y) Y[o] = cmul(e, a);
-            if (P) P[o] = a.x * a.x + a.y * a.y;
+        for (int h2 = 0; h2 < H2; ++h2) {
+            const float2 re = unpack2(are[h2][j]), im = unpack2(aim[h2][j]);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int h = 2 * h2 + t;
+                if (h >= nhl) break;
+                const float2 a = t ? make_float2(re.y, im.y) : make_float2(re.x, im.x);
+                const long o = (long)(h0 + h) * r0_count + jj;
+                if (Y) Y[o] = cmul(e, a);
+                if (P) P[o] = a.x * a.x + a.y * a.y;
+            }
         }
     }
 }
