@@ -29,8 +29,27 @@ __device__ __forceinline__ double displacement3(double v, double a, double b, do
     return __dadd_rn(displacement(v, a, t), __dmul_rn(__ddiv_rn(b, 6.0), __dmul_rn(tt, t)));
 }
 
-__device__ __forceinline__ int bin_shift(double d, double dr) {
+// The range bin of displacement d: floor(d / dr + 1/2), with d / dr the correctly rounded
+// FP64 quotient.  The quotient is first taken as p = d x inv_dr (inv_dr = 1 / dr rounded):
+// p lies within 3 units in the last place of the rounded quotient q, so x = p + 1/2 and
+// q + 1/2 (each rounded) have the same floor unless an integer lies between them, which
+// needs x within 2^-50 |p| + 2^-53 of that integer.  Only then (about one entry in 10^12 of
+// random displacements, and every exact half-bin tie) is the division carried out.  The
+// host form (tests) is the same operations; it needs FMA contraction off.
+__host__ __device__ __forceinline__ int bin_shift(double d, double dr, double inv_dr) {
+#ifdef __CUDA_ARCH__
+    const double p = __dmul_rn(d, inv_dr);
+    const double x = __dadd_rn(p, 0.5);
+#else
+    const double p = d * inv_dr;
+    const double x = p + 0.5;
+#endif
+    if (fabs(x - rint(x)) > fabs(p) * 0x1p-48 + 0x1p-44) return (int)floor(x);
+#ifdef __CUDA_ARCH__
     return (int)floor(__dadd_rn(__ddiv_rn(d, dr), 0.5));
+#else
+    return (int)floor(d / dr + 0.5);
+#endif
 }
 
 // exp(+j 4 pi x / lambda): FP64 cycle count 2x/lambda, reduced to [-1/2, 1/2] in FP64,
@@ -155,6 +174,7 @@ __host__ __device__ inline void pair_slot3(int s, int Fv, int Fa, int Fb, int &f
 struct RadarD {     // radar constants as the kernels use them
     int M, N;
     double prf, dr, lambda;
+    double inv_dr;   // 1 / dr, rounded (bin_shift)
 };
 
 inline RadarD radar_d(const grft_radar &r) {
@@ -164,6 +184,7 @@ inline RadarD radar_d(const grft_radar &r) {
     d.prf = r.prf_hz;
     d.dr = r.dr_m;
     d.lambda = r.c_mps / r.fc_hz;
+    d.inv_dr = 1.0 / r.dr_m;
     return d;
 }
 

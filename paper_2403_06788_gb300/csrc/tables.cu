@@ -18,16 +18,17 @@ __global__ void k_bins_phases(RadarD R, const double *__restrict__ v, const doub
     int h = (int)(i / R.M), m = (int)(i % R.M);
     double t = slow_time(m, R.prf);
     double d = displacement(v[h], a[h], t);
-    rho[i] = bin_shift(d, R.dr);
+    rho[i] = bin_shift(d, R.dr, R.inv_dr);
     w[i] = range_phase(d, R.lambda);
 }
 
 // Plain grid: hypothesis h = vi * na + ai (global index h0 + local).  One thread per pulse m
 // and group of PT_GROUP hypotheses: t = m / PRF (an FP64 division) once for the group, and
 // the phase's cycle count 2 d / lambda as d x (2 / lambda) (within two ulps of the divided
-// one, far below the FP32 phase's resolution), so the bin's division d / dr is the only one
-// per entry: FP64 throughput is what bounds this kernel on GB300.  The bins are the same
-// IEEE operations as the definition's.
+// one, far below the FP32 phase's resolution), and the bin's quotient d / dr as a product
+// with the rounded reciprocal, divided only where that could change the bin (bin_shift):
+// FP64 throughput is what bounds this kernel on GB300.  The bins are those of the
+// definition's IEEE operations.
 constexpr int PT_GROUP = 8;
 __global__ void k_plain_tables(RadarD R, double v0, double dv, double a0, double da, int na,
                                long h0, int nh, double two_over_lambda, int32_t *__restrict__ rho,
@@ -48,7 +49,7 @@ __global__ void k_plain_tables(RadarD R, double v0, double dv, double a0, double
         // displacement(v, a, t) with t t shared: (v t) + ((0.5 a)(t t))
         const double d = __dadd_rn(__dmul_rn(v, t), __dmul_rn(__dmul_rn(0.5, a), tt));
         const long o = (long)hl * R.M + m;
-        rho[o] = bin_shift(d, R.dr);
+        rho[o] = bin_shift(d, R.dr, R.inv_dr);
         const double u = __dmul_rn(d, two_over_lambda);
         const double f = __dsub_rn(u, rint(u));
         float s, c;
@@ -69,7 +70,7 @@ __global__ void k_coarse_tables(RadarD R, grft_dsgrid g, Rate3 rate, int cell_be
     double ac = axis_value(g.ac.start, g.ac.step, c % g.ac.count);
     double t = slow_time(m, R.prf);
     double d = rate.on ? displacement3(vc, ac, axis_value(rate.start, rate.step, cw), t) : displacement(vc, ac, t);
-    rho[idx] = bin_shift(d, R.dr);
+    rho[idx] = bin_shift(d, R.dr, R.inv_dr);
     w[idx] = range_phase(d, R.lambda);
 }
 
