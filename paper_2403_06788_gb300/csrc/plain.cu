@@ -2,7 +2,7 @@
 //   Y[h][n0] = e0(n0) * sum_m s[m][n0 + rho_h(m)] * w_h(m)
 // FP32 SIMT.  A CTA owns a group of PL_H hypotheses and a tile of PL_THREADS*PL_J range
 // bins; each thread accumulates PL_J bins (32 apart, so warp accesses are contiguous) for
-// all PL_H hypotheses (8 x 2 by default; 8 x 4 and 16 x 2 selectable).  Bins and phases come from a per-chunk table (FP64-built).
+// all PL_H hypotheses (8 x 4 by default; 8 x 2 and 16 x 2 selectable).  Bins and phases come from a per-chunk table (FP64-built).
 // Consecutive hypotheses of a group are neighbouring accelerations, whose bin shift is
 // nearly always the same at a given pulse: a per-pulse flag marks the pulses where all of
 // them share the first one's shift (one row of samples, no per-hypothesis check); at the
@@ -223,17 +223,17 @@ int launch_plain_shape(const Ctx &c, const RadarD &R, const float2 *echo, const 
     return check_launch();
 }
 
-// Tile shape of k_plain (hypotheses x bins per thread): 8 x 2 at three CTAs per SM by
-// default; DSGRFT_PLAIN_SHAPE=8x4 or 16x2 selects the two-CTA shapes (the same arithmetic
-// per output, so the same results bit for bit).  For 2^39 hypothesis-pulses: 8 x 2 114.7 ms,
-// 8 x 4 115.9, 16 x 2 116.9 (whole calls, tables included): neither the L2 gathers, which
-// 16 x 2 halves per FMA, nor the occupancy bounds the kernel much.
+// Tile shape of k_plain (hypotheses x bins per thread): 8 x 4 at two CTAs per SM by
+// default; DSGRFT_PLAIN_SHAPE=8x2 (three CTAs per SM) or 16x2 selects the others (the same
+// arithmetic per output, so the same results bit for bit).  For 2^39 hypothesis-pulses:
+// 8 x 4 101.9 ms, 8 x 2 104.7, 16 x 2 105.2 (whole calls, tables included): neither the L2
+// gathers, which 16 x 2 halves per FMA, nor the occupancy bounds the kernel much.
 int plain_shape() {
     static const int v = [] {
         const char *e = getenv("DSGRFT_PLAIN_SHAPE");
         if (e && e[0] == '1') return 2;
-        if (e && e[0] == '8' && e[2] == '4') return 1;
-        return 0;
+        if (e && e[0] == '8' && e[2] == '2') return 0;
+        return 1;
     }();
     return v;
 }
@@ -251,9 +251,9 @@ int launch_plain(const Ctx &c, const RadarD &R, const float2 *echo, const grft_g
     float2 *Yc = Y ? Y + h0 * g.r0_count : nullptr;
     float *Pc = P ? P + h0 * g.r0_count : nullptr;
     switch (plain_shape()) {
-    case 1: return launch_plain_shape<8, 4>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    case 0: return launch_plain_shape<8, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
     case 2: return launch_plain_shape<16, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
-    default: return launch_plain_shape<8, 2>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
+    default: return launch_plain_shape<8, 4>(c, R, echo, g, nh, rho, w, e0, Yc, Pc);
     }
 }
 

@@ -1,5 +1,5 @@
-"""GPU: the tile shapes of the plain GRFT kernel (eq. standard-GRFT-TD), 8 x 2 (the default),
-8 x 4 and 16 x 2 hypotheses x bins per thread (DSGRFT_PLAIN_SHAPE), give the same results bit for bit and match
+"""GPU: the tile shapes of the plain GRFT kernel (eq. standard-GRFT-TD), 8 x 4 (the default),
+8 x 2 and 16 x 2 hypotheses x bins per thread (DSGRFT_PLAIN_SHAPE), give the same results bit for bit and match
 the FP64 oracle on every output within the FP32 tolerance.  The grid mixes hypotheses whose
 bin shifts differ inside a CTA's group (the per-hypothesis reload path) with ones that share
 it, over a ragged pulse count, a partial last group and bins that leave the echo at both
