@@ -55,6 +55,7 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
     __shared__ int s_rho[PL_MCHUNK][PL_H];
     __shared__ alignas(16) float s_w[PL_MCHUNK][H2][4];   // (re h, re h+1, im h, im h+1)
     __shared__ int s_same[PL_MCHUNK];            // every hypothesis of the group shifts like the first
+    __shared__ int s_same3[PL_MCHUNK];           // ... at pulses mm, mm + 1 and mm + 2
     __shared__ int s_rng[2];                     // least and greatest shift of the chunk
 
     const int h0 = blockIdx.y * PL_H;
@@ -98,6 +99,14 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
                 hi = max(hi, r);
             }
             s_same[threadIdx.x] = same;
+            int same3 = same;
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                const int mk = min((int)threadIdx.x + k, PL_MCHUNK - 1);
+#pragma unroll
+                for (int h = 1; h < PL_H; ++h) same3 &= s_rho[mk][h] == s_rho[mk][0];
+            }
+            s_same3[threadIdx.x] = same3;
             lo = __reduce_min_sync(0xffffffffu, lo);
             hi = __reduce_max_sync(0xffffffffu, hi);
             if ((threadIdx.x & 31) == 0) {
@@ -129,26 +138,31 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
             ffma2(are[h2][j], sr, w.x);
             ffma2(aim[h2][j], sr, w.y);
         };
-        // Accumulate pulse mm whose samples (at the first hypothesis' shift) are in sv0.
-        auto pulse = [&](int mm, const float2 (&sv0)[PL_J]) {
+        // pulse mm whose hypotheses all take the samples in sv0
+        auto pulse_same = [&](int mm, const float2 (&sv0)[PL_J]) {
             const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0][0]);
+            // (re, re), (im, im) and (-im, -im) of every sample, reused by all hypotheses
+            uint64_t sr[PL_J], si[PL_J], sn[PL_J];
+#pragma unroll
+            for (int j = 0; j < PL_J; ++j) {
+                sr[j] = pack2(sv0[j].x, sv0[j].x);
+                si[j] = pack2(sv0[j].y, sv0[j].y);
+                sn[j] = pack2(-sv0[j].y, -sv0[j].y);
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < H2; ++h2) {
+                const ulonglong2 w = wp[h2];
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j) mac(h2, j, sr[j], si[j], sn[j], w);
+            }
+        };
+        // pulse mm whose samples at the first hypothesis' shift are in sv0
+        auto pulse = [&](int mm, const float2 (&sv0)[PL_J]) {
             if (s_same[mm]) {                // CTA-uniform: one row of samples for all hypotheses
-                // (re, re), (im, im) and (-im, -im) of every sample, reused by all hypotheses
-                uint64_t sr[PL_J], si[PL_J], sn[PL_J];
-#pragma unroll
-                for (int j = 0; j < PL_J; ++j) {
-                    sr[j] = pack2(sv0[j].x, sv0[j].x);
-                    si[j] = pack2(sv0[j].y, sv0[j].y);
-                    sn[j] = pack2(-sv0[j].y, -sv0[j].y);
-                }
-#pragma unroll
-                for (int h2 = 0; h2 < H2; ++h2) {
-                    const ulonglong2 w = wp[h2];
-#pragma unroll
-                    for (int j = 0; j < PL_J; ++j) mac(h2, j, sr[j], si[j], sn[j], w);
-                }
+                pulse_same(mm, sv0);
                 return;
             }
+            const ulonglong2 *wp = reinterpret_cast<const ulonglong2 *>(&s_w[mm][0][0]);
             int prev = s_rho[mm][0];
             float2 cur[PL_J];
 #pragma unroll
@@ -180,6 +194,19 @@ __global__ __launch_bounds__(PL_THREADS, PL_J == 2 && PL_H == 8 ? 3 : 2) void k_
         load_row(0, s_rho[0][0], b0);
         if (mn > 1) load_row(1, s_rho[1][0], b1);
         for (int mm = 0; mm < mn; mm += 3) {
+            if (inside && mm + 4 < mn && s_same3[mm]) {    // CTA-uniform: three pulses, no branch
+                const float2 *row = echo + (long)(mc + mm) * N + n0;
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j) b2[j] = __ldg(row + 2L * N + s_rho[mm + 2][0] + 32 * j);
+                pulse_same(mm, b0);
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j) b0[j] = __ldg(row + 3L * N + s_rho[mm + 3][0] + 32 * j);
+                pulse_same(mm + 1, b1);
+#pragma unroll
+                for (int j = 0; j < PL_J; ++j) b1[j] = __ldg(row + 4L * N + s_rho[mm + 4][0] + 32 * j);
+                pulse_same(mm + 2, b2);
+                continue;
+            }
             if (mm + 2 < mn) load_row(mm + 2, s_rho[mm + 2][0], b2);
             pulse(mm, b0);
             if (mm + 1 >= mn) break;
