@@ -134,6 +134,7 @@ __global__ __launch_bounds__(256) void k_ds_simt_pair(
     __shared__ alignas(16) float2 sA[SM_BK][SM_BN];
     __shared__ alignas(16) float4 sB[SM_BK][SP_BS];      // (Dr, Dr, Di, Di) of each slot's first hypothesis
     __shared__ int s_f[SP_BS], s_fm[SP_BS];
+    static_assert(SM_BN == 16 * SM_TN && SP_BS == 16 * SM_TF, "16 x 16 threads over the tile");
 
     const int cl = blockIdx.z;
     const int jt = blockIdx.x * SM_BN;
@@ -188,11 +189,17 @@ __global__ __launch_bounds__(256) void k_ds_simt_pair(
             rb[u] = (m < M && f >= 0) ? D[(long)m * F + f] : make_float2(0.f, 0.f);
         }
     };
+    // sA holds each thread's SM_TN bins as SM_TN / 2 16-byte words spread over the row: bin
+    // pair q of thread tx at word q * 16 + tx, so the 16 threads of a row read 256
+    // consecutive bytes per load (their bins tx * SM_TN .. lie 64 bytes apart, which would
+    // put four of every eight threads of a load phase on the same banks)
     auto store = [&]() {
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
             const int i = threadIdx.x + 256 * u;
-            sA[i / SM_BN][i % SM_BN] = Z ? ra[u] : cmul(ra[u], rw[u]);
+            const int jn = i % SM_BN;
+            sA[i / SM_BN][((jn % SM_TN) >> 1) * (SM_BN / SM_TN * 2) + (jn / SM_TN) * 2 + (jn & 1)] =
+                Z ? ra[u] : cmul(ra[u], rw[u]);
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -209,10 +216,10 @@ __global__ __launch_bounds__(256) void k_ds_simt_pair(
         for (int mm = 0; mm < SM_BK; ++mm) {
             uint64_t a[SM_TN];
             ulonglong2 b[SM_TF];
-            const ulonglong2 *pa = reinterpret_cast<const ulonglong2 *>(&sA[mm][tx * SM_TN]);
+            const ulonglong2 *pa = reinterpret_cast<const ulonglong2 *>(&sA[mm][tx * 2]);
 #pragma unroll
             for (int q = 0; q < SM_TN / 2; ++q) {
-                const ulonglong2 t = pa[q];
+                const ulonglong2 t = pa[q * (SM_BN / SM_TN)];
                 a[2 * q] = t.x;
                 a[2 * q + 1] = t.y;
             }
