@@ -173,9 +173,9 @@ int grft_plain(const grft_radar *radar, const grft_c32 *echo, const grft_grid *g
 #define GRFT_PLAIN_STATIC_SCRATCH_BYTES (8u << 20)
 
 /* grft_plain without any device allocation (the paper has no counterpart; this is for
- * callers that cannot call cudaMalloc, e.g. a processing loop with a fixed memory budget,
- * code running during stream capture, or a process whose device memory belongs to another
- * pool).  Same arguments, results and output layout as grft_plain (bit-identical); the
+ * callers that cannot call cudaMalloc, e.g. a processing loop with a fixed memory budget
+ * that must not grow or wait on an allocator, or a process whose device memory belongs to
+ * another pool).  Same arguments, results and output layout as grft_plain (bit-identical); the
  * bin/phase tables live in a fixed array of GRFT_PLAIN_STATIC_SCRATCH_BYTES inside the
  * library image (held by every GPU that loads the library until the process exits)
  * instead of the library workspace, and the grid is processed in chunks that fit it.

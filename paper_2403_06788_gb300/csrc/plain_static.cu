@@ -1,9 +1,9 @@
 // grft_plain_static: plain GRFT that allocates no device memory.
 //
 // Who needs it: callers that must not call cudaMalloc (or any allocating routine) once
-// they are running, such as a radar processing loop that owns a fixed memory budget, code
-// that runs while a CUDA stream is being captured into a graph, or a process whose device
-// memory is managed by someone else's pool.  grft_plain() takes its bin/phase tables from
+// they are running, such as a radar processing loop that owns a fixed memory budget and
+// must not wait on an allocator, or a process whose device memory is managed by someone
+// else's pool.  grft_plain() takes its bin/phase tables from
 // a library workspace that is allocated (and grown) on first use; this variant keeps them
 // in a fixed array that is part of the library image instead, so that the only memory it
 // touches is the caller's (echo, Y, P) and that array.

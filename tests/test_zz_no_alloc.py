@@ -1,5 +1,5 @@
 """grft_plain_static — plain GRFT for callers that cannot allocate device memory (a
-processing loop with a fixed memory budget, code running under stream capture, a process
+processing loop with a fixed memory budget that must not wait on an allocator, a process
 whose device memory belongs to another pool).  It keeps its tables in a fixed array inside
 the library instead of the allocated workspace and runs the same kernels over the same
 groups of hypotheses, so its output must equal grft_plain's bit for bit; two calls in a row
