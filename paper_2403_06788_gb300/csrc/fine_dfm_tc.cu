@@ -248,19 +248,23 @@ __device__ __forceinline__ float2 ld_global_nc_hint(const float2 *src, uint64_t 
 }
 
 __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_constant__ TcBatch B,
-                                                             uint16_t *__restrict__ Zhi,
-                                                             uint16_t *__restrict__ Zlo, int tab_cap) {
+                                                             const __grid_constant__ CUtensorMap mapZhi,
+                                                             const __grid_constant__ CUtensorMap mapZlo,
+                                                             int tab_cap) {
     // One CTA per (item, cell, 128-bin tile), four warps; warp w owns the 32 bins 32w + lane of
     // the tile and every pulse, taken in sub-steps of 8 pulses.  A lane's gathers for one pulse
     // are consecutive bins of the echo row (the warp reads one 256-byte run per pulse).  The
     // converted values pass through a warp-private shared tile [plane][32 rows][8 chunks of
     // 16 bytes] (chunk index XOR row % 8: conflict-free on both sides) and leave, once the four
     // sub-steps of a 32-pulse stage are in, as whole 128-byte lines of the K-major operand rows
-    // (k' = (m/32)*64 + (re|im)*32 + m%32).  The cell's bins and phases are staged in shared
-    // memory; the next sub-step's samples are requested before the current one is converted.
-    extern __shared__ uint4 sp_smem[];          // [warps][2 planes][32][8], then w[tab_cap], rho[tab_cap]
+    // (k' = (m/32)*64 + (re|im)*32 + m%32), written by one tensor-map store per plane and
+    // stage (the tile's chunk XOR row % 8 order is the copy's 128-byte swizzle).  The cell's
+    // bins and phases are staged in shared memory; the next sub-step's samples are requested
+    // before the current one is converted.
+    extern __shared__ uint4 sp_smem[];          // [warps][2 planes][32][8] (1024-byte aligned), then w[tab_cap], rho[tab_cap]
     __shared__ int s_rng[2];                    // least and greatest bin shift of the cell
-    float2 *s_w = reinterpret_cast<float2 *>(sp_smem + SP_TR_WORDS);
+    uint4 *const tiles = reinterpret_cast<uint4 *>((reinterpret_cast<uintptr_t>(sp_smem) + 1023) & ~(uintptr_t)1023);
+    float2 *s_w = reinterpret_cast<float2 *>(tiles + SP_TR_WORDS);
     int *s_rho = reinterpret_cast<int *>(s_w + tab_cap);
     const TcItem &p = B.it[find_item_cta(B, blockIdx.x)];
     const int local = blockIdx.x - p.cta0;
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
     }
     const int *rho_t = tab_smem ? s_rho : B.rho + tab;
     const float2 *w_t = tab_smem ? s_w : B.w + tab;
-    uint4 *tr = sp_smem + warp * 512;            // this warp's tile: hi plane, then lo plane
+    uint4 *tr = tiles + warp * 512;              // this warp's tile: hi plane, then lo plane
     const size_t row0 = (size_t)p.zrow0 + (size_t)cl * p.r0_pad + j0 + warp * 32;
     const uint64_t pol_z = l2_policy_evict_first();
     const bool with_lo = B.nprod >= 2;          // block-uniform
@@ -319,6 +323,10 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
             split2(re[2 * q], re[2 * q + 1], fp16, rh[q], rl[q]);
             split2(im[2 * q], im[2 * q + 1], fp16, ih[q], il[q]);
         }
+        if (g == 0) {                            // the previous stage's copies have read the tile
+            if (lane == 0) bulk_wait_read<0>();
+            __syncwarp();
+        }
         tr[lane * 8 + (g ^ sw)] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
         tr[lane * 8 + ((4 + g) ^ sw)] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
         if (with_lo) {
@@ -326,21 +334,20 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
             tr[256 + lane * 8 + ((4 + g) ^ sw)] = make_uint4(il[0], il[1], il[2], il[3]);
         }
         if (g == 3) {
+            // the stage's 32 rows x 128 bytes per plane, one tensor-map store each
+            fence_proxy_async_shared();
             __syncwarp();
-            // the lane's 16-byte chunk ch = lane mod 8 of each row: 8 pulses of one part
-            const int ch = lane & 7;
-            const int col = kt * TC_BK + ch * 8;
-            for (int pl = 0; pl < (with_lo ? 2 : 1); ++pl) {
-                uint16_t *Z = pl ? Zlo : Zhi;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int row = (q * 32 + lane) >> 3;
-                    const uint4 x = tr[pl * 256 + row * 8 + (ch ^ (row & 7))];
-                    st_global_v4_hint(Z + (row0 + row) * (size_t)B.zld + col, x.x, x.y, x.z, x.w, pol_z);
-                }
+            if (lane == 0) {
+                tma_store_2d_hint(&mapZhi, tr, kt * TC_BK, (int)row0, pol_z);
+                if (with_lo) tma_store_2d_hint(&mapZlo, tr + 256, kt * TC_BK, (int)row0, pol_z);
+                bulk_commit();
             }
-            __syncwarp();
         }
+    };
+    // every copy has completed before the CTA's shared memory goes
+    auto finish = [&]() {
+        if (lane == 0) bulk_wait<0>();
+        __syncwarp();
     };
 
     // Fast path (block-uniform): the tables are staged, every bin of the tile is inside the
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
                 cv(s + 2, vc);
                 cv(s + 3, vd);
             }
+            finish();
             return;
         }
         const int Sw = p.M / 8;                 // whole sub-steps
@@ -412,6 +420,7 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
             }
             put(s, re, im);
         }
+        finish();
         return;
     }
 
@@ -452,6 +461,7 @@ __global__ void __launch_bounds__(SP_THREADS, 4) k_coarse_split(const __grid_con
         if (s + 2 < S) load8(s + 2, va);
         cv8(s + 1, vb);
     }
+    finish();
 }
 
 // =========================================================================== kernel b
@@ -1244,18 +1254,28 @@ struct Round {
     long rows;
 };
 
-int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo) {
-    // shared memory: the warp tiles, then the bins and phases of a cell (largest M of the
-    // round, up to SP_TAB_MAX; larger items read their tables from global memory)
+int launch_split(const Ctx &c, const TcBatch &b, uint16_t *Zhi, uint16_t *Zlo, long zrows) {
+    // shared memory: the warp tiles (1024-byte aligned for the 128-byte swizzle), then the
+    // bins and phases of a cell (largest M of the round, up to SP_TAB_MAX; larger items read
+    // their tables from global memory)
     static bool attr[64] = {false};
     int cap = 0;
     for (int i = 0; i < b.n_items; ++i) cap = b.it[i].M > cap ? b.it[i].M : cap;
     if (cap > SP_TAB_MAX) cap = SP_TAB_MAX;
-    const size_t most = SP_TR_WORDS * sizeof(uint4) + (size_t)SP_TAB_MAX * (sizeof(float2) + sizeof(int));
-    const size_t bytes = SP_TR_WORDS * sizeof(uint4) + (size_t)cap * (sizeof(float2) + sizeof(int));
+    const size_t most = 1024 + SP_TR_WORDS * sizeof(uint4) + (size_t)SP_TAB_MAX * (sizeof(float2) + sizeof(int));
+    const size_t bytes = 1024 + SP_TR_WORDS * sizeof(uint4) + (size_t)cap * (sizeof(float2) + sizeof(int));
     if (c.device >= 64 || !set_smem_attr((const void *)k_coarse_split, most, c.device, attr)) return GRFT_ECUDA;
+    // the operand planes as [rows][zld] 16-bit elements; a box of 64 elements (one 32-pulse
+    // stage: re and im parts) x 32 rows is one warp tile
+    CUtensorMap mh, ml;
+    if (zrows <= 0 || zrows > 0x7fffffffL) return GRFT_EINVAL;
+    if (!encode_tma_2d(&mh, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)Zhi, (uint64_t)b.zld, (uint64_t)zrows,
+                       (uint64_t)b.zld * 2, TC_BK, 32, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_tma_2d(&ml, CU_TENSOR_MAP_DATA_TYPE_UINT16, (void *)(Zlo ? Zlo : Zhi), (uint64_t)b.zld,
+                       (uint64_t)zrows, (uint64_t)b.zld * 2, TC_BK, 32, CU_TENSOR_MAP_SWIZZLE_128B))
+        return GRFT_ECUDA;
     KernelTimer kt(c, GRFT_KERNEL_SPLIT);
-    k_coarse_split<<<b.total_ctas, SP_THREADS, bytes, c.stream>>>(b, Zhi, Zlo, cap);
+    k_coarse_split<<<b.total_ctas, SP_THREADS, bytes, c.stream>>>(b, mh, ml, cap);
     return check_launch();
 }
 
@@ -1437,7 +1457,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     }();
     if (rounds.size() == 1 || !Zhi[1] || !Zlo[1] || !overlap) {   // rounds in sequence on the caller's stream
         for (const Round &rd : rounds) {
-            if ((e = launch_split(c, rd.b, Zhi[0], Zlo[0]))) return e;
+            if ((e = launch_split(c, rd.b, Zhi[0], Zlo[0], rd.rows))) return e;
             if ((e = launch_round_gemm(c, rd, Mpad, Fpad, Bhi, Blo, Zhi[0], Zlo[0], variant, key))) return e;
         }
         return GRFT_OK;
@@ -1454,7 +1474,7 @@ int launch_ds_tc(const Ctx &c, const DsTcItem *items, int n_items, const grft_ds
     for (size_t r = 0; r < rounds.size(); ++r) {
         const int buf = (int)(r & 1);
         if (r >= 2 && cudaStreamWaitEvent(pp->side, pp->gemm_done[buf], 0) != cudaSuccess) return GRFT_ECUDA;
-        if ((e = launch_split(cs, rounds[r].b, Zhi[buf], Zlo[buf]))) return e;
+        if ((e = launch_split(cs, rounds[r].b, Zhi[buf], Zlo[buf], rounds[r].rows))) return e;
         if (cudaEventRecord(pp->split_done[buf], pp->side) != cudaSuccess ||
             cudaStreamWaitEvent(c.stream, pp->split_done[buf], 0) != cudaSuccess)
             return GRFT_ECUDA;
